@@ -1,0 +1,295 @@
+"""Seeded synthetic inputs for the N-component free-energy LBM.
+
+This module is the one piece shared by the oracle, the tests and the
+benchmark.  It holds no arithmetic of the method itself: it only builds
+initial volume-fraction fields (tanh-smoothed discs, layers and half-spaces,
+or seeded random mixtures), surface-tension matrices and run parameters, in
+FP64 on the host, with numpy's PCG64 generator.  Neither the oracle nor the
+CUDA library draws random numbers, so both sides always see identical inputs.
+
+Array convention: every field has shape (nz, ny, nx) (nz = 1 for 2-D), so a
+C-order ravel gives the x-fastest site index used by the C ABI.  A field
+stack for N components has shape (N, nz, ny, nx).
+
+Interface profile: a "tanh interface of width 2 lu" is read as
+C = 1/2 (1 + tanh(d / 2)) with d the signed distance, which is the D = 4
+equilibrium profile 1/2 (1 + tanh(2 d / D)) of the free energy in Sec. II.
+Interfaces are placed half-way between nodes so that no node starts with two
+equal largest volume fractions (the viscosity rule of Sec. III B picks the
+largest one).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+D2Q9 = 9
+D3Q19 = 19
+
+__all__ = [
+    "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
+    "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
+    "batch_sweep", "random_sigma", "random_simplex_points", "CONFIGS",
+]
+
+
+def tanh_step(d):
+    """1/2 (1 + tanh(d/2)): 1 deep on the positive side of a width-2 interface."""
+    return 0.5 * (1.0 + np.tanh(0.5 * np.asarray(d, dtype=np.float64)))
+
+
+def _coords(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64),
+                          np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def random_sigma(rng, N, lo=0.004, hi=0.012):
+    """Symmetric N x N surface-tension matrix, off-diagonal U(lo, hi), zero diagonal."""
+    s = np.zeros((N, N))
+    for i in range(N):
+        for j in range(i + 1, N):
+            s[i, j] = s[j, i] = rng.uniform(lo, hi)
+    return s
+
+
+def random_simplex_points(rng, N, count, absent=None):
+    """Random points on the unit simplex sum_i C_i = 1 (component `absent` set to 0)."""
+    x = rng.uniform(0.0, 1.0, size=(count, N))
+    if absent is not None:
+        x[:, absent] = 0.0
+    return x / x.sum(axis=1, keepdims=True)
+
+
+def base_params(lattice, nx, ny, nz, N, sigma, tau, *, walls=(False, False, False),
+                lambda_trt=-1.0, m=1.0 / 50.0, D=4.0, omega_stab=float("nan"),
+                body_force=(0.0, 0.0, 0.0), implicit=None, name=""):
+    sigma = np.asarray(sigma, dtype=np.float64)
+    tau = np.asarray(tau, dtype=np.float64)
+    if tau.ndim == 0:
+        tau = np.full(N, float(tau))
+    return dict(name=name, lattice=lattice, nx=nx, ny=ny, nz=nz,
+                walls=tuple(bool(w) for w in walls), N=N, sigma=sigma, tau=tau,
+                lambda_trt=float(lambda_trt), m=float(m), D=float(D),
+                omega_stab=float(omega_stab),
+                body_force=tuple(float(b) for b in body_force),
+                implicit=(N - 1 if implicit is None else int(implicit)))
+
+
+def lens_2d(nx=64, ny=64, radius=12.0, sigma3=(0.01, 0.008, 0.008), tau=1.0, m=0.05,
+            extra_sigma=None, N=3, walls_y=True):
+    """Liquid lens: C1 below, C2 above a horizontal interface, a disc of C3 on it.
+
+    Defaults are the 64 x 64 lens (periodic in x, walls in y) with
+    (sigma12, sigma13, sigma23) = (0.01, 0.008, 0.008), tau = 1, m = 0.05.
+    For N > 3 the extra components are small discs of radius ny/8 placed in
+    the lower fluid, each with its own sigma row from `extra_sigma`.
+    """
+    x, y, z = _coords(nx, ny, 1)
+    yc = ny / 2.0 - 0.5
+    xc = nx / 2.0 - 0.5
+    lower = tanh_step(yc - y)
+    disc = tanh_step(radius - np.hypot(x - xc, y - yc))
+    C = np.zeros((N, 1, ny, nx))
+    C[2] = disc
+    C[0] = lower * (1.0 - disc)
+    C[1] = (1.0 - lower) * (1.0 - disc)
+    s12, s13, s23 = sigma3
+    sigma = np.zeros((N, N))
+    sigma[0, 1] = sigma[1, 0] = s12
+    sigma[0, 2] = sigma[2, 0] = s13
+    sigma[1, 2] = sigma[2, 1] = s23
+    if N > 3:
+        r = ny / 8.0
+        for e in range(3, N):
+            cx = (e - 2) * nx / (N - 1) - 0.5
+            cy = ny / 4.0 - 0.5
+            d = tanh_step(r - np.hypot(x - cx, y - cy))
+            C[:3] *= (1.0 - d)
+            C[e] = d
+            for j in range(N):
+                if j != e:
+                    val = extra_sigma[e][j] if extra_sigma is not None else 0.005
+                    sigma[e, j] = sigma[j, e] = val
+    p = base_params(D2Q9, nx, ny, 1, N, sigma, tau, walls=(False, walls_y, False), m=m,
+                    name=f"lens_{nx}x{ny}_N{N}")
+    p["C0"] = C
+    return p
+
+
+def spinodal_2d(nx=512, ny=512, N=4, seed=1002, amp=0.02, sigma=0.005, tau=0.8, m=0.1):
+    """Quaternary spinodal mixture: C_i = 1/N + U(-amp, amp), renormalised to sum 1."""
+    rng = np.random.default_rng(seed)
+    C = 1.0 / N + rng.uniform(-amp, amp, size=(N, 1, ny, nx))
+    C /= C.sum(axis=0, keepdims=True)
+    sig = np.full((N, N), float(sigma))
+    np.fill_diagonal(sig, 0.0)
+    p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, name=f"spinodal_{nx}x{ny}_N{N}")
+    p["C0"] = C
+    return p
+
+
+def layered_poiseuille(nx=32, ny=32, nz=192, taus=(0.6, 0.7, 0.8, 0.9, 1.0, 1.2),
+                       force=1e-6, lattice=D3Q19, absent=True, sigma=0.005, m=1.0 / 50.0):
+    """Equal fluid layers stacked along the wall-normal axis with a body force along x.
+
+    3-D (D3Q19): walls at the z ends, layers along z.  2-D (D2Q9, nz must be 1):
+    walls at the y ends, layers along y.  With `absent`, one more component is
+    added that is identically zero; it is an evolved component and layer 0 is
+    the implicit one (C_implicit = 1 - sum of the others).
+    """
+    L = len(taus)
+    if lattice == D3Q19:
+        x, y, z = _coords(nx, ny, nz)
+        s, W = z, nz
+        walls = (False, False, True)
+    else:
+        assert nz == 1
+        x, y, z = _coords(nx, ny, 1)
+        s, W = y, ny
+        walls = (False, True, False)
+    N = L + (1 if absent else 0)
+    width = W / L
+    C = np.zeros((N,) + s.shape)
+    H = [tanh_step(s - (b * width - 0.5)) for b in range(1, L)]
+    C[0] = 1.0 - H[0]
+    for lay in range(1, L - 1):
+        C[lay] = H[lay - 1] - H[lay]
+    C[L - 1] = H[L - 2]
+    tau = list(taus) + ([1.0] if absent else [])
+    sig = np.full((N, N), float(sigma))
+    np.fill_diagonal(sig, 0.0)
+    p = base_params(lattice, nx, ny, nz if lattice == D3Q19 else 1, N, sig, tau,
+                    walls=walls, lambda_trt=3.0 / 16.0, m=m,
+                    body_force=(force, 0.0, 0.0), implicit=0,
+                    name=f"poiseuille_{nx}x{ny}x{nz}_N{N}")
+    p["C0"] = C
+    p["layer_width"] = width
+    return p
+
+
+def _janus_fields(x, y, z, centres, pairs, radius, N, split_axis=0):
+    C = np.zeros((N,) + x.shape)
+    for (cx, cy, cz), (a, b) in zip(centres, pairs):
+        r = np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2)
+        drop = tanh_step(radius - r)
+        coord = (x, y, z)[split_axis] - (cx, cy, cz)[split_axis]
+        h = tanh_step(coord)
+        C[a] += drop * (1.0 - h)
+        C[b] += drop * h
+    C[0] = 1.0 - C[1:].sum(axis=0)
+    return C
+
+
+def janus_3d(n=256, radius=32.0, seed=1004, N=4, tau=1.0, m=1.0 / 50.0):
+    """Four Janus droplets (two components each, split by the plane x = x_c) in matrix C1."""
+    rng = np.random.default_rng(seed)
+    sig = random_sigma(rng, N)
+    x, y, z = _coords(n, n, n)
+    q = n / 4.0
+    centres = [(q - 0.5, q - 0.5, q - 0.5), (3 * q - 0.5, 3 * q - 0.5, q - 0.5),
+               (q - 0.5, 3 * q - 0.5, 3 * q - 0.5), (3 * q - 0.5, q - 0.5, 3 * q - 0.5)]
+    pairs = [(1, 2), (2, 3), (1, 3), (1, 2)]
+    C = _janus_fields(x, y, z, centres, pairs, radius * n / 256.0 if n != 256 else radius, N)
+    p = base_params(D3Q19, n, n, n, N, sig, tau, m=m, name=f"janus3d_{n}^3_N{N}")
+    p["C0"] = C
+    p["centres"] = centres
+    p["radius"] = radius * n / 256.0 if n != 256 else radius
+    return p
+
+
+def janus_2d(nx=100, ny=100, radius=20.0, offset=25.0, tau=1.0, m=1.0 / 50.0, sigma=None):
+    """Janus droplet of Sec. IV A: fluid 2 disc in the centre, discs of 3 and 4 at +/- offset.
+
+    Overlaps are removed in the order 2, 3, 4 (later discs take only what is
+    left).  Default tensions: sigma14 = sigma24 = 0.0095, the rest 0.005.
+    """
+    x, y, z = _coords(nx, ny, 1)
+    xc, yc = nx / 2.0 - 0.5, ny / 2.0 - 0.5
+    d2 = tanh_step(radius - np.hypot(x - xc, y - yc))
+    d3 = tanh_step(radius - np.hypot(x - xc - offset, y - yc)) * (1.0 - d2)
+    d4 = tanh_step(radius - np.hypot(x - xc + offset, y - yc)) * (1.0 - d2 - d3)
+    C = np.zeros((4, 1, ny, nx))
+    C[1], C[2], C[3] = d2, d3, d4
+    C[0] = 1.0 - C[1:].sum(axis=0)
+    if sigma is None:
+        sigma = np.full((4, 4), 0.005)
+        sigma[0, 3] = sigma[3, 0] = 0.0095
+        sigma[1, 3] = sigma[3, 1] = 0.0095
+        np.fill_diagonal(sigma, 0.0)
+    p = base_params(D2Q9, nx, ny, 1, 4, sigma, tau, m=m, name=f"janus2d_{nx}x{ny}")
+    p["C0"] = C
+    return p
+
+
+def droplet_2d(n=128, radius=20.0, sigma=0.005, tau=1.0, m=1.0 / 50.0):
+    """Binary droplet (component 1) of the given radius in component 0, periodic box."""
+    x, y, z = _coords(n, n, 1)
+    c = n / 2.0 - 0.5
+    d = tanh_step(radius - np.hypot(x - c, y - c))
+    C = np.stack([1.0 - d, d])
+    sig = np.array([[0.0, sigma], [sigma, 0.0]])
+    p = base_params(D2Q9, n, n, 1, 2, sig, tau, m=m, name=f"droplet_{n}_R{radius}")
+    p["C0"] = C
+    p["radius"] = radius
+    p["centre"] = (c, c)
+    return p
+
+
+def planar_2d(nx=4, ny=64, sigma=0.005, tau=1.0, m=1.0 / 50.0, offset=0.0, width=2.0):
+    """Binary slab: component 1 for |y - yc| < ny/4, with tanh edges of width `width` lu."""
+    x, y, z = _coords(nx, ny, 1)
+    yc = ny / 2.0 - 0.5
+    a = 0.5 * (1.0 + np.tanh((ny / 4.0 - np.abs(y - yc) + offset) / width))
+    C = np.stack([1.0 - a, a])
+    sig = np.array([[0.0, sigma], [sigma, 0.0]])
+    p = base_params(D2Q9, nx, ny, 1, 2, sig, tau, m=m, name=f"planar_{nx}x{ny}")
+    p["C0"] = C
+    return p
+
+
+def batch_sweep(nsims=512, seed=1005, sizes=(64, 96, 128, 192, 256), Ns=(3, 4, 5)):
+    """Parameter sweep: even-indexed simulations are lenses, odd-indexed are Janus drops.
+
+    Grid edge, N and the surface tensions are drawn per simulation from the
+    generator seeded with seed + index.  All are FP32-path jobs with tau = 1.
+    """
+    sims = []
+    for s in range(nsims):
+        rng = np.random.default_rng(seed + s)
+        n = int(rng.choice(sizes))
+        N = int(rng.choice(Ns))
+        sig = random_sigma(rng, N)
+        if s % 2 == 0:
+            p = lens_2d(nx=n, ny=n, radius=n * 12.0 / 64.0,
+                        sigma3=(sig[0, 1], sig[0, 2], sig[1, 2]), tau=1.0, m=0.05,
+                        extra_sigma=sig, N=N, walls_y=True)
+        else:
+            x, y, z = _coords(n, n, 1)
+            c = n / 2.0 - 0.5
+            rad = n * 20.0 / 100.0
+            drop = tanh_step(rad - np.hypot(x - c, y - c))
+            h = tanh_step(x - c)
+            C = np.zeros((N, 1, n, n))
+            C[1] = drop * (1.0 - h)
+            C[2] = drop * h
+            for e in range(3, N):
+                cx = (e - 2) * n / (N - 1) - 0.5
+                d = tanh_step(n / 8.0 - np.hypot(x - cx, y - (n / 8.0 + 1.5)))
+                C[1:e] *= (1.0 - d)
+                C[e] = d
+            C[0] = 1.0 - C[1:].sum(axis=0)
+            p = base_params(D2Q9, n, n, 1, N, sig, 1.0, m=0.05, name=f"janus_{n}_N{N}")
+            p["C0"] = C
+        p["index"] = s
+        sims.append(p)
+    return sims
+
+
+# The five reference workloads, by name; each entry builds its parameter dict.
+CONFIGS = {
+    "lens64_N3_fp64": lambda: lens_2d(),
+    "spinodal512_N4": lambda: spinodal_2d(),
+    "poiseuille3d_N7": lambda: layered_poiseuille(),
+    "janus3d256_N4": lambda: janus_3d(),
+}
