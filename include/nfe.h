@@ -1,0 +1,206 @@
+/*
+ * nfe.h -- C ABI of the N-component free-energy lattice Boltzmann library
+ * (arXiv 2605.22214, Rennick, Zhang, Bingert, Krause and Kusumaatmaja),
+ * built for one NVIDIA GB300 (sm_103a).
+ *
+ * The library advances, on one GPU, the per-time-step lattice update of the
+ * paper's method for N immiscible components:
+ *   - isotropic gradients and Laplacians of the volume fractions C_i
+ *     (Sec. III A, Eqs. 35-36), the chemical potentials (Sec. II, Eq. 7) and
+ *     the reduction-consistent flux potential
+ *     S_i = sum_j alpha_ij (mu_j + phi_j + xi_j)          (Sec. II, Eqs. 8-19),
+ *   - the momentum-conserving surface-tension force
+ *     F_s = grad E_B + sum_{i != j} kappa_ij lap C_j grad C_i  (Sec. III A, Eq. 34),
+ *   - TRT collision with forcing and streaming of the hydrodynamic populations
+ *     f_k on D2Q9 or D3Q19 (Sec. III A, Eqs. 22-30, 37-38), and the
+ *     Cahn-Hilliard lattice Boltzmann update of the N-1 evolved volume
+ *     fractions (Sec. III B, Eqs. 39-43) with tau_g = 1,
+ *   - halfway bounce-back and the wall-gradient rule on walls, periodic
+ *     wrap on every other edge (Sec. III C, Eqs. 44-45).
+ *
+ * Conventions shared by every call:
+ *   - Site index s = x + nx * (y + ny * z), x fastest.  Field arrays are
+ *     planar: component c of site s sits at [c * n + s], n = nx * ny * nz.
+ *   - Components are numbered 0 .. N-1 (the paper counts 1 .. N).  One of them,
+ *     `implicit_component`, is not evolved: C_implicit = 1 - sum of the others
+ *     (Sec. II, below Eq. 3).  An absent component that must stay exactly 0.0
+ *     has to be an evolved one.
+ *   - The library owns all device memory it allocates (cudaMalloc at create,
+ *     cudaFree at destroy).  Host buffers passed in are read or written
+ *     during the call only and remain the caller's.
+ *   - Every call returns an nfe_status; none throws, aborts or exits.
+ *     nfe_last_error() gives a one-line message for the last failure on the
+ *     calling thread.
+ *   - Work is queued on the stream given in nfe_params.cuda_stream (borrowed;
+ *     NULL = the legacy default stream).  nfe_step is asynchronous; the calls
+ *     that return data to the host synchronise that stream.
+ */
+#ifndef NFE_H
+#define NFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    NFE_OK = 0,
+    NFE_EINVAL = 1,        /* an argument is out of range or inconsistent */
+    NFE_ENOMEM = 2,        /* device or host allocation failed */
+    NFE_ECUDA = 3,         /* a CUDA runtime call failed (message in nfe_last_error) */
+    NFE_ESINGULAR = 4,     /* the alpha, Lambda or Theta system (Eqs. 8-19) has no unique solution */
+    NFE_ENONFINITE = 5,    /* a kernel produced a NaN or Inf volume fraction */
+    NFE_ETIMEOUT = 6,      /* a device-side wait of the batched kernel ran out of spins */
+    NFE_EUNSUPPORTED = 7   /* a valid combination this build does not implement */
+} nfe_status;
+
+enum { NFE_D2Q9 = 9, NFE_D3Q19 = 19 };
+
+enum {
+    NFE_FP64 = 0,             /* all state and arithmetic in FP64 */
+    NFE_FP32 = 1,             /* f and C stored and computed in FP32 */
+    NFE_FP32_F16STORE = 2,    /* f stored as FP16 f_k / w_k * 2^scale_exp, arithmetic FP32 */
+    NFE_FP32_BF16STORE = 3    /* f stored as BF16 f_k / w_k, arithmetic FP32 */
+};
+
+enum { NFE_WALL_X = 1, NFE_WALL_Y = 2, NFE_WALL_Z = 4 };
+
+/* Flags (nfe_params.flags). */
+enum {
+    NFE_NONCONSERVATIVE_FORCE = 1,  /* F_s = sum_i mu_i grad C_i (Eq. 31) instead of Eq. 34 */
+    NFE_NO_PHI = 2                  /* drop phi_j from the flux potential (Eq. 12) */
+};
+
+#define NFE_MAX_N 8
+
+/* Lattice and domain.  2-D grids use NFE_D2Q9 with nz = 1.  A set bit of
+ * wall_mask puts halfway walls at -1/2 and n_axis - 1/2 on that axis
+ * (Sec. III C); the other axes are periodic. */
+typedef struct {
+    int lattice;              /* NFE_D2Q9 or NFE_D3Q19 */
+    int nx, ny, nz;           /* nodes per axis, each >= 1 (nz = 1 for D2Q9); nx*ny*nz < 2^31 */
+    unsigned wall_mask;       /* NFE_WALL_* bits; NFE_WALL_Z is invalid for D2Q9 */
+} nfe_grid;
+
+/* Physical and numerical parameters (Sec. II and Sec. III). */
+typedef struct {
+    const double *sigma;      /* N x N surface tensions, row-major, symmetric,
+                                 zero diagonal, positive off-diagonal (host) */
+    const double *tau;        /* N relaxation times tau_i > 1/2; omega+ = 1/tau of
+                                 the component with the largest C (Eq. 42) (host) */
+    double lambda_trt;        /* magic parameter of Eq. 26; < 0 selects BGK (omega- = omega+) */
+    double m;                 /* coefficient m of g^eq (Eq. 40); mobility M = m / 6 (Eq. 43, tau_g = 1) */
+    double D;                 /* interface width (Sec. II; the paper uses 4) */
+    double omega_stab;        /* Omega of Eq. 17; NaN selects 0 when every spreading
+                                 parameter (Eq. 16) is negative and 1/90 otherwise */
+    double body_force[3];     /* F_b (Eq. 2), lattice units */
+    int precision;            /* NFE_FP64, NFE_FP32, NFE_FP32_F16STORE, NFE_FP32_BF16STORE */
+    int implicit_component;   /* 0 .. N-1: the component computed as 1 - sum of the others */
+    int flags;                /* NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI (ablations) */
+    int scale_exp;            /* FP16 storage scale 2^scale_exp; ignored otherwise */
+    void *cuda_stream;        /* cudaStream_t to queue work on (borrowed); NULL = default */
+} nfe_params;
+
+/* Global quantities of the current state, reduced on the GPU in FP64. */
+typedef struct {
+    int64_t step;                    /* time steps taken since create / set_fields */
+    int N;
+    double mass[NFE_MAX_N];          /* sum over sites of C_i */
+    double momentum[3];              /* sum over sites of rho v, v of Eq. 37 (incl. F/2) */
+    double force_sum[3];             /* sum over sites of F_s */
+    double force_abs_sum[3];         /* sum over sites of |F_s| per axis */
+    double max_abs_C[NFE_MAX_N];     /* max over sites of |C_i| */
+    double min_C[NFE_MAX_N];         /* min over sites of C_i */
+    double max_speed;                /* max over sites of |v| */
+    int nonfinite;                   /* 1 if any population or volume fraction is NaN/Inf */
+} nfe_diag;
+
+/* Facts about a created simulation. */
+typedef struct {
+    int lattice, N, precision;
+    int64_t sites;                   /* nx * ny * nz */
+    double omega_stab;               /* Omega actually used */
+    double factor_residual;          /* largest dropped coefficient of the factored flux
+                                        potential, relative (checks alpha/Lambda/Theta) */
+    int kernels_per_step;            /* kernel launches of one nfe_step(1) */
+    double min_bytes_per_site;       /* f (Q-1) and C (N-1) read once and written once */
+    size_t state_bytes;              /* size of the raw state (nfe_get_state) */
+    size_t device_bytes;             /* device memory held by the simulation */
+} nfe_info;
+
+typedef struct nfe_sim nfe_sim;
+
+/* Validate the arguments, build the tables of Sec. II (alpha and gamma from
+ * Eqs. 8-9, Lambda from Eqs. 14-15, Theta from Eqs. 18-19, and the factored
+ * flux potential S_i = C_i q_i(C) + (3D/4) lap C_i), allocate the device
+ * state and set f = 0 (P = 0, v = 0) and C = 0.
+ * Errors: NFE_EINVAL (bad grid, N outside 2..8, tau <= 1/2, sigma not
+ * symmetric or not positive, bad precision or flags), NFE_ESINGULAR,
+ * NFE_ENOMEM, NFE_ECUDA.  *out is NULL on error. */
+nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *params, nfe_sim **out);
+
+/* Set the volume fractions (host, FP64, N x n; the row of the implicit
+ * component is ignored and recomputed) and optionally the velocity (host,
+ * FP64, 3 x n, or NULL for rest).  Populations are set to f^eq(P = 0, v)
+ * (Eq. 27).  Resets the step counter.  Synchronises the stream. */
+nfe_status nfe_set_fields(nfe_sim *sim, const double *C, const double *v);
+
+/* Queue nsteps >= 0 time steps on the stream (asynchronous; replays a
+ * captured CUDA graph).  Returns launch errors only; use nfe_sync or
+ * nfe_diagnostics to learn about NFE_ENONFINITE. */
+nfe_status nfe_step(nfe_sim *sim, int64_t nsteps);
+
+/* Wait for the stream; NFE_ENONFINITE if a volume fraction went NaN/Inf. */
+nfe_status nfe_sync(nfe_sim *sim);
+
+/* Copy the current fields to host FP64 buffers (each may be NULL):
+ * C (N x n, all components), v (3 x n, Eq. 37), P (n, Eq. 38).
+ * Synchronises the stream. */
+nfe_status nfe_fields(nfe_sim *sim, double *C, double *v, double *P);
+
+/* Copy the populations f_k, k = 1 .. Q-1, to a host FP64 buffer ((Q-1) x n),
+ * in the velocity order of Eqs. 20-21 (D2Q9) or the D3Q19 order documented
+ * in the design doc.  f_0 is not kept: it feeds no moment.  Synchronises. */
+nfe_status nfe_populations(nfe_sim *sim, double *f);
+
+/* FP64 reductions of the current state on the GPU.  Synchronises. */
+nfe_status nfe_diagnostics(nfe_sim *sim, nfe_diag *out);
+
+/* Raw state (checkpoint / resume, host buffer of info.state_bytes bytes):
+ * populations and evolved volume fractions in device format, plus the step
+ * counter.  get then set restores the simulation bit for bit. */
+nfe_status nfe_get_state(nfe_sim *sim, void *host_buf, size_t bytes);
+nfe_status nfe_set_state(nfe_sim *sim, const void *host_buf, size_t bytes);
+
+nfe_status nfe_get_info(const nfe_sim *sim, nfe_info *out);
+
+/* Kernel timing on the simulation's stream: when enabled, CUDA events bracket
+ * every kernel launch of nfe_step (graphs are bypassed).  read returns, per
+ * kernel kind, the launch count and total milliseconds since the last reset.
+ * names[i] points to static strings. */
+nfe_status nfe_profile_enable(nfe_sim *sim, int on);
+nfe_status nfe_profile_read(nfe_sim *sim, int max_kinds, int *kinds,
+                            const char **names, int64_t *launches, double *total_ms);
+
+void nfe_destroy(nfe_sim *sim);
+
+/* Host-only evaluation (no GPU) of the library's factored bulk flux potential
+ * S_i = C_i q_i(C), i.e. sum_j alpha_ij (dE_B/dC_j + phi_j + xi_j) of Eq. 12
+ * without its Laplacian terms, exactly as the kernels evaluate it, at npts
+ * points C (host, npts x N, row-major, on the simplex).  S (host, npts x N)
+ * receives S_i for the evolved components and 0 for the implicit one.  Same
+ * validation and errors as nfe_create for sigma, D, omega_stab and
+ * implicit_component. */
+nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double omega_stab,
+                                   int implicit_component, int npts, const double *C, double *S);
+
+const char *nfe_status_string(nfe_status s);
+const char *nfe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFE_H */

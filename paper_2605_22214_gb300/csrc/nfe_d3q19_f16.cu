@@ -1,0 +1,6 @@
+// D3Q19 time-step kernels, N = 2 .. 8, f16 storage/arithmetic variant.
+#include "nfe_kernels.cuh"
+
+namespace nfe {
+const Ops *ops_d3q19_f16(int N) { return ops_for_n<LD3Q19, float, __half>(N, NFE_FP32_F16STORE); }
+}  // namespace nfe

@@ -1,0 +1,596 @@
+// Host side of the C ABI declared in include/nfe.h: validation, the Sec. II
+// tables, device memory, CUDA-graph replay of the time step, checkpoints,
+// diagnostics and kernel timing.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nfe_internal.h"
+#include "nfe_tables.h"
+
+using namespace nfe;
+
+namespace {
+
+thread_local std::string g_err;
+
+nfe_status fail(nfe_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+nfe_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(NFE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);         \
+    } while (0)
+
+const Ops *select_ops(int lattice, int N, int prec) {
+    if (lattice == NFE_D2Q9) {
+        switch (prec) {
+            case NFE_FP64: return ops_d2q9_fp64(N);
+            case NFE_FP32: return ops_d2q9_fp32(N);
+            case NFE_FP32_F16STORE: return ops_d2q9_f16(N);
+            case NFE_FP32_BF16STORE: return ops_d2q9_bf16(N);
+        }
+    } else if (lattice == NFE_D3Q19) {
+        switch (prec) {
+            case NFE_FP64: return ops_d3q19_fp64(N);
+            case NFE_FP32: return ops_d3q19_fp32(N);
+            case NFE_FP32_F16STORE: return ops_d3q19_f16(N);
+            case NFE_FP32_BF16STORE: return ops_d3q19_bf16(N);
+        }
+    }
+    return nullptr;
+}
+
+struct TimedLaunch {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct nfe_sim {
+    nfe_grid grid{};
+    int N = 0;
+    int prec = 0;
+    Geom geom{};
+    const Ops *ops = nullptr;
+    Tables tab;
+    Coef<double> cd{};
+    Coef<float> cfl{};
+    const void *coef = nullptr;       // points at cd or cfl
+    void *q4dev = nullptr;
+    Buffers buf{};
+    int uidx[NFE_MAX_N] = {0};        // internal slot -> user component
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int64_t step = 0;
+    size_t fplanes_bytes = 0, cplanes_bytes = 0;
+    size_t fields_planes = 0;
+    size_t device_bytes = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool profiling = false;
+    std::vector<TimedLaunch> timed;
+    std::vector<cudaEvent_t> event_pool;
+    int64_t prof_launches[K_NKINDS] = {0};
+    double prof_ms[K_NKINDS] = {0};
+};
+
+namespace {
+
+template <typename T>
+void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
+    const int N = s.N;
+    std::memset(&c, 0, sizeof c);
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            c.beta[a][b] = T(s.tab.beta[a * N + b]);
+            c.kappa[a][b] = T(s.tab.kappa[a * N + b]);
+        }
+    const int m2 = N * (N + 1) / 2;
+    for (int e = 0; e < N - 1; ++e)
+        for (int j = 0; j < m2; ++j) c.q2[e][j] = T(s.tab.q2[e * m2 + j]);
+    for (int a = 0; a < N; ++a) {
+        const double tau = p.tau[s.uidx[a]];
+        c.omp[a] = T(1.0 / tau);
+        c.omm[a] = p.lambda_trt < 0.0 ? T(1.0 / tau) : T(1.0 / (p.lambda_trt / (tau - 0.5) + 0.5));
+        c.uidx[a] = s.uidx[a];
+    }
+    c.m = T(p.m);
+    c.d34 = T(0.75 * p.D);
+    for (int d = 0; d < 3; ++d) c.fb[d] = T(p.body_force[d]);
+    const double sc = (s.prec == NFE_FP32_F16STORE) ? std::ldexp(1.0, p.scale_exp) : 1.0;
+    c.fscale = T(sc);
+    c.finv = T(1.0 / sc);
+    c.has_q4 = s.tab.omega != 0.0 ? 1 : 0;
+    c.nonconservative = (p.flags & NFE_NONCONSERVATIVE_FORCE) ? 1 : 0;
+    c.q4 = static_cast<const T *>(s.q4dev);
+}
+
+nfe_status free_all(nfe_sim *s) {
+    for (auto &g : s->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    for (auto &t : s->timed) { s->event_pool.push_back(t.a); s->event_pool.push_back(t.b); }
+    s->timed.clear();
+    for (auto e : s->event_pool) cudaEventDestroy(e);
+    s->event_pool.clear();
+    void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1], s->buf.v, s->buf.S,
+                    s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    std::memset(&s->buf, 0, sizeof s->buf);
+    s->q4dev = nullptr;
+    if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+    s->stream = nullptr;
+    return NFE_OK;
+}
+
+nfe_status dev_alloc(nfe_sim *s, void **p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return fail(NFE_ENOMEM, "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    s->device_bytes += bytes;
+    return NFE_OK;
+}
+
+cudaEvent_t get_event(nfe_sim *s) {
+    if (!s->event_pool.empty()) {
+        cudaEvent_t e = s->event_pool.back();
+        s->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// one time step from buffer `cur`, optionally with events around each kernel
+nfe_status launch_step(nfe_sim *s, int cur, bool timed) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
+    if (timed) { e0 = get_event(s); e1 = get_event(s); e2 = get_event(s); CK(cudaEventRecord(e0, s->stream)); }
+    CK(s->ops->collide(s->geom, s->coef, s->buf, cur, s->stream));
+    cudaEvent_t e1b = nullptr;
+    if (timed) {
+        // the second interval starts where the first ends, with its own event
+        e1b = get_event(s);
+        CK(cudaEventRecord(e1, s->stream));
+        CK(cudaEventRecord(e1b, s->stream));
+    }
+    CK(s->ops->ch_update(s->geom, s->coef, s->buf, cur, s->stream));
+    if (timed) {
+        CK(cudaEventRecord(e2, s->stream));
+        s->timed.push_back({K_COLLIDE, e0, e1});
+        s->timed.push_back({K_CH, e1b, e2});
+    }
+    return NFE_OK;
+}
+
+nfe_status ensure_graph(nfe_sim *s, int cur) {
+    if (s->graph[cur]) return NFE_OK;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
+    nfe_status st = launch_step(s, cur, false);
+    if (st == NFE_OK) st = launch_step(s, 1 - cur, false);
+    cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+    if (st != NFE_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&s->graph[cur], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) { s->graph[cur] = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+    return NFE_OK;
+}
+
+nfe_status ensure_fields(nfe_sim *s) {
+    if (s->buf.fields) return NFE_OK;
+    nfe_status st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.fields),
+                              s->fields_planes * size_t(s->geom.n) * sizeof(double));
+    if (st != NFE_OK) return st;
+    st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.partials),
+                   size_t(kReduceBlocks) * diag_count(s->N) * sizeof(double));
+    if (st != NFE_OK) return st;
+    return dev_alloc(s, reinterpret_cast<void **>(&s->buf.diag), diag_count(s->N) * sizeof(double));
+}
+
+nfe_status check_sim(const nfe_sim *s) {
+    if (!s) return fail(NFE_EINVAL, "sim is NULL");
+    return NFE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *nfe_status_string(nfe_status s) {
+    switch (s) {
+        case NFE_OK: return "ok";
+        case NFE_EINVAL: return "invalid argument";
+        case NFE_ENOMEM: return "out of memory";
+        case NFE_ECUDA: return "CUDA error";
+        case NFE_ESINGULAR: return "singular alpha/Lambda/Theta system";
+        case NFE_ENONFINITE: return "non-finite volume fraction";
+        case NFE_ETIMEOUT: return "device wait timed out";
+        case NFE_EUNSUPPORTED: return "unsupported combination";
+    }
+    return "unknown status";
+}
+
+const char *nfe_last_error(void) { return g_err.c_str(); }
+
+nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim **out) {
+    if (!out) return fail(NFE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !p) return fail(NFE_EINVAL, "grid or params is NULL");
+    if (grid->lattice != NFE_D2Q9 && grid->lattice != NFE_D3Q19) return fail(NFE_EINVAL, "lattice must be NFE_D2Q9 or NFE_D3Q19");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(NFE_EINVAL, "grid sizes must be >= 1");
+    if (grid->lattice == NFE_D2Q9 && (grid->nz != 1 || (grid->wall_mask & NFE_WALL_Z)))
+        return fail(NFE_EINVAL, "D2Q9 needs nz = 1 and no z walls");
+    if (grid->wall_mask & ~7u) return fail(NFE_EINVAL, "unknown wall bits");
+    const long long n = (long long)grid->nx * grid->ny * grid->nz;
+    if (n > (1LL << 31) - 4096) return fail(NFE_EINVAL, "grid has %lld sites; the limit is 2^31 - 4096", n);
+    if (N < 2 || N > NFE_MAX_N) return fail(NFE_EINVAL, "N = %d outside 2..%d", N, NFE_MAX_N);
+    if (!p->sigma || !p->tau) return fail(NFE_EINVAL, "sigma or tau is NULL");
+    double smax = 0.0;
+    for (int i = 0; i < N * N; ++i) smax = std::fmax(smax, std::fabs(p->sigma[i]));
+    for (int i = 0; i < N; ++i) {
+        if (p->sigma[i * N + i] != 0.0) return fail(NFE_EINVAL, "sigma[%d][%d] must be 0", i, i);
+        for (int j = 0; j < N; ++j) {
+            if (i == j) continue;
+            if (!(p->sigma[i * N + j] > 0.0) || !std::isfinite(p->sigma[i * N + j]))
+                return fail(NFE_EINVAL, "sigma[%d][%d] must be positive and finite", i, j);
+            if (std::fabs(p->sigma[i * N + j] - p->sigma[j * N + i]) > 1e-15 * smax)
+                return fail(NFE_EINVAL, "sigma is not symmetric at (%d, %d)", i, j);
+        }
+        if (!(p->tau[i] > 0.5) || !std::isfinite(p->tau[i])) return fail(NFE_EINVAL, "tau[%d] must be > 1/2", i);
+    }
+    if (!(p->D > 0.0) || !std::isfinite(p->D)) return fail(NFE_EINVAL, "D must be positive");
+    if (!(p->m >= 0.0) || !std::isfinite(p->m)) return fail(NFE_EINVAL, "m must be >= 0");
+    if (!std::isfinite(p->lambda_trt)) return fail(NFE_EINVAL, "lambda_trt must be finite");
+    if (!std::isnan(p->omega_stab) && !(p->omega_stab >= 0.0)) return fail(NFE_EINVAL, "omega_stab must be >= 0 or NaN");
+    for (int d = 0; d < 3; ++d) if (!std::isfinite(p->body_force[d])) return fail(NFE_EINVAL, "body force must be finite");
+    if (p->implicit_component < 0 || p->implicit_component >= N) return fail(NFE_EINVAL, "implicit_component out of range");
+    if (p->precision < NFE_FP64 || p->precision > NFE_FP32_BF16STORE) return fail(NFE_EINVAL, "unknown precision");
+    if (p->flags & ~(NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI)) return fail(NFE_EINVAL, "unknown flags");
+    if (p->flags & NFE_NO_PHI) return fail(NFE_EUNSUPPORTED, "NFE_NO_PHI is not implemented on the GPU");
+    if (p->precision == NFE_FP32_F16STORE && (p->scale_exp < -20 || p->scale_exp > 20))
+        return fail(NFE_EINVAL, "scale_exp outside -20..20");
+
+    nfe_sim *s = new (std::nothrow) nfe_sim();
+    if (!s) return fail(NFE_ENOMEM, "host allocation failed");
+    s->grid = *grid;
+    s->N = N;
+    s->prec = p->precision;
+    s->geom = Geom{grid->nx, grid->ny, grid->nz, (grid->wall_mask & NFE_WALL_X) ? 1 : 0,
+                   (grid->wall_mask & NFE_WALL_Y) ? 1 : 0, (grid->wall_mask & NFE_WALL_Z) ? 1 : 0, n};
+    int a = 0;
+    for (int c = 0; c < N; ++c) if (c != p->implicit_component) s->uidx[a++] = c;
+    s->uidx[N - 1] = p->implicit_component;
+
+    const double omega = std::isnan(p->omega_stab) ? (auto_omega(N, p->sigma) ? 1.0 / 90.0 : 0.0) : p->omega_stab;
+    std::string err;
+    nfe_status st = build_tables(N, p->sigma, s->uidx, p->D, omega, !(p->flags & NFE_NO_PHI), s->tab, err);
+    if (st != NFE_OK) { delete s; return fail(st, "%s", err.c_str()); }
+    s->ops = select_ops(grid->lattice, N, p->precision);
+    if (!s->ops) { delete s; return fail(NFE_EUNSUPPORTED, "no kernels for this lattice/N/precision"); }
+
+    if (p->cuda_stream) {
+        s->stream = static_cast<cudaStream_t>(p->cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreate(&s->stream);
+        if (e != cudaSuccess) { delete s; return cuda_fail(e, "cudaStreamCreate"); }
+        s->own_stream = true;
+    }
+    const int Q = s->ops->Q;
+    s->fplanes_bytes = size_t(Q - 1) * n * s->ops->f_elem_bytes;
+    s->cplanes_bytes = size_t(N - 1) * n * s->ops->c_elem_bytes;
+    s->fields_planes = size_t(std::max(N + 7, Q - 1));
+    const size_t ce = s->ops->c_elem_bytes;
+#define ALLOC(ptr, bytes) do { st = dev_alloc(s, reinterpret_cast<void **>(&(ptr)), (bytes)); \
+        if (st != NFE_OK) { free_all(s); delete s; return st; } } while (0)
+    ALLOC(s->buf.f[0], s->fplanes_bytes);
+    ALLOC(s->buf.f[1], s->fplanes_bytes);
+    ALLOC(s->buf.C[0], s->cplanes_bytes);
+    ALLOC(s->buf.C[1], s->cplanes_bytes);
+    ALLOC(s->buf.v, size_t(s->ops->D) * n * ce);
+    ALLOC(s->buf.S, size_t(N - 1) * n * ce);
+    ALLOC(s->buf.flag, sizeof(int));
+    if (!s->tab.q4.empty()) ALLOC(s->q4dev, s->tab.q4.size() * ce);
+#undef ALLOC
+    // upload q4 in the arithmetic type
+    if (s->q4dev) {
+        cudaError_t e;
+        if (s->prec == NFE_FP64) {
+            e = cudaMemcpy(s->q4dev, s->tab.q4.data(), s->tab.q4.size() * sizeof(double), cudaMemcpyHostToDevice);
+        } else {
+            std::vector<float> tmp(s->tab.q4.begin(), s->tab.q4.end());
+            e = cudaMemcpy(s->q4dev, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice);
+        }
+        if (e != cudaSuccess) { free_all(s); delete s; return cuda_fail(e, "upload q4"); }
+    }
+    if (s->prec == NFE_FP64) { fill_coef<double>(*s, *p, s->cd); s->coef = &s->cd; }
+    else { fill_coef<float>(*s, *p, s->cfl); s->coef = &s->cfl; }
+
+    cudaError_t e = cudaMemsetAsync(s->buf.f[0], 0, s->fplanes_bytes, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->buf.C[0], 0, s->cplanes_bytes, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) { free_all(s); delete s; return cuda_fail(e, "initialise state"); }
+    s->buf.cur = 0;
+    *out = s;
+    return NFE_OK;
+}
+
+void nfe_destroy(nfe_sim *s) {
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    free_all(s);
+    delete s;
+}
+
+nfe_status nfe_set_fields(nfe_sim *s, const double *C, const double *v) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (!C) return fail(NFE_EINVAL, "C is NULL");
+    if ((st = ensure_fields(s)) != NFE_OK) return st;
+    const size_t n = size_t(s->geom.n);
+    const int N = s->N;
+    // evolved components in internal order, FP64, into the fields scratch
+    for (int e = 0; e < N - 1; ++e)
+        CK(cudaMemcpyAsync(s->buf.fields + e * n, C + size_t(s->uidx[e]) * n, n * sizeof(double),
+                           cudaMemcpyHostToDevice, s->stream));
+    CK(s->ops->pack_C(s->geom, s->buf, 0, s->buf.fields, s->stream));
+    if (v) {
+        CK(cudaMemcpyAsync(s->buf.fields + (N - 1) * n, v, 3 * n * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        CK(s->ops->init_f(s->geom, s->coef, s->buf, 0, s->buf.fields + (N - 1) * n, s->stream));
+    } else {
+        CK(cudaMemsetAsync(s->buf.f[0], 0, s->fplanes_bytes, s->stream));
+    }
+    CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    s->buf.cur = 0;
+    s->step = 0;
+    return NFE_OK;
+}
+
+nfe_status nfe_step(nfe_sim *s, int64_t nsteps) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (nsteps < 0) return fail(NFE_EINVAL, "nsteps < 0");
+    if (s->profiling) {
+        for (int64_t i = 0; i < nsteps; ++i) {
+            if ((st = launch_step(s, s->buf.cur, true)) != NFE_OK) return st;
+            s->buf.cur ^= 1;
+            s->step++;
+        }
+        return NFE_OK;
+    }
+    while (nsteps >= 2) {
+        if ((st = ensure_graph(s, s->buf.cur)) != NFE_OK) return st;
+        CK(cudaGraphLaunch(s->graph[s->buf.cur], s->stream));
+        nsteps -= 2;
+        s->step += 2;
+    }
+    if (nsteps == 1) {
+        if ((st = launch_step(s, s->buf.cur, false)) != NFE_OK) return st;
+        s->buf.cur ^= 1;
+        s->step++;
+    }
+    return NFE_OK;
+}
+
+nfe_status nfe_sync(nfe_sim *s) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    CK(cudaStreamSynchronize(s->stream));
+    int flag = 0;
+    CK(cudaMemcpy(&flag, s->buf.flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(NFE_ENONFINITE, "a volume fraction became NaN or Inf");
+    return NFE_OK;
+}
+
+nfe_status nfe_fields(nfe_sim *s, double *C, double *v, double *P) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if ((st = ensure_fields(s)) != NFE_OK) return st;
+    CK(s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream));
+    const size_t n = size_t(s->geom.n);
+    const int N = s->N;
+    if (C) CK(cudaMemcpyAsync(C, s->buf.fields, N * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (v) CK(cudaMemcpyAsync(v, s->buf.fields + N * n, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (P) CK(cudaMemcpyAsync(P, s->buf.fields + (N + 3) * n, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_populations(nfe_sim *s, double *f) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (!f) return fail(NFE_EINVAL, "f is NULL");
+    if ((st = ensure_fields(s)) != NFE_OK) return st;
+    CK(s->ops->unpack_f(s->geom, s->coef, s->buf, s->buf.cur, s->buf.fields, s->stream));
+    CK(cudaMemcpyAsync(f, s->buf.fields, size_t(s->ops->Q - 1) * s->geom.n * sizeof(double),
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_diagnostics(nfe_sim *s, nfe_diag *out) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (!out) return fail(NFE_EINVAL, "out is NULL");
+    if ((st = ensure_fields(s)) != NFE_OK) return st;
+    const int N = s->N;
+    CK(s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream));
+    CK(s->ops->reduce(s->geom, s->buf, s->buf.cur, kReduceBlocks, s->stream));
+    std::vector<double> d(diag_count(N));
+    CK(cudaMemcpyAsync(d.data(), s->buf.diag, d.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    std::memset(out, 0, sizeof *out);
+    out->step = s->step;
+    out->N = N;
+    for (int i = 0; i < N; ++i) {
+        out->mass[i] = d[i];
+        out->max_abs_C[i] = d[N + 9 + i];
+        out->min_C[i] = d[2 * N + 9 + i];
+    }
+    for (int k = 0; k < 3; ++k) {
+        out->momentum[k] = d[N + k];
+        out->force_sum[k] = d[N + 3 + k];
+        out->force_abs_sum[k] = d[N + 6 + k];
+    }
+    out->max_speed = d[3 * N + 9];
+    out->nonfinite = d[3 * N + 10] != 0.0 ? 1 : 0;
+    for (int i = 0; i < N; ++i) if (!std::isfinite(out->mass[i])) out->nonfinite = 1;
+    return NFE_OK;
+}
+
+nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (!out) return fail(NFE_EINVAL, "out is NULL");
+    std::memset(out, 0, sizeof *out);
+    out->lattice = s->grid.lattice;
+    out->N = s->N;
+    out->precision = s->prec;
+    out->sites = s->geom.n;
+    out->omega_stab = s->tab.omega;
+    out->factor_residual = s->tab.residual;
+    out->kernels_per_step = 2;
+    out->min_bytes_per_site = 2.0 * ((s->ops->Q - 1) * s->ops->f_elem_bytes + (s->N - 1) * s->ops->c_elem_bytes);
+    out->state_bytes = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
+    out->device_bytes = s->device_bytes;
+    return NFE_OK;
+}
+
+nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
+    if (!host || bytes != need) return fail(NFE_EINVAL, "state buffer must be %zu bytes", need);
+    char *h = static_cast<char *>(host);
+    CK(cudaStreamSynchronize(s->stream));
+    std::memcpy(h, &s->step, sizeof(int64_t));
+    CK(cudaMemcpyAsync(h + sizeof(int64_t), s->buf.f[s->buf.cur], s->fplanes_bytes, cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaMemcpyAsync(h + sizeof(int64_t) + s->fplanes_bytes, s->buf.C[s->buf.cur], s->cplanes_bytes,
+                       cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_set_state(nfe_sim *s, const void *host, size_t bytes) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
+    if (!host || bytes != need) return fail(NFE_EINVAL, "state buffer must be %zu bytes", need);
+    const char *h = static_cast<const char *>(host);
+    CK(cudaStreamSynchronize(s->stream));
+    std::memcpy(&s->step, h, sizeof(int64_t));
+    CK(cudaMemcpyAsync(s->buf.f[s->buf.cur], h + sizeof(int64_t), s->fplanes_bytes, cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemcpyAsync(s->buf.C[s->buf.cur], h + sizeof(int64_t) + s->fplanes_bytes, s->cplanes_bytes,
+                       cudaMemcpyHostToDevice, s->stream));
+    CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_profile_enable(nfe_sim *s, int on) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    CK(cudaStreamSynchronize(s->stream));
+    for (auto &t : s->timed) { s->event_pool.push_back(t.a); s->event_pool.push_back(t.b); }
+    s->timed.clear();
+    for (int k = 0; k < K_NKINDS; ++k) { s->prof_launches[k] = 0; s->prof_ms[k] = 0.0; }
+    s->profiling = on != 0;
+    return NFE_OK;
+}
+
+nfe_status nfe_profile_read(nfe_sim *s, int max_kinds, int *kinds, const char **names,
+                            int64_t *launches, double *total_ms) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (!kinds) return fail(NFE_EINVAL, "kinds is NULL");
+    CK(cudaStreamSynchronize(s->stream));
+    for (auto &t : s->timed) {
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, t.a, t.b));
+        s->prof_launches[t.kind] += 1;
+        s->prof_ms[t.kind] += ms;
+        s->event_pool.push_back(t.a);
+        s->event_pool.push_back(t.b);
+    }
+    s->timed.clear();
+    int c = 0;
+    for (int k = 0; k < K_NKINDS && c < max_kinds; ++k) {
+        if (s->prof_launches[k] == 0) continue;
+        if (names) names[c] = kKernelNames[k];
+        if (launches) launches[c] = s->prof_launches[k];
+        if (total_ms) total_ms[c] = s->prof_ms[k];
+        ++c;
+    }
+    *kinds = c;
+    return NFE_OK;
+}
+
+nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double omega_stab,
+                                   int implicit_component, int npts, const double *Cpts, double *S) {
+    if (N < 2 || N > NFE_MAX_N) return fail(NFE_EINVAL, "N = %d outside 2..%d", N, NFE_MAX_N);
+    if (!sigma || !Cpts || !S || npts < 0) return fail(NFE_EINVAL, "NULL argument or npts < 0");
+    if (!(D > 0.0)) return fail(NFE_EINVAL, "D must be positive");
+    if (implicit_component < 0 || implicit_component >= N) return fail(NFE_EINVAL, "implicit_component out of range");
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j < N; ++j)
+            if ((i == j && sigma[i * N + j] != 0.0) || (i != j && !(sigma[i * N + j] > 0.0)) ||
+                sigma[i * N + j] != sigma[j * N + i])
+                return fail(NFE_EINVAL, "sigma must be symmetric, zero on the diagonal, positive elsewhere");
+    int uidx[NFE_MAX_N];
+    int a = 0;
+    for (int c = 0; c < N; ++c) if (c != implicit_component) uidx[a++] = c;
+    uidx[N - 1] = implicit_component;
+    const double omega = std::isnan(omega_stab) ? (auto_omega(N, sigma) ? 1.0 / 90.0 : 0.0) : omega_stab;
+    Tables tab;
+    std::string err;
+    nfe_status st = build_tables(N, sigma, uidx, D, omega, true, tab, err);
+    if (st != NFE_OK) return fail(st, "%s", err.c_str());
+    const int m2 = N * (N + 1) / 2, m4 = mono4_count(N);
+    for (int p = 0; p < npts; ++p) {
+        double c[NFE_MAX_N];
+        for (int k = 0; k < N; ++k) c[k] = Cpts[size_t(p) * N + uidx[k]];
+        double *out = S + size_t(p) * N;
+        out[implicit_component] = 0.0;
+        for (int e = 0; e < N - 1; ++e) {
+            double q = 0.0;
+            int idx = 0;
+            for (int i = 0; i < N; ++i)
+                for (int j = i; j < N; ++j) q += tab.q2[e * m2 + idx++] * c[i] * c[j];
+            if (!tab.q4.empty()) {
+                int jdx = 0;
+                for (int i = 0; i < N; ++i)
+                    for (int j = i; j < N; ++j)
+                        for (int k = j; k < N; ++k)
+                            for (int l = k; l < N; ++l) q += tab.q4[e * m4 + jdx++] * c[i] * c[j] * c[k] * c[l];
+            }
+            out[uidx[e]] = c[e] * q;
+        }
+    }
+    return NFE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Internal interface between the host side (nfe_host.cpp) and the kernels
+// (nfe_kernels.cuh, instantiated per lattice in nfe_d2q9.cu / nfe_d3q19.cu).
+// Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nfe.h"
+
+namespace nfe {
+
+constexpr int kMaxN = NFE_MAX_N;
+constexpr int kMaxMono2 = kMaxN * (kMaxN + 1) / 2;   // degree-2 monomials in 8 variables
+
+// Degree-4 monomials a <= b <= c <= d in N variables: C(N+3, 4).
+__host__ __device__ constexpr int mono4_count(int n) { return n * (n + 1) * (n + 2) * (n + 3) / 24; }
+
+// Grid geometry as the kernels see it.
+struct Geom {
+    int nx, ny, nz;
+    int wx, wy, wz;       // 1 = halfway walls on that axis
+    long long n;          // nx * ny * nz
+};
+
+// Per-simulation coefficients, passed to the kernels by value.  Components are
+// in the internal order: the evolved components first (in the user's order),
+// the implicit one last (slot N-1).
+template <typename T>
+struct Coef {
+    T beta[kMaxN][kMaxN];         // beta_ab = 6 sigma_ab / D (Sec. II)
+    T kappa[kMaxN][kMaxN];        // kappa_ab = 3 D sigma_ab / 4
+    T q2[kMaxN - 1][kMaxMono2];   // factored flux potential, degree-2 part, per evolved slot
+    T omp[kMaxN];                 // omega+ of each component (1 / tau_i)
+    T omm[kMaxN];                 // omega- of each component (Eq. 26, or omega+ for BGK)
+    int uidx[kMaxN];              // user index of each internal slot (argmax ties -> lowest)
+    T m;                          // g^eq coefficient m (Eq. 40)
+    T d34;                        // 3 D / 4
+    T fb[3];                      // body force
+    T fscale;                     // FP16 storage scale 2^scale_exp (1 otherwise)
+    T finv;                       // 1 / fscale
+    int has_q4;                   // Omega != 0: degree-4 part present
+    int nonconservative;          // force of Eq. 31 instead of Eq. 34
+    const T *q4;                  // (N-1) x mono4_count(N), device memory, or nullptr
+};
+
+// One kernel kind for profiling.
+enum KernelKind { K_COLLIDE = 0, K_CH = 1, K_FUSED = 2, K_MOMENTS = 3, K_REDUCE = 4, K_NKINDS = 5 };
+extern const char *kKernelNames[K_NKINDS];
+
+// Device buffers of one simulation.
+struct Buffers {
+    void *f[2];           // populations k = 1..Q-1, planar, storage type
+    void *C[2];           // evolved volume fractions, planar, compute type
+    void *v;              // scratch: velocity (D planes), compute type
+    void *S;              // scratch: flux potential (N-1 planes), compute type
+    double *fields;       // moments output: C (N), v (3), P, Fs (3) planes, FP64
+    double *partials;     // reduction partials
+    double *diag;         // reduction result
+    int *flag;            // non-finite flag
+    int cur;              // index of the buffer holding the current state
+};
+
+// Launchers exported by the lattice translation units.  Each returns
+// cudaSuccess or the launch error.
+struct Ops {
+    int Q, D, N, prec;
+    // one time step: state in buffers cur -> 1 - cur (does not flip cur);
+    // `kind` receives the kernel kinds launched (for profiling), in order.
+    cudaError_t (*collide)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
+    cudaError_t (*ch_update)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
+    // fields (C, v, P, Fs in FP64) of the state in buffer cur
+    cudaError_t (*moments)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
+    // FP64 reductions of bufs.fields (+ f and C finiteness) into bufs.diag
+    cudaError_t (*reduce)(const Geom &, const Buffers &, int cur, int nblocks, cudaStream_t);
+    // f = f^eq(P = 0, v) from an FP64 device velocity array (3 x n)
+    cudaError_t (*init_f)(const Geom &, const void *coef, const Buffers &, int cur, const double *v, cudaStream_t);
+    // populations of buffer cur to FP64 ((Q-1) x n, device)
+    cudaError_t (*unpack_f)(const Geom &, const void *coef, const Buffers &, int cur, double *out, cudaStream_t);
+    // evolved C from FP64 device array ((N-1) x n) into buffer cur
+    cudaError_t (*pack_C)(const Geom &, const Buffers &, int cur, const double *in, cudaStream_t);
+    int f_elem_bytes;     // bytes per stored population
+    int c_elem_bytes;     // bytes per stored volume fraction (and per scratch value)
+};
+
+// One translation unit per lattice and precision (compiled in parallel).
+const Ops *ops_d2q9_fp64(int N);
+const Ops *ops_d2q9_fp32(int N);
+const Ops *ops_d2q9_f16(int N);
+const Ops *ops_d2q9_bf16(int N);
+const Ops *ops_d3q19_fp64(int N);
+const Ops *ops_d3q19_fp32(int N);
+const Ops *ops_d3q19_f16(int N);
+const Ops *ops_d3q19_bf16(int N);
+
+// Number of values one reduction block writes (and the diag layout):
+//  [0, N) mass, [N, N+3) momentum, [N+3, N+6) force sum, [N+6, N+9) |force| sum,
+//  [N+9, 2N+9) max |C|, [2N+9, 3N+9) min C, 3N+9 max speed, 3N+10 nonfinite.
+__host__ __device__ constexpr int diag_count(int N) { return 3 * N + 11; }
+constexpr int kReduceBlocks = 1024;
+
+}  // namespace nfe

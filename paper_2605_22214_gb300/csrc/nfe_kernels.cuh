@@ -1,0 +1,553 @@
+// Device code of the N-component free-energy LBM time step (arXiv 2605.22214).
+//
+// One time step is two kernels on planar (SoA) arrays, one thread per site:
+//   k_collide : C on the 1-ring -> isotropic grad / Laplacian of every C_i
+//               (Eqs. 35-36), E_B (Eq. 5) and grad E_B, the factored flux
+//               potential S_i = C_i q_i(C) + (3D/4) lap C_i (Eq. 12), the force
+//               F = grad E_B + sum_{a != b} kappa_ab lap C_b grad C_a + F_b
+//               (Eq. 34); f_k(x) -> v, P (Eqs. 37-38); TRT collision with the
+//               forcing split (Eqs. 23-30); push-streaming with halfway
+//               bounce-back (Eqs. 44-45).  Writes v and S for the second kernel.
+//   k_ch      : C_i(x, t+1) = sum_k g^eq_{i,k}(x - e_k, t), the Cahn-Hilliard LBE
+//               of Eq. 39 with tau_g = 1 (so the post-collision g is g^eq and no
+//               g population needs storing), bounce-back for sources in a wall.
+// Both kernels are templated on the lattice, on N and on the arithmetic type;
+// k_collide also on the storage type of f.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "nfe_internal.h"
+
+namespace nfe {
+
+// ----------------------------------------------------------------------------
+// Lattices.  D2Q9 in the order of Eqs. 20-21; D3Q19 in the standard set
+// (axis pairs, then the xy, xz and yz diagonals).  In both, the opposite of
+// an odd k is k + 1.
+// ----------------------------------------------------------------------------
+struct LD2Q9 {
+    static constexpr int Q = 9, D = 2;
+    __host__ __device__ static constexpr int ex(int k) {
+        return k == 1 || k == 5 || k == 7 ? 1 : (k == 2 || k == 6 || k == 8 ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ey(int k) {
+        return k == 3 || k == 5 || k == 8 ? 1 : (k == 4 || k == 6 || k == 7 ? -1 : 0);
+    }
+    __host__ __device__ static constexpr int ez(int) { return 0; }
+    __host__ __device__ static constexpr double w(int k) { return k == 0 ? 4.0 / 9.0 : (k < 5 ? 1.0 / 9.0 : 1.0 / 36.0); }
+};
+
+struct LD3Q19 {
+    static constexpr int Q = 19, D = 3;
+    // velocity k as (ex, ey, ez)
+    __host__ __device__ static constexpr int ex(int k) {
+        return (k == 1 || k == 7 || k == 9 || k == 11 || k == 13) ? 1
+             : (k == 2 || k == 8 || k == 10 || k == 12 || k == 14) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int ey(int k) {
+        return (k == 3 || k == 7 || k == 10 || k == 15 || k == 17) ? 1
+             : (k == 4 || k == 8 || k == 9 || k == 16 || k == 18) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr int ez(int k) {
+        return (k == 5 || k == 11 || k == 14 || k == 15 || k == 18) ? 1
+             : (k == 6 || k == 12 || k == 13 || k == 16 || k == 17) ? -1 : 0;
+    }
+    __host__ __device__ static constexpr double w(int k) { return k == 0 ? 1.0 / 3.0 : (k < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+};
+
+__host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// ----------------------------------------------------------------------------
+// Storage of f.  FP16 keeps f_k / w_k * 2^scale_exp, BF16 keeps f_k / w_k:
+// in the pressure-based scheme f_k ~ w_k (3P + 3 e.v + ...) is already a
+// deviation from rest, so dividing by w_k brings every direction to one scale.
+// ----------------------------------------------------------------------------
+template <typename S, typename T> struct FStore;
+template <typename T> struct FStore<double, T> {
+    __device__ static T load(const double *p, double, T) { return T(*p); }
+    __device__ static void store(double *p, T v, double, T) { *p = double(v); }
+};
+template <typename T> struct FStore<float, T> {
+    __device__ static T load(const float *p, double, T) { return T(*p); }
+    __device__ static void store(float *p, T v, double, T) { *p = float(v); }
+};
+template <> struct FStore<__half, float> {
+    __device__ static float load(const __half *p, double w, float finv) { return __half2float(*p) * (float(w) * finv); }
+    __device__ static void store(__half *p, float v, double w, float finv) { *p = __float2half_rn(v * (float(1.0 / w) / finv)); }
+};
+template <> struct FStore<__nv_bfloat16, float> {
+    __device__ static float load(const __nv_bfloat16 *p, double w, float) { return __bfloat162float(*p) * float(w); }
+    __device__ static void store(__nv_bfloat16 *p, float v, double w, float) { *p = __float2bfloat16_rn(v * float(1.0 / w)); }
+};
+
+// ----------------------------------------------------------------------------
+// Site helpers
+// ----------------------------------------------------------------------------
+
+// Index of x + e_k, or -1 when x + e_k lies beyond a wall.
+template <class L>
+__device__ __forceinline__ int neighbour(const Geom &g, int x, int y, int z, int k) {
+    int xx = x + L::ex(k), yy = y + L::ey(k), zz = z + L::ez(k);
+    if (L::ex(k) != 0) {
+        if (xx < 0) { if (g.wx) return -1; xx += g.nx; }
+        else if (xx >= g.nx) { if (g.wx) return -1; xx -= g.nx; }
+    }
+    if (L::ey(k) != 0) {
+        if (yy < 0) { if (g.wy) return -1; yy += g.ny; }
+        else if (yy >= g.ny) { if (g.wy) return -1; yy -= g.ny; }
+    }
+    if (L::ez(k) != 0) {
+        if (zz < 0) { if (g.wz) return -1; zz += g.nz; }
+        else if (zz >= g.nz) { if (g.wz) return -1; zz -= g.nz; }
+    }
+    return xx + g.nx * (yy + g.ny * zz);
+}
+
+template <int N, typename T>
+__device__ __forceinline__ T bulk_energy(const T (&c)[N], const Coef<T> &cf) {
+    // E_B = sum_{a<b} beta_ab [f(C_a) + f(C_b) - f(C_a + C_b)], f(C) = C^2 (1 - C)^2 (Eq. 5)
+    T fw[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) { T u = c[a] * (T(1) - c[a]); fw[a] = u * u; }
+    T E = T(0);
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = a + 1; b < N; ++b) {
+            T t = c[a] + c[b];
+            T u = t * (T(1) - t);
+            E += cf.beta[a][b] * (fw[a] + fw[b] - u * u);
+        }
+    return E;
+}
+
+template <int N, typename T>
+__device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T (&q)[N - 1]) {
+    // q_e(C): degree-2 monomials C_a C_b (a <= b) in nested-loop order, and the
+    // degree-4 monomials a <= b <= c <= d of the stabiliser part when Omega != 0.
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) q[e] = T(0);
+    int idx = 0;
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+        for (int b = a; b < N; ++b) {
+            T p = c[a] * c[b];
+#pragma unroll
+            for (int e = 0; e < N - 1; ++e) q[e] += cf.q2[e][idx] * p;
+            ++idx;
+        }
+    if (cf.has_q4) {
+        constexpr int M4 = mono4_count(N);
+        int j = 0;
+#pragma unroll
+        for (int a = 0; a < N; ++a)
+#pragma unroll
+            for (int b = a; b < N; ++b) {
+                T pab = c[a] * c[b];
+#pragma unroll
+                for (int d0 = b; d0 < N; ++d0) {
+                    T pabc = pab * c[d0];
+#pragma unroll
+                    for (int d1 = d0; d1 < N; ++d1) {
+                        T p = pabc * c[d1];
+#pragma unroll
+                        for (int e = 0; e < N - 1; ++e) q[e] += __ldg(cf.q4 + e * M4 + j) * p;
+                        ++j;
+                    }
+                }
+            }
+    }
+}
+
+// Stencil pass at one site: all N volume fractions at x, their grad and
+// Laplacian (Eqs. 35-36) with the wall rule (a neighbour inside a wall takes
+// the value at x, Sec. III C), grad E_B, and the neighbour indices.
+template <class L, int N, typename T>
+struct Stencil {
+    T c[N];
+    T lap[N];
+    T gr[N][3];
+    T gE[3];
+    int nb[L::Q];
+};
+
+template <class L, int N, typename T>
+__device__ __forceinline__ void stencil(const Geom &g, const Coef<T> &cf, const T *__restrict__ C,
+                                        int s, int x, int y, int z, Stencil<L, N, T> &st) {
+    const size_t n = size_t(g.n);
+    T rest = T(0);
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) { st.c[a] = C[a * n + s]; rest += st.c[a]; }
+    st.c[N - 1] = T(1) - rest;
+    const T E0 = bulk_energy<N, T>(st.c, cf);
+#pragma unroll
+    for (int a = 0; a < N; ++a) { st.lap[a] = T(0); st.gr[a][0] = st.gr[a][1] = st.gr[a][2] = T(0); }
+    st.gE[0] = st.gE[1] = st.gE[2] = T(0);
+    st.nb[0] = s;
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k) {
+        const int j = neighbour<L>(g, x, y, z, k);
+        st.nb[k] = j;
+        if (j < 0) continue;               // wall: psi(x + e_k) := psi(x), difference 0
+        T cn[N];
+        T r2 = T(0);
+#pragma unroll
+        for (int a = 0; a < N - 1; ++a) { cn[a] = C[a * n + j]; r2 += cn[a]; }
+        cn[N - 1] = T(1) - r2;
+        const T wk = T(L::w(k));
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const T d = cn[a] - st.c[a];
+            st.lap[a] += wk * d;
+            if (L::ex(k)) st.gr[a][0] += (L::ex(k) > 0 ? wk : -wk) * d;
+            if (L::ey(k)) st.gr[a][1] += (L::ey(k) > 0 ? wk : -wk) * d;
+            if (L::ez(k)) st.gr[a][2] += (L::ez(k) > 0 ? wk : -wk) * d;
+        }
+        const T dE = bulk_energy<N, T>(cn, cf) - E0;
+        if (L::ex(k)) st.gE[0] += (L::ex(k) > 0 ? wk : -wk) * dE;
+        if (L::ey(k)) st.gE[1] += (L::ey(k) > 0 ? wk : -wk) * dE;
+        if (L::ez(k)) st.gE[2] += (L::ez(k) > 0 ? wk : -wk) * dE;
+    }
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        st.lap[a] *= T(6);                 // 2 / c_s^2
+        st.gr[a][0] *= T(3); st.gr[a][1] *= T(3); st.gr[a][2] *= T(3);   // 1 / c_s^2
+    }
+    st.gE[0] *= T(3); st.gE[1] *= T(3); st.gE[2] *= T(3);
+}
+
+// F_s (Eq. 34, or Eq. 31 when cf.nonconservative) and the flux potential S.
+template <class L, int N, typename T>
+__device__ __forceinline__ void force_and_potential(const Coef<T> &cf, const Stencil<L, N, T> &st,
+                                                    T (&Fs)[3], T (&S)[N - 1]) {
+    if (!cf.nonconservative) {
+        Fs[0] = st.gE[0]; Fs[1] = st.gE[1]; Fs[2] = st.gE[2];
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            T h = T(0);
+#pragma unroll
+            for (int b = 0; b < N; ++b) if (b != a) h += cf.kappa[a][b] * st.lap[b];
+            Fs[0] += h * st.gr[a][0]; Fs[1] += h * st.gr[a][1]; Fs[2] += h * st.gr[a][2];
+        }
+    } else {
+        // mu_a = sum_{b != a} beta_ab (f'(C_a) - f'(C_a + C_b)) + kappa_ab lap C_b (Eq. 7)
+        Fs[0] = Fs[1] = Fs[2] = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const T ca = st.c[a];
+            const T fpa = T(2) * ca * (T(1) - T(3) * ca + T(2) * ca * ca);
+            T mu = T(0);
+#pragma unroll
+            for (int b = 0; b < N; ++b) if (b != a) {
+                const T t = ca + st.c[b];
+                const T fpt = T(2) * t * (T(1) - T(3) * t + T(2) * t * t);
+                mu += cf.beta[a][b] * (fpa - fpt) + cf.kappa[a][b] * st.lap[b];
+            }
+            Fs[0] += mu * st.gr[a][0]; Fs[1] += mu * st.gr[a][1]; Fs[2] += mu * st.gr[a][2];
+        }
+    }
+    T q[N - 1];
+    flux_poly<N, T>(st.c, cf, q);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) S[e] = st.c[e] * q[e] + cf.d34 * st.lap[e];
+}
+
+// omega+ / omega- of the component with the largest C (Eq. 42); ties go to the
+// lowest user index.
+template <int N, typename T>
+__device__ __forceinline__ void relaxation(const Coef<T> &cf, const T (&c)[N], T &op, T &om) {
+    T best = c[0];
+    int bu = cf.uidx[0];
+    op = cf.omp[0]; om = cf.omm[0];
+#pragma unroll
+    for (int a = 1; a < N; ++a) {
+        if (c[a] > best || (c[a] == best && cf.uidx[a] < bu)) {
+            best = c[a]; bu = cf.uidx[a]; op = cf.omp[a]; om = cf.omm[a];
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Kernels
+// ----------------------------------------------------------------------------
+
+template <class L, int N, typename T, typename SF>
+__global__ void __launch_bounds__(256)
+k_collide(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
+          const T *__restrict__ C, T *__restrict__ vout, T *__restrict__ Sout) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const int x = s % g.nx;
+    const int r = s / g.nx;
+    const int y = r % g.ny;
+    const int z = r / g.ny;
+    const size_t n = size_t(g.n);
+
+    Stencil<L, N, T> st;
+    stencil<L, N, T>(g, cf, C, s, x, y, z, st);
+    T Fs[3], S[N - 1];
+    force_and_potential<L, N, T>(cf, st, Fs, S);
+    const T F0 = Fs[0] + cf.fb[0], F1 = Fs[1] + cf.fb[1], F2 = Fs[2] + cf.fb[2];
+
+    T f[L::Q];
+    T sumf = T(0), j0 = T(0), j1 = T(0), j2 = T(0);
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k) {
+        f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, L::w(k), cf.finv);
+        sumf += f[k];
+        if (L::ex(k)) j0 += L::ex(k) > 0 ? f[k] : -f[k];
+        if (L::ey(k)) j1 += L::ey(k) > 0 ? f[k] : -f[k];
+        if (L::ez(k)) j2 += L::ez(k) > 0 ? f[k] : -f[k];
+    }
+    // Eq. 37 with rho = 1, and Eq. 38 with s_0(v) = -w_0 v.v / (2 c_s^2)
+    const T v0 = j0 + T(0.5) * F0, v1 = j1 + T(0.5) * F1, v2 = j2 + T(0.5) * F2;
+    const T vv = v0 * v0 + v1 * v1 + v2 * v2;
+    const T w0 = T(L::w(0));
+    const T P = (sumf - T(1.5) * w0 * vv) / (T(3) * (T(1) - w0));
+    const T vF = v0 * F0 + v1 * F1 + v2 * F2;
+    T op, om;
+    relaxation<N, T>(cf, st.c, op, om);
+    const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
+
+#pragma unroll
+    for (int k = 1; k < L::Q; k += 2) {
+        const int kb = k + 1;
+        const T wk = T(L::w(k));
+        const T eu = T(L::ex(k)) * v0 + T(L::ey(k)) * v1 + T(L::ez(k)) * v2;
+        const T eF = T(L::ex(k)) * F0 + T(L::ey(k)) * F1 + T(L::ez(k)) * F2;
+        // symmetric / antisymmetric parts of f^eq (Eq. 27) and of F_k (Eq. 30)
+        const T eqp = wk * (T(3) * P + T(4.5) * eu * eu - T(1.5) * vv);
+        const T eqm = wk * (T(3) * eu);
+        const T Fp = wk * (T(9) * eu * eF - T(3) * vF);
+        const T Fm = wk * (T(3) * eF);
+        const T fp = T(0.5) * (f[k] + f[kb]);
+        const T fm = T(0.5) * (f[k] - f[kb]);
+        const T sym = -op * (fp - eqp) + ap * Fp;
+        const T anti = -om * (fm - eqm) + am * Fm;
+        const T pk = f[k] + sym + anti;      // post-collision f_k
+        const T pkb = f[kb] + sym - anti;    // post-collision f_kbar
+        // push: f_k(x + e_k, t+1) = pk, or bounce-back into f_kbar(x) at a wall (Eq. 44)
+        const int jk = st.nb[k], jkb = st.nb[kb];
+        if (jk >= 0) FStore<SF, T>::store(fout + (k - 1) * n + jk, pk, L::w(k), cf.finv);
+        else         FStore<SF, T>::store(fout + (kb - 1) * n + s, pk, L::w(kb), cf.finv);
+        if (jkb >= 0) FStore<SF, T>::store(fout + (kb - 1) * n + jkb, pkb, L::w(kb), cf.finv);
+        else          FStore<SF, T>::store(fout + (k - 1) * n + s, pkb, L::w(k), cf.finv);
+    }
+    vout[s] = v0;
+    vout[n + s] = v1;
+    if (L::D == 3) vout[2 * n + s] = v2;
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) Sout[e * n + s] = S[e];
+}
+
+template <class L, int N, typename T>
+__global__ void __launch_bounds__(256)
+k_ch(Geom g, Coef<T> cf, const T *__restrict__ C, const T *__restrict__ V, const T *__restrict__ S,
+     T *__restrict__ Cout, int *__restrict__ flag) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const int x = s % g.nx;
+    const int r = s / g.nx;
+    const int y = r % g.ny;
+    const int z = r / g.ny;
+    const size_t n = size_t(g.n);
+    const T m = cf.m;
+
+    T c0[N - 1], S0[N - 1], acc[N - 1];
+    const T u0 = V[s], u1 = V[n + s], u2 = (L::D == 3) ? V[2 * n + s] : T(0);
+    const T uu = u0 * u0 + u1 * u1 + u2 * u2;
+    const T w0 = T(L::w(0));
+    const T s0 = -T(1.5) * w0 * uu;
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) {
+        c0[e] = C[e * n + s];
+        S0[e] = S[e * n + s];
+        // g^eq_{e,0}(x) = C (1 + s_0(v)) + (1 - w_0) m S (Eq. 40)
+        acc[e] = c0[e] * (T(1) + s0) + (T(1) - w0) * m * S0[e];
+    }
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k) {
+        const T wk = T(L::w(k));
+        const int j = neighbour<L>(g, x, y, z, opp(k));      // source x - e_k
+        if (j >= 0) {
+            const T a0 = V[j], a1 = V[n + j], a2 = (L::D == 3) ? V[2 * n + j] : T(0);
+            const T eu = T(L::ex(k)) * a0 + T(L::ey(k)) * a1 + T(L::ez(k)) * a2;
+            const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (a0 * a0 + a1 * a1 + a2 * a2));
+#pragma unroll
+            for (int e = 0; e < N - 1; ++e) acc[e] += C[e * n + j] * sk - wk * m * S[e * n + j];
+        } else {
+            // bounce-back: g_k(x, t+1) = g*_kbar(x, t) = g^eq_kbar(x, t)
+            const T eu = -(T(L::ex(k)) * u0 + T(L::ey(k)) * u1 + T(L::ez(k)) * u2);
+            const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+#pragma unroll
+            for (int e = 0; e < N - 1; ++e) acc[e] += c0[e] * sk - wk * m * S0[e];
+        }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) {
+        Cout[e * n + s] = acc[e];
+        bad |= !isfinite(acc[e]);
+    }
+    if (bad) atomicOr(flag, 1);
+}
+
+// Fields of the current state in FP64: C (N planes, user order), v (3), P, F_s (3).
+template <class L, int N, typename T, typename SF>
+__global__ void __launch_bounds__(256)
+k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ C,
+          double *__restrict__ out, int *__restrict__ flag) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const int x = s % g.nx;
+    const int r = s / g.nx;
+    const int y = r % g.ny;
+    const int z = r / g.ny;
+    const size_t n = size_t(g.n);
+    Stencil<L, N, T> st;
+    stencil<L, N, T>(g, cf, C, s, x, y, z, st);
+    T Fs[3], S[N - 1];
+    force_and_potential<L, N, T>(cf, st, Fs, S);
+    T sumf = T(0), j0 = T(0), j1 = T(0), j2 = T(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k) {
+        const T fk = FStore<SF, T>::load(fin + (k - 1) * n + s, L::w(k), cf.finv);
+        bad |= !isfinite(fk);
+        sumf += fk;
+        if (L::ex(k)) j0 += L::ex(k) > 0 ? fk : -fk;
+        if (L::ey(k)) j1 += L::ey(k) > 0 ? fk : -fk;
+        if (L::ez(k)) j2 += L::ez(k) > 0 ? fk : -fk;
+    }
+    const T v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0]);
+    const T v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1]);
+    const T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2]);
+    const T w0 = T(L::w(0));
+    const T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) / (T(3) * (T(1) - w0));
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        out[size_t(cf.uidx[a]) * n + s] = double(st.c[a]);
+        bad |= !isfinite(st.c[a]);
+    }
+    out[(N + 0) * n + s] = double(v0);
+    out[(N + 1) * n + s] = double(v1);
+    out[(N + 2) * n + s] = double(v2);
+    out[(N + 3) * n + s] = double(P);
+    out[(N + 4) * n + s] = double(Fs[0]);
+    out[(N + 5) * n + s] = double(Fs[1]);
+    out[(N + 6) * n + s] = double(Fs[2]);
+    if (bad) atomicOr(flag, 1);
+}
+
+// f = f^eq(P = 0, v): f_k = s_k(v) for k >= 1 (Eqs. 27-28).
+template <class L, typename T, typename SF>
+__global__ void k_init_f(Geom g, Coef<T> cf, const double *__restrict__ v, SF *__restrict__ f) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const size_t n = size_t(g.n);
+    const double a0 = v[s], a1 = v[n + s], a2 = v[2 * n + s];
+    const double uu = a0 * a0 + a1 * a1 + a2 * a2;
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k) {
+        const double eu = L::ex(k) * a0 + L::ey(k) * a1 + L::ez(k) * a2;
+        const double sk = L::w(k) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
+        FStore<SF, T>::store(f + (k - 1) * n + s, T(sk), L::w(k), cf.finv);
+    }
+}
+
+template <class L, typename T, typename SF>
+__global__ void k_unpack_f(Geom g, Coef<T> cf, const SF *__restrict__ f, double *__restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const size_t n = size_t(g.n);
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k)
+        out[(k - 1) * n + s] = double(FStore<SF, T>::load(f + (k - 1) * n + s, L::w(k), cf.finv));
+}
+
+template <typename T>
+__global__ void k_pack_C(long long total, const double *__restrict__ in, T *__restrict__ out) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < total) out[i] = T(in[i]);
+}
+
+// FP64 reductions.  Block partials of diag_count(N) values, then one block
+// combines them.  Layout as in nfe_internal.h.
+__global__ void k_reduce_partial(long long n, int N, const double *__restrict__ fields,
+                                 double *__restrict__ partials);
+__global__ void k_reduce_final(int nblocks, int N, const double *__restrict__ partials,
+                               const int *__restrict__ flag, double *__restrict__ diag);
+
+// ----------------------------------------------------------------------------
+// Launchers
+// ----------------------------------------------------------------------------
+
+inline unsigned blocks_for(long long n, int bs) { return unsigned((n + bs - 1) / bs); }
+
+template <class L, int N, typename T, typename SF>
+struct Launch {
+    static cudaError_t collide(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_collide<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
+            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
+            static_cast<const T *>(b.C[cur]), static_cast<T *>(b.v), static_cast<T *>(b.S));
+        return cudaGetLastError();
+    }
+    static cudaError_t ch_update(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_ch<L, N, T><<<blocks_for(g.n, 256), 256, 0, st>>>(
+            g, cf, static_cast<const T *>(b.C[cur]), static_cast<const T *>(b.v),
+            static_cast<const T *>(b.S), static_cast<T *>(b.C[1 - cur]), b.flag);
+        return cudaGetLastError();
+    }
+    static cudaError_t moments(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
+            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag);
+        return cudaGetLastError();
+    }
+    static cudaError_t reduce(const Geom &g, const Buffers &b, int, int nblocks, cudaStream_t st) {
+        k_reduce_partial<<<nblocks, 256, 0, st>>>(g.n, N, b.fields, b.partials);
+        k_reduce_final<<<1, 256, 0, st>>>(nblocks, N, b.partials, b.flag, b.diag);
+        return cudaGetLastError();
+    }
+    static cudaError_t init_f(const Geom &g, const void *coef, const Buffers &b, int cur, const double *v, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_init_f<L, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(g, cf, v, static_cast<SF *>(b.f[cur]));
+        return cudaGetLastError();
+    }
+    static cudaError_t unpack_f(const Geom &g, const void *coef, const Buffers &b, int cur, double *out, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_unpack_f<L, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(g, cf, static_cast<const SF *>(b.f[cur]), out);
+        return cudaGetLastError();
+    }
+    static cudaError_t pack_C(const Geom &g, const Buffers &b, int cur, const double *in, cudaStream_t st) {
+        const long long total = g.n * (N - 1);
+        k_pack_C<T><<<blocks_for(total, 256), 256, 0, st>>>(total, in, static_cast<T *>(b.C[cur]));
+        return cudaGetLastError();
+    }
+    static const Ops *ops(int prec) {
+        static const Ops o = {L::Q, L::D, N, prec, &collide, &ch_update, &moments, &reduce,
+                              &init_f, &unpack_f, &pack_C, int(sizeof(SF)), int(sizeof(T))};
+        return &o;
+    }
+};
+
+template <class L, typename T, typename SF>
+const Ops *ops_for_n(int N, int prec) {
+    switch (N) {
+        case 2: return Launch<L, 2, T, SF>::ops(prec);
+        case 3: return Launch<L, 3, T, SF>::ops(prec);
+        case 4: return Launch<L, 4, T, SF>::ops(prec);
+        case 5: return Launch<L, 5, T, SF>::ops(prec);
+        case 6: return Launch<L, 6, T, SF>::ops(prec);
+        case 7: return Launch<L, 7, T, SF>::ops(prec);
+        case 8: return Launch<L, 8, T, SF>::ops(prec);
+        default: return nullptr;
+    }
+}
+
+}  // namespace nfe

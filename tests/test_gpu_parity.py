@@ -1,0 +1,203 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: FP64 volume fractions 1e-12 relative after 100 steps, FP32 1e-5;
+populations, velocity and pressure are small derived signals (their largest
+value can be 1e-6 while C is O(1)), so they are compared relative to their own
+largest value with 1e-10 (FP64) and 1e-3 (FP32).  An absent evolved component
+must be exactly 0.0.
+"""
+import numpy as np
+import pytest
+
+import nfe_workloads as W
+import paper_2605_22214_gb300 as nfe
+from oracle import lbm, observables
+
+from ._lib import lib, rel
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": dict(C=1e-12, f=1e-10), "fp32": dict(C=1e-5, f=1e-3)}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lib()
+
+
+def oracle_run(p, steps):
+    prm = lbm.Params(p)
+    st = lbm.init_state(prm, p["C0"], flux_form="factored")
+    st = lbm.run(prm, st, steps, flux_form="factored")
+    C, v, P, _ = lbm.fields(prm, st, flux_form="factored")
+    return dict(C=C, v=v, P=P, f=st.f[1:])
+
+
+def gpu_run(p, steps, precision="fp64", **kw):
+    with nfe.Sim(p, precision, **kw) as s:
+        s.set_fields(p["C0"])
+        s.step(steps)
+        s.sync()
+        C, v, P = s.fields()
+        f = s.populations()
+    return dict(C=C, v=v, P=P, f=f)
+
+
+def compare(p, steps, precision):
+    o = oracle_run(p, steps)
+    g = gpu_run(p, steps, precision)
+    tol = TOL[precision]
+    errs = {k: rel(g[k], o[k]) for k in ("C", "f", "v", "P")}
+    assert errs["C"] <= tol["C"], errs
+    for k in ("f", "v", "P"):
+        assert errs[k] <= tol["f"], errs
+    return o, g, errs
+
+
+def _mixture(nx, ny, N, seed, walls=(False, False, False), taus=None, lam=-1.0, fb=(0, 0, 0), omega=float("nan")):
+    rng = np.random.default_rng(seed)
+    sig = W.random_sigma(rng, N)
+    C = 1.0 / N + rng.uniform(-0.05, 0.05, size=(N, 1, ny, nx))
+    C /= C.sum(axis=0, keepdims=True)
+    p = W.base_params(9, nx, ny, 1, N, sig, taus if taus is not None else 1.0, walls=walls, lambda_trt=lam,
+                      m=0.05, body_force=fb, omega_stab=omega)
+    p["C0"] = C
+    return p
+
+
+CASES = {
+    "lens_walls_N3": lambda: W.lens_2d(nx=40, ny=36, radius=8),
+    "spinodal_N4": lambda: W.spinodal_2d(nx=48, ny=40),
+    "janus_N4": lambda: W.janus_2d(nx=48, ny=40, radius=9, offset=11),
+    "mixture_N5_trt_omega_wallsx": lambda: _mixture(36, 30, 5, 11, walls=(True, False, False),
+                                                    taus=[0.6, 0.8, 1.0, 0.7, 1.3], lam=3 / 16,
+                                                    fb=(1e-6, -2e-6, 0), omega=1 / 90),
+    "mixture_N8": lambda: _mixture(20, 18, 8, 12),
+    "janus3d_N4": lambda: W.janus_3d(n=16, radius=4),
+    "poiseuille3d_N7": lambda: W.layered_poiseuille(nx=6, ny=5, nz=24),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_fp64_parity_100_steps(case):
+    compare(CASES[case](), 100, "fp64")
+
+
+@pytest.mark.parametrize("case", ["lens_walls_N3", "spinodal_N4", "janus3d_N4", "poiseuille3d_N7"])
+def test_fp32_parity_100_steps(case):
+    compare(CASES[case](), 100, "fp32")
+
+
+@pytest.mark.parametrize("shape,walls,N", [((3, 5), (False, True), 2), ((5, 1), (False, False), 3),
+                                           ((3, 4), (True, False), 2), ((7, 3), (True, True), 4)])
+def test_tiny_and_degenerate_grids(shape, walls, N):
+    nx, ny = shape
+    p = _mixture(nx, ny, N, 20 + nx, walls=(walls[0], walls[1], False))
+    compare(p, 30, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_spinodal_elementwise(precision):
+    # The benchmarked workload (512 x 512, N = 4) element by element after 3 steps.
+    p = W.spinodal_2d()
+    compare(p, 3, precision)
+
+
+def _absent_lens(N=4):
+    p = W.lens_2d(nx=40, ny=36, radius=8)
+    C = np.zeros((N,) + p["C0"].shape[1:])
+    C[:3] = p["C0"]
+    sig = np.full((N, N), 0.005)
+    np.fill_diagonal(sig, 0)
+    sig[:3, :3] = p["sigma"]
+    q = W.base_params(9, 40, 36, 1, N, sig, 1.0, walls=(False, True, False), m=0.05, implicit=0)
+    q["C0"] = C
+    return q
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "f16", "bf16"])
+def test_absent_component_stays_exactly_zero(precision):
+    p = _absent_lens()
+    with nfe.Sim(p, precision, scale_exp=10) as s:
+        s.set_fields(p["C0"])
+        for _ in range(3):
+            s.step(100)
+            C, _, _ = s.fields()
+            assert (C[3] == 0.0).all()
+    p = W.layered_poiseuille(nx=6, ny=5, nz=24)
+    with nfe.Sim(p, precision, scale_exp=10) as s:
+        s.set_fields(p["C0"])
+        s.step(300)
+        C, _, _ = s.fields()
+        assert (C[6] == 0.0).all()
+
+
+def test_mass_and_momentum_conservation_fp64():
+    p = W.janus_2d(nx=64, ny=64, radius=12, offset=15)
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        d0 = s.diagnostics()
+        for _ in range(5):
+            s.step(200)
+            d = s.diagnostics()
+            np.testing.assert_allclose(d["mass"], d0["mass"], rtol=1e-13)
+            assert np.abs(d["force_sum"]).max() <= 1e-13 * d["force_abs_sum"].sum()
+            assert np.abs(d["momentum"]).max() <= 1e-13 * d["force_abs_sum"].sum() + 1e-16
+            assert d["nonfinite"] == 0
+
+
+def test_momentum_changes_by_body_force():
+    p = W.janus_2d(nx=48, ny=48, radius=9, offset=11)
+    p["body_force"] = (1e-6, -5e-7, 0.0)
+    n = 48 * 48
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        s.step(10)
+        m0 = s.diagnostics()["momentum"]
+        s.step(50)
+        m1 = s.diagnostics()["momentum"]
+    np.testing.assert_allclose(m1 - m0, 50 * n * np.array(p["body_force"]), rtol=1e-10, atol=1e-16)
+
+
+def test_checkpoint_roundtrip_and_graph_replay_are_bitwise():
+    p = W.spinodal_2d(nx=40, ny=32, seed=3)
+    with nfe.Sim(p, "fp32") as s:
+        s.set_fields(p["C0"])
+        s.step(5)
+        snap = s.get_state()
+        s.step(11)                # graph replay (5 x 2 steps) + one direct step
+        a = s.get_state()
+        s.set_state(snap)
+        for _ in range(11):
+            s.step(1)             # direct launches only
+        b = s.get_state()
+        s.set_state(snap)
+        s.profile_enable(True)
+        s.step(11)                # timed launches
+        c = s.get_state()
+        prof = s.profile_read()
+    assert np.array_equal(a, b) and np.array_equal(a, c)
+    assert set(prof) == {"collide_stream", "ch_update"}
+    assert prof["collide_stream"][0] == 11
+
+
+def test_nonfinite_flag_reported():
+    p = W.spinodal_2d(nx=16, ny=16, seed=4)
+    C0 = p["C0"].copy()
+    C0[1, 0, 3, 4] = np.nan
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(C0)
+        s.step(2)
+        with pytest.raises(nfe.NfeError) as e:
+            s.sync()
+        assert e.value.status == 5
+        assert s.diagnostics()["nonfinite"] == 1
+
+
+@pytest.mark.parametrize("precision", ["f16", "bf16"])
+def test_low_precision_storage_tracks_fp32(precision):
+    # FP16/BF16 storage of f as deviations f_k / w_k: C stays close to the FP32 run.
+    p = W.spinodal_2d(nx=48, ny=40)
+    g32 = gpu_run(p, 200, "fp32")
+    glo = gpu_run(p, 200, precision, scale_exp=10)
+    assert rel(glo["C"], g32["C"]) < (1e-4 if precision == "f16" else 1e-3)
