@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Throughput of the N-component free-energy LBM time step on GB300.
+
+Workload: the quaternary spinodal mixture, 512 x 512 D2Q9, N = 4, all
+sigma_ij = 0.005, tau = 0.8, m = 0.1, C_i = 1/4 + U(-0.02, 0.02) renormalised
+(seed 1002).  One bench step = one time step of the whole lattice (stencils,
+flux potential, conservative force, collide+stream of f, Cahn-Hilliard update
+of C).  The whole working set (~30 MB in FP32) fits in the 129 MB L2, so a
+256 MiB buffer is written between timed steps and every timed step starts
+with a cold L2; CUDA events on the library's stream bracket each step.
+
+Metric: MLUPS x N (million lattice-site updates per second times the number
+of components), for the FP32 path (headline `value`) with the FP64 path
+reported beside it (`fp64_path`).  `roofline` is for the dominant kernel,
+against the measured HBM copy bandwidth.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nfe|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica (the path has
+no data exchange between simulations); the slowest rank's time is used.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import nfe_workloads as W  # noqa: E402
+
+WORKLOAD = "spinodal 512x512 D2Q9 N=4 (sigma=0.005, tau=0.8, m=0.1, seed 1002)"
+METRIC = "MLUPS x N (FP32 path; FP64 path beside), cold-L2 time per step"
+UNIT = "MLUPS*N"
+FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return ws, rank
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def run_nfe(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_22214_gb300 as nfe
+    from paper_2605_22214_gb300 import build as nfe_build
+
+    ws, rank = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    nfe_build.build()
+    hbm, peak_kind = _peaks()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    p = W.spinodal_2d(seed=1002 + 1000 * rank)
+    n = p["nx"] * p["ny"] * p["nz"]
+    N = p["N"]
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed_steps(sim, K, W_, clocks=None):
+        """Sum of per-step event times with an L2 flush before every step (ms)."""
+        with torch.cuda.stream(stream):
+            for _ in range(W_):
+                flush.zero_()
+                sim.step(1)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        total = 0.0
+        pending = []
+        t0 = time.perf_counter()
+        ctx = clocks if clocks is not None else _Null()
+        with ctx:
+            with torch.cuda.stream(stream):
+                for i in range(K):
+                    flush.zero_()
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    sim.step(1)
+                    b.record(stream)
+                    pending.append((a, b))
+                    if len(pending) >= 256:
+                        b.synchronize()
+                        total += sum(x.elapsed_time(y) for x, y in pending)
+                        pending.clear()
+            torch.cuda.synchronize()
+        total += sum(x.elapsed_time(y) for x, y in pending)
+        wall = time.perf_counter() - t0
+        barrier()
+        return total, wall
+
+    def kernel_times(sim, K):
+        """Per-kernel average duration (ms) from the library's own events, flushed L2."""
+        sim.profile_enable(True)
+        with torch.cuda.stream(stream):
+            for _ in range(K):
+                flush.zero_()
+                sim.step(1)
+        prof = sim.profile_read()
+        sim.profile_enable(False)
+        return {k: (cnt, ms / cnt) for k, (cnt, ms) in prof.items()}
+
+    results = {}
+    for prec in ("fp32", "fp64"):
+        K = args.steps if prec == "fp32" else max(1, args.steps // 4)
+        sim = nfe.Sim(p, prec, stream=stream.cuda_stream)
+        sim.set_fields(p["C0"])
+        info = sim.info()
+        clocks = Clocks(local) if prec == "fp32" else None
+        ms_total, wall = timed_steps(sim, K, args.warmup, clocks)
+        ms_total = max_over_ranks(ms_total)
+        ms_step = ms_total / K
+        kt = kernel_times(sim, min(K, 500))
+        d = sim.diagnostics()
+        results[prec] = dict(sim=sim, info=info, ms_step=ms_step, K=K, kt=kt, diag=d, clocks=clocks, wall=wall)
+
+    # end-to-end through the C ABI with host buffers: H2D of the full state from pinned
+    # memory, one step, D2H of the full state, every step (wall clock, synchronised)
+    r32 = results["fp32"]
+    sim = r32["sim"]
+    nbytes = r32["info"]["state_bytes"]
+    hbuf = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+    nfe.nfe_get_state_ptr(sim.h, hbuf.data_ptr(), nbytes)
+    Ke = max(1, min(args.steps, 200))
+    for _ in range(3):
+        nfe.nfe_set_state_ptr(sim.h, hbuf.data_ptr(), nbytes)
+        sim.step(1)
+        nfe.nfe_get_state_ptr(sim.h, hbuf.data_ptr(), nbytes)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(Ke):
+        nfe.nfe_set_state_ptr(sim.h, hbuf.data_ptr(), nbytes)
+        sim.step(1)
+        nfe.nfe_get_state_ptr(sim.h, hbuf.data_ptr(), nbytes)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_val = ws * n * Ke * N / e2e_s / 1e6
+
+    def roofline(r):
+        kt = r["kt"]
+        prec_bytes = 4 if r is r32 else 8
+        # dominant kernel and its compulsory bytes per site (each array it touches once)
+        dom = max(kt, key=lambda k: kt[k][1])
+        Q, D = 9, 2
+        if dom == "collide_stream":
+            bps = prec_bytes * ((Q - 1) + (N - 1) + (Q - 1) + D + (N - 1))
+        else:
+            bps = prec_bytes * ((N - 1) + D + (N - 1) + (N - 1))
+        ach = bps * n / (kt[dom][1] * 1e-3) / 1e9
+        return dict(bound="hbm", kernel=dom, bytes_per_site=bps, achieved=round(ach, 1), peak=hbm,
+                    unit="GB/s", frac=round(ach / hbm, 4), peak_source=peak_kind, traffic=None,
+                    kernel_ms=round(kt[dom][1], 5))
+
+    def path_summary(r):
+        mlups = ws * n / (r["ms_step"] * 1e-3) / 1e6
+        eff = r["info"]["min_bytes_per_site"] * n / (r["ms_step"] * 1e-3) / 1e9
+        return dict(value=round(mlups * N, 1), mlups=round(mlups, 1), ms_per_step=round(r["ms_step"], 5),
+                    effective_gbs=round(eff, 1), effective_frac=round(eff / hbm, 4),
+                    min_bytes_per_site=r["info"]["min_bytes_per_site"],
+                    kernels={k: dict(launches=c, avg_ms=round(t, 5)) for k, (c, t) in r["kt"].items()},
+                    )
+
+    s32 = path_summary(r32)
+    s64 = path_summary(results["fp64"])
+    s64["roofline"] = roofline(results["fp64"])
+    line = {
+        "metric": METRIC,
+        "value": s32["value"],
+        "unit": UNIT,
+        "n_gpus": ws,
+        "steps": r32["K"],
+        "warmup": args.warmup,
+        "ms_per_step": s32["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded spinodal mixture, numpy PCG64)",
+        "config": {"workload": WORKLOAD, "sites": n, "N": N, "lattice": "D2Q9", "precision": "fp32",
+                   "l2": "256 MiB buffer written before every timed step (cold L2)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "mlups": s32["mlups"],
+        "effective_gbs": s32["effective_gbs"],
+        "effective_frac": s32["effective_frac"],
+        "roofline": roofline(r32),
+        "kernels": s32["kernels"],
+        "fp64_path": s64,
+        "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes, "steps": Ke,
+                "how": "nfe_set_state (pinned host -> device), nfe_step(1), nfe_get_state (device -> pinned host)"},
+        "gpu_launches": r32["info"]["kernels_per_step"] * r32["K"],
+        "clocks": r32["clocks"].summary() if r32["clocks"] is not None else None,
+    }
+    for r in results.values():
+        r["sim"].close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, budget_s=args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def _oracle_rate(p, budget_s, min_steps=2):
+    """Time the FP64 oracle, as it stands, on p for about budget_s seconds."""
+    from oracle import lbm
+    prm = lbm.Params(p)
+    st = lbm.init_state(prm, p["C0"])
+    st = lbm.step(prm, st)                      # warm-up
+    steps = 0
+    t0 = time.perf_counter()
+    while steps < min_steps or time.perf_counter() - t0 < budget_s:
+        st = lbm.step(prm, st)
+        steps += 1
+    dt = time.perf_counter() - t0
+    n = p["nx"] * p["ny"] * p["nz"]
+    return n * steps / dt / 1e6, steps, dt
+
+
+def cpu_baseline(p, budget_s=15.0):
+    mlups, steps, dt = _oracle_rate(p, budget_s)
+    return {"value": round(mlups * p["N"], 4), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps} time steps of the full 512x512 N=4 workload in {dt:.1f} s "
+                      "(numpy FP64 oracle, literal f and g populations, single thread)"}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, same config, metric and unit."""
+    ws, rank = _dist()
+    if rank != 0:
+        return
+    full = W.spinodal_2d(seed=1002)
+    # each bench step: one time step of a periodic square sample of the workload's initial
+    # field, sized so the whole --steps/--warmup run ends within about two minutes
+    rate, _, _ = _oracle_rate(W.spinodal_2d(nx=64, ny=64, seed=1002), 2.0)
+    per_step = 120.0 / max(1, args.steps + args.warmup)
+    side = int(max(8, min(512, math.sqrt(rate * 1e6 * per_step))))
+    p = dict(full)
+    p["nx"] = p["ny"] = side
+    p["C0"] = full["C0"][:, :, :side, :side] / full["C0"][:, :, :side, :side].sum(axis=0, keepdims=True)
+    from oracle import lbm
+    prm = lbm.Params(p)
+    st = lbm.init_state(prm, p["C0"])
+    for _ in range(args.warmup):
+        st = lbm.step(prm, st)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        st = lbm.step(prm, st)
+    dt = time.perf_counter() - t0
+    val = side * side * args.steps * p["N"] / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(val, 4), "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded spinodal mixture, numpy PCG64)",
+            "config": {"workload": WORKLOAD, "sample": f"{side}x{side} periodic corner of the 512x512 input"},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(val, 4), "unit": UNIT,
+                             "sample": f"{args.steps} steps of a {side}x{side} sample"},
+            "e2e": {"value": round(val, 4), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["nfe", "reference"], default="nfe")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_nfe(args)
+
+
+if __name__ == "__main__":
+    main()
