@@ -125,6 +125,8 @@ typedef struct {
     double factor_residual;          /* largest dropped coefficient of the factored flux
                                         potential, relative (checks alpha/Lambda/Theta) */
     int kernels_per_step;            /* kernel launches of one nfe_step(1) */
+    int variant;                     /* tile shape in use (-1: not tuned yet) */
+    int nvariants;                   /* tile shapes available for this lattice/N/precision */
     double min_bytes_per_site;       /* f (Q-1) and C (N-1) read once and written once */
     size_t state_bytes;              /* size of the raw state (nfe_get_state) */
     size_t device_bytes;             /* device memory held by the simulation */
@@ -175,6 +177,12 @@ nfe_status nfe_get_state(nfe_sim *sim, void *host_buf, size_t bytes);
 nfe_status nfe_set_state(nfe_sim *sim, const void *host_buf, size_t bytes);
 
 nfe_status nfe_get_info(const nfe_sim *sim, nfe_info *out);
+
+/* Tile shape of the time-step kernel.  variant < 0 (the default) lets the
+ * first nfe_step time every shape on the current state and keep the fastest
+ * (the state is not modified); 0 .. nvariants-1 fixes one.  All shapes give
+ * bit-identical results. */
+nfe_status nfe_set_variant(nfe_sim *sim, int variant);
 
 /* Kernel timing on the simulation's stream: when enabled, CUDA events bracket
  * every kernel launch of nfe_step (graphs are bypassed).  read returns, per

@@ -33,7 +33,7 @@ STATUS = {0: "NFE_OK", 1: "NFE_EINVAL", 2: "NFE_ENOMEM", 3: "NFE_ECUDA", 4: "NFE
 EXPORTS = ["nfe_create", "nfe_set_fields", "nfe_step", "nfe_sync", "nfe_fields", "nfe_populations",
            "nfe_diagnostics", "nfe_get_state", "nfe_set_state", "nfe_get_info", "nfe_profile_enable",
            "nfe_profile_read", "nfe_destroy", "nfe_status_string", "nfe_last_error",
-           "nfe_bulk_potential_host"]
+           "nfe_bulk_potential_host", "nfe_set_variant"]
 
 
 class nfe_grid(C.Structure):
@@ -59,7 +59,8 @@ class nfe_diag(C.Structure):
 class nfe_info(C.Structure):
     _fields_ = [("lattice", C.c_int), ("N", C.c_int), ("precision", C.c_int), ("sites", C.c_int64),
                 ("omega_stab", C.c_double), ("factor_residual", C.c_double),
-                ("kernels_per_step", C.c_int), ("min_bytes_per_site", C.c_double),
+                ("kernels_per_step", C.c_int), ("variant", C.c_int), ("nvariants", C.c_int),
+                ("min_bytes_per_site", C.c_double),
                 ("state_bytes", C.c_size_t), ("device_bytes", C.c_size_t)]
 
 
@@ -95,6 +96,7 @@ def load():
         "nfe_set_state": ([P, P, C.c_size_t], C.c_int),
         "nfe_get_info": ([P, C.POINTER(nfe_info)], C.c_int),
         "nfe_profile_enable": ([P, C.c_int], C.c_int),
+        "nfe_set_variant": ([P, C.c_int], C.c_int),
         "nfe_profile_read": ([P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_char_p),
                               C.POINTER(C.c_int64), dp], C.c_int),
         "nfe_destroy": ([P], None),
@@ -220,6 +222,10 @@ def nfe_set_state_ptr(h, ptr, nbytes):
     _check(load().nfe_set_state(h, C.c_void_p(ptr), int(nbytes)))
 
 
+def nfe_set_variant(h, variant):
+    _check(load().nfe_set_variant(h, int(variant)))
+
+
 def nfe_profile_enable(h, on=True):
     _check(load().nfe_profile_enable(h, 1 if on else 0))
 
@@ -299,6 +305,9 @@ class Sim:
 
     def set_state(self, buf):
         nfe_set_state(self.h, buf)
+
+    def set_variant(self, variant):
+        nfe_set_variant(self.h, variant)
 
     def profile_enable(self, on=True):
         nfe_profile_enable(self.h, on)

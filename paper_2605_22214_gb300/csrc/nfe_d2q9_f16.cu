@@ -1,6 +1,7 @@
-// D2Q9 time-step kernels, N = 2 .. 8, f16 storage/arithmetic variant.
-#include "nfe_kernels.cuh"
+// D2Q9 time-step kernels, N = 2 .. 8, f16 storage/arithmetic variant: the fused
+// single-kernel step (three tile shapes) plus the shared helpers.
+#include "nfe_fused2d.cuh"
 
 namespace nfe {
-const Ops *ops_d2q9_f16(int N) { return ops_for_n<LD2Q9, float, __half>(N, NFE_FP32_F16STORE); }
+const Ops *ops_d2q9_f16(int N) { return ops_fused2d<float, __half>(N, NFE_FP32_F16STORE); }
 }  // namespace nfe

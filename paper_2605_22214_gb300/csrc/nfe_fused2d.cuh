@@ -1,0 +1,433 @@
+// Fused D2Q9 time step: one kernel per step, one CTA per TX x TY tile.
+//
+//   phase 1  evolved C on the tile and a 2-site ring -> shared memory (wrapped
+//            coordinates), with C_implicit = 1 - sum and the bulk energy E_B
+//            (Eq. 5) computed once per site;
+//   phase 2  on the tile and a 1-site ring: isotropic grad / Laplacian of every
+//            C_i and grad E_B from shared memory (Eqs. 35-36, wall rule of
+//            Sec. III C), flux potential S_i = C_i q_i(C) + (3D/4) lap C_i
+//            (Eq. 12, factored), force F (Eq. 34), f_k(x) from HBM, v and P
+//            (Eqs. 37-38); (C, v, S) of every site -> shared memory;
+//   phase 3  tile sites: TRT collision with forcing (Eqs. 23-30), push-stream
+//            with halfway bounce-back (Eqs. 44-45);
+//   phase 4  tile sites: C_i(x, t+1) = sum_k g^eq_{i,k}(x - e_k) (Eqs. 39-41,
+//            tau_g = 1) from the shared (C, v, S) of the 1-ring.
+// Only f (8 populations) and the N-1 evolved C are read from and written to
+// HBM; every other quantity lives in registers or shared memory.  CTAs whose
+// tile plus ring is inside the domain take a path without wrap or wall tests.
+#pragma once
+
+#include "nfe_kernels.cuh"
+
+namespace nfe {
+
+// Shared-memory record of NV values of type T, stored as 16-byte chunks in
+// separate planes so that consecutive threads never hit the same bank.
+template <typename T, int NV>
+struct SRec {
+    static constexpr int PER = 16 / sizeof(T);               // values per chunk
+    static constexpr int NC = (NV + PER - 1) / PER;           // chunks per record
+    static constexpr int NVP = NC * PER;                      // padded count
+};
+
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; };
+template <> struct Vec16<double> { using type = double2; };
+
+template <typename T, int NV>
+__device__ __forceinline__ void srec_load(const T *base, int count, int i, T (&out)[SRec<T, NV>::NVP]) {
+    using V = typename Vec16<T>::type;
+#pragma unroll
+    for (int c = 0; c < SRec<T, NV>::NC; ++c) {
+        const V v = reinterpret_cast<const V *>(base + size_t(c) * count * SRec<T, NV>::PER)[i];
+        if constexpr (sizeof(T) == 4) {
+            out[4 * c + 0] = v.x; out[4 * c + 1] = v.y; out[4 * c + 2] = v.z; out[4 * c + 3] = v.w;
+        } else {
+            out[2 * c + 0] = v.x; out[2 * c + 1] = v.y;
+        }
+    }
+}
+
+template <typename T, int NV>
+__device__ __forceinline__ void srec_store(T *base, int count, int i, const T (&in)[SRec<T, NV>::NVP]) {
+    using V = typename Vec16<T>::type;
+#pragma unroll
+    for (int c = 0; c < SRec<T, NV>::NC; ++c) {
+        V v;
+        if constexpr (sizeof(T) == 4) {
+            v.x = in[4 * c + 0]; v.y = in[4 * c + 1]; v.z = in[4 * c + 2]; v.w = in[4 * c + 3];
+        } else {
+            v.x = in[2 * c + 0]; v.y = in[2 * c + 1];
+        }
+        reinterpret_cast<V *>(base + size_t(c) * count * SRec<T, NV>::PER)[i] = v;
+    }
+}
+
+template <int N, typename T, int TX, int TY>
+struct Fused2DShape {
+    static constexpr int AX = TX + 4, AY = TY + 4, ACOUNT = AX * AY;   // tile + 2-ring
+    static constexpr int BX = TX + 2, BY = TY + 2, BCOUNT = BX * BY;   // tile + 1-ring
+    using RA = SRec<T, N>;            // evolved C (N-1) and E_B
+    using RB = SRec<T, 2 * N>;        // evolved C (N-1), vx, vy, S (N-1)
+    static constexpr int A_VALUES = RA::NVP * ACOUNT;
+    static constexpr int B_VALUES = RB::NVP * BCOUNT;
+    static constexpr size_t BYTES = sizeof(T) * size_t(A_VALUES + B_VALUES);
+    static constexpr int NHALO = BCOUNT - TX * TY;
+};
+
+__device__ __forceinline__ int wrap(int v, int n) {
+    // v in [-n, 2n)
+    return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+__device__ __forceinline__ int imod(int v, int n) { return ((v % n) + n) % n; }
+
+// Stencil of one site from record A at local index ia (row pitch AX).  `wall`
+// holds bit k set when x + e_k lies beyond a wall (then that term is dropped).
+template <int N, typename T, int AX, bool CHECK>
+__device__ __forceinline__ void stencil2d(const T *sA, int acount, int ia, unsigned wall,
+                                          T (&c)[N], T (&lap)[N], T (&gx)[N], T (&gy)[N], T &gEx, T &gEy) {
+    using RA = SRec<T, N>;
+    T r0[RA::NVP];
+    srec_load<T, N>(sA, acount, ia, r0);
+    T d[9][N];            // d[k][a]: neighbour minus centre, a < N-1 volume fractions, a = N-1 bulk energy
+    constexpr int off[9] = {0, 1, -1, AX, -AX, AX + 1, -AX - 1, -AX + 1, AX - 1};
+#pragma unroll
+    for (int k = 1; k < 9; ++k) {
+        if (CHECK && ((wall >> k) & 1u)) {
+#pragma unroll
+            for (int a = 0; a < N; ++a) d[k][a] = T(0);
+        } else {
+            T r[RA::NVP];
+            srec_load<T, N>(sA, acount, ia + off[k], r);
+#pragma unroll
+            for (int a = 0; a < N; ++a) d[k][a] = r[a] - r0[a];
+        }
+    }
+    const T third = T(1) / T(3), twelfth = T(1) / T(12), two3 = T(2) / T(3), sixth = T(1) / T(6);
+    T sl = T(0), sgx = T(0), sgy = T(0);
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) {
+        c[a] = r0[a];
+        const T ax = (d[1][a] + d[2][a]) + (d[3][a] + d[4][a]);
+        const T dg = (d[5][a] + d[6][a]) + (d[7][a] + d[8][a]);
+        lap[a] = two3 * ax + sixth * dg;                                    // (2/c_s^2) sum w_k d_k
+        gx[a] = third * (d[1][a] - d[2][a]) + twelfth * ((d[5][a] - d[6][a]) + (d[7][a] - d[8][a]));
+        gy[a] = third * (d[3][a] - d[4][a]) + twelfth * ((d[5][a] - d[6][a]) - (d[7][a] - d[8][a]));
+        sl += lap[a]; sgx += gx[a]; sgy += gy[a];
+    }
+    // implicit component: C_N = 1 - sum, its stencils are minus the sum of the others
+    T rest = T(0);
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) rest += r0[a];
+    c[N - 1] = T(1) - rest;
+    lap[N - 1] = -sl; gx[N - 1] = -sgx; gy[N - 1] = -sgy;
+    constexpr int e = N - 1;
+    gEx = third * (d[1][e] - d[2][e]) + twelfth * ((d[5][e] - d[6][e]) + (d[7][e] - d[8][e]));
+    gEy = third * (d[3][e] - d[4][e]) + twelfth * ((d[5][e] - d[6][e]) - (d[7][e] - d[8][e]));
+}
+
+// Phase 2 at one site: S, F, v, P from the stencil and f.  f must hold f_1..f_8.
+template <int N, typename T>
+__device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N], const T (&lap)[N],
+                                             const T (&gx)[N], const T (&gy)[N], T gEx, T gEy,
+                                             const T (&f)[9], T (&S)[N - 1], T &Fx, T &Fy,
+                                             T &vx, T &vy, T &P, T &sumf) {
+    // force of Eq. 34 (or Eq. 31)
+    if (!cf.nonconservative) {
+        Fx = gEx; Fy = gEy;
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            T h = T(0);
+#pragma unroll
+            for (int b = 0; b < N; ++b) if (b != a) h += cf.kappa[a][b] * lap[b];
+            Fx += h * gx[a]; Fy += h * gy[a];
+        }
+    } else {
+        Fx = T(0); Fy = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const T ca = c[a];
+            const T fpa = T(2) * ca * (T(1) - T(3) * ca + T(2) * ca * ca);
+            T mu = T(0);
+#pragma unroll
+            for (int b = 0; b < N; ++b) if (b != a) {
+                const T t = ca + c[b];
+                const T fpt = T(2) * t * (T(1) - T(3) * t + T(2) * t * t);
+                mu += cf.beta[a][b] * (fpa - fpt) + cf.kappa[a][b] * lap[b];
+            }
+            Fx += mu * gx[a]; Fy += mu * gy[a];
+        }
+    }
+    Fx += cf.fb[0]; Fy += cf.fb[1];
+    T q[N - 1];
+    flux_poly<N, T>(c, cf, q);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
+    // moments (Eqs. 37-38), rho = 1
+    const T jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[7] - f[8]);
+    const T jy = (f[3] - f[4]) + (f[5] - f[6]) - (f[7] - f[8]);
+    sumf = ((f[1] + f[2]) + (f[3] + f[4])) + ((f[5] + f[6]) + (f[7] + f[8]));
+    vx = jx + T(0.5) * Fx;
+    vy = jy + T(0.5) * Fy;
+    const T w0 = T(4) / T(9);
+    P = (sumf - T(1.5) * w0 * (vx * vx + vy * vy)) / (T(3) * (T(1) - w0));
+}
+
+template <int N, typename T, typename SF, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
+          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag) {
+    using Sh = Fused2DShape<N, T, TX, TY>;
+    using RA = typename Sh::RA;
+    using RB = typename Sh::RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    T *sB = sA + Sh::A_VALUES;
+    const int nx = g.nx, ny = g.ny;
+    const size_t n = size_t(g.n);
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.x;
+    // uniform per CTA: does the tile plus its 2-ring cross the domain edge?
+    const bool edge = (x0 - 2 < 0) || (x0 + TX + 2 > nx) || (y0 - 2 < 0) || (y0 + TY + 2 > ny);
+
+    // ---- phase 1: C and E_B on tile + 2-ring ---------------------------------
+    for (int i = tid; i < Sh::ACOUNT; i += TX * TY) {
+        const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
+        int gx = x0 + lx - 2, gy = y0 + ly - 2;
+        if (edge) {
+            // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
+            // such entries are never used by a real site's stencil
+            gx = g.wx ? min(max(gx, 0), nx - 1) : imod(gx, nx);
+            gy = g.wy ? min(max(gy, 0), ny - 1) : imod(gy, ny);
+        }
+        const int s = gx + nx * gy;
+        T rec[RA::NVP];
+        T cc[N];
+        T rest = T(0);
+#pragma unroll
+        for (int a = 0; a < N - 1; ++a) { cc[a] = Cin[a * n + s]; rec[a] = cc[a]; rest += cc[a]; }
+        cc[N - 1] = T(1) - rest;
+        rec[N - 1] = bulk_energy<N, T>(cc, cf);
+#pragma unroll
+        for (int a = N; a < RA::NVP; ++a) rec[a] = T(0);
+        srec_store<T, N>(sA, Sh::ACOUNT, i, rec);
+    }
+    __syncthreads();
+
+    // ---- phase 2a: own site ---------------------------------------------------
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx0 = x0 + tx, gy0 = y0 + ty;
+    const bool own = gx0 < nx && gy0 < ny;             // ragged far edge: duplicates only
+    const int sx = edge ? imod(gx0, nx) : gx0;         // wrapped (periodic duplicates)
+    const int sy = edge ? imod(gy0, ny) : gy0;
+    const int s0 = sx + nx * sy;
+    // wall mask of the own site: bit k set when x + e_k is beyond a wall
+    unsigned wall0 = 0;
+    if (edge) {
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            const int xx = gx0 + LD2Q9::ex(k), yy = gy0 + LD2Q9::ey(k);
+            if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) wall0 |= 1u << k;
+        }
+    }
+    T f[9];
+    T c[N], lap[N], gxv[N], gyv[N], gEx, gEy;
+    T S[N - 1], Fx, Fy, vx, vy, P, sumf;
+    {
+        const int ia = (ty + 2) * Sh::AX + (tx + 2);
+        if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
+        else      stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
+        f[0] = T(0);
+#pragma unroll
+        for (int k = 1; k < 9; ++k) f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv);
+        site_physics<N, T>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
+        T rec[RB::NVP];
+#pragma unroll
+        for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 1 + a] = S[a]; }
+        rec[N - 1] = vx; rec[N] = vy;
+#pragma unroll
+        for (int a = 2 * N; a < RB::NVP; ++a) rec[a] = T(0);
+        srec_store<T, 2 * N>(sB, Sh::BCOUNT, (ty + 1) * Sh::BX + (tx + 1), rec);
+    }
+
+    // ---- phase 2b: the 1-ring around the tile ---------------------------------
+    for (int h = tid; h < Sh::NHALO; h += TX * TY) {
+        // enumerate the ring: top row, bottom row, then left and right columns
+        int bx, by;
+        if (h < Sh::BX) { bx = h; by = 0; }
+        else if (h < 2 * Sh::BX) { bx = h - Sh::BX; by = Sh::BY - 1; }
+        else { const int r = h - 2 * Sh::BX; by = 1 + (r >> 1); bx = (r & 1) ? Sh::BX - 1 : 0; }
+        const int hx = x0 + bx - 1, hy = y0 + by - 1;
+        bool beyond = false;
+        unsigned wall = 0;
+        int wx_ = hx, wy_ = hy;
+        if (edge) {
+            if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) beyond = true;
+            wx_ = imod(hx, nx);
+            wy_ = imod(hy, ny);
+#pragma unroll
+            for (int k = 1; k < 9; ++k) {
+                const int xx = hx + LD2Q9::ex(k), yy = hy + LD2Q9::ey(k);
+                if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) wall |= 1u << k;
+            }
+        }
+        if (beyond) continue;          // sources beyond a wall are replaced by bounce-back
+        const int s = wx_ + nx * wy_;
+        T hc[N], hl[N], hgx[N], hgy[N], hEx, hEy;
+        const int ia = (by + 1) * Sh::AX + (bx + 1);
+        if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall, hc, hl, hgx, hgy, hEx, hEy);
+        else      stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
+        T hf[9];
+        hf[0] = T(0);
+#pragma unroll
+        for (int k = 1; k < 9; ++k) hf[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD2Q9::w(k), cf.finv);
+        T hS[N - 1], hFx, hFy, hvx, hvy, hP, hsum;
+        site_physics<N, T>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
+        T rec[RB::NVP];
+#pragma unroll
+        for (int a = 0; a < N - 1; ++a) { rec[a] = hc[a]; rec[N + 1 + a] = hS[a]; }
+        rec[N - 1] = hvx; rec[N] = hvy;
+#pragma unroll
+        for (int a = 2 * N; a < RB::NVP; ++a) rec[a] = T(0);
+        srec_store<T, 2 * N>(sB, Sh::BCOUNT, by * Sh::BX + bx, rec);
+    }
+
+    // ---- phase 3: collide and push-stream the own site ----------------------
+    if (own) {
+        T op, om;
+        relaxation<N, T>(cf, c, op, om);
+        const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
+        const T vv = vx * vx + vy * vy, vF = vx * Fx + vy * Fy;
+#pragma unroll
+        for (int k = 1; k < 9; k += 2) {
+            const int kb = k + 1;
+            const T wk = T(LD2Q9::w(k));
+            const T eu = T(LD2Q9::ex(k)) * vx + T(LD2Q9::ey(k)) * vy;
+            const T eF = T(LD2Q9::ex(k)) * Fx + T(LD2Q9::ey(k)) * Fy;
+            const T eqp = wk * (T(3) * P + T(4.5) * eu * eu - T(1.5) * vv);
+            const T eqm = wk * (T(3) * eu);
+            const T Fp = wk * (T(9) * eu * eF - T(3) * vF);
+            const T Fm = wk * (T(3) * eF);
+            const T fp = T(0.5) * (f[k] + f[kb]);
+            const T fm = T(0.5) * (f[k] - f[kb]);
+            const T sym = -op * (fp - eqp) + ap * Fp;
+            const T anti = -om * (fm - eqm) + am * Fm;
+            const T pk = f[k] + sym + anti;
+            const T pkb = f[kb] + sym - anti;
+            if (!edge) {
+                const int dk = LD2Q9::ex(k) + nx * LD2Q9::ey(k);
+                FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), pk, LD2Q9::w(k), cf.finv);
+                FStore<SF, T>::store(fout + (kb - 1) * n + (s0 - dk), pkb, LD2Q9::w(kb), cf.finv);
+            } else {
+                if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, pk, LD2Q9::w(kb), cf.finv);
+                else FStore<SF, T>::store(fout + (k - 1) * n + (wrap(sx + LD2Q9::ex(k), nx) + nx * wrap(sy + LD2Q9::ey(k), ny)),
+                                          pk, LD2Q9::w(k), cf.finv);
+                if ((wall0 >> kb) & 1u) FStore<SF, T>::store(fout + (k - 1) * n + s0, pkb, LD2Q9::w(k), cf.finv);
+                else FStore<SF, T>::store(fout + (kb - 1) * n + (wrap(sx - LD2Q9::ex(k), nx) + nx * wrap(sy - LD2Q9::ey(k), ny)),
+                                          pkb, LD2Q9::w(kb), cf.finv);
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 4: Cahn-Hilliard update of the own site ----------------------
+    if (own) {
+        const T m = cf.m;
+        const T w0 = T(4) / T(9);
+        const int ib = (ty + 1) * Sh::BX + (tx + 1);
+        T r0[RB::NVP];
+        srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib, r0);
+        const T vv0 = r0[N - 1] * r0[N - 1] + r0[N] * r0[N];
+        T acc[N - 1], lapS[N - 1];
+#pragma unroll
+        for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (T(1) - T(1.5) * w0 * vv0); lapS[e] = T(0); }
+        constexpr int offB[9] = {0, 1, -1, TX + 2, -(TX + 2), TX + 3, -(TX + 3), -(TX + 2) + 1, (TX + 2) - 1};
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            const T wk = T(LD2Q9::w(k));
+            // source x - e_k is the neighbour in direction kbar
+            const int kb = opp(k);
+            if (edge && ((wall0 >> kb) & 1u)) {
+                // bounce-back: g_k(x, t+1) = g^eq_kbar(x, t)
+                const T eu = -(T(LD2Q9::ex(k)) * r0[N - 1] + T(LD2Q9::ey(k)) * r0[N]);
+                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
+#pragma unroll
+                for (int e = 0; e < N - 1; ++e) { acc[e] += r0[e] * sk; lapS[e] += wk * r0[N + 1 + e]; }
+            } else {
+                T r[RB::NVP];
+                srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib + offB[kb], r);
+                const T eu = T(LD2Q9::ex(k)) * r[N - 1] + T(LD2Q9::ey(k)) * r[N];
+                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (r[N - 1] * r[N - 1] + r[N] * r[N]));
+#pragma unroll
+                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * r[N + 1 + e]; }
+            }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int e = 0; e < N - 1; ++e) {
+            const T out = acc[e] + m * ((T(1) - w0) * r0[N + 1 + e] - lapS[e]);
+            Cout[e * n + s0] = out;
+            bad |= !isfinite(out);
+        }
+        if (bad) atomicOr(flag, 1);
+    }
+}
+
+template <int N, typename T, typename SF, int TX, int TY>
+cudaError_t launch_fused2d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
+    using Sh = Fused2DShape<N, T, TX, TY>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
+    k_fused2d<N, T, SF, TX, TY><<<grid, TX * TY, Sh::BYTES, st>>>(
+        g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
+        static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]), b.flag);
+    return cudaGetLastError();
+}
+
+}  // namespace nfe
+
+namespace nfe {
+
+// D2Q9 dispatch: the fused step with three tile heights (TX = 32).
+template <int N, typename T, typename SF>
+struct Fused2DLaunch {
+    static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        switch (variant) {
+            case 0: return launch_fused2d<N, T, SF, 32, 4>(g, cf, b, cur, st);
+            case 1: return launch_fused2d<N, T, SF, 32, 8>(g, cf, b, cur, st);
+            default: return launch_fused2d<N, T, SF, 32, 16>(g, cf, b, cur, st);
+        }
+    }
+    static const Ops *ops(int prec) {
+        using B = Launch<LD2Q9, N, T, SF>;
+        static const Ops o = {9, 2, N, prec, 1, {K_FUSED, K_FUSED}, {&step, nullptr}, 3,
+                              {"fused 32x4", "fused 32x8", "fused 32x16", nullptr},
+                              &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C,
+                              int(sizeof(SF)), int(sizeof(T))};
+        return &o;
+    }
+};
+
+template <typename T, typename SF>
+const Ops *ops_fused2d(int N, int prec) {
+    switch (N) {
+        case 2: return Fused2DLaunch<2, T, SF>::ops(prec);
+        case 3: return Fused2DLaunch<3, T, SF>::ops(prec);
+        case 4: return Fused2DLaunch<4, T, SF>::ops(prec);
+        case 5: return Fused2DLaunch<5, T, SF>::ops(prec);
+        case 6: return Fused2DLaunch<6, T, SF>::ops(prec);
+        case 7: return Fused2DLaunch<7, T, SF>::ops(prec);
+        case 8: return Fused2DLaunch<8, T, SF>::ops(prec);
+        default: return nullptr;
+    }
+}
+
+}  // namespace nfe

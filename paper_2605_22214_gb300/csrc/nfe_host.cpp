@@ -87,6 +87,7 @@ struct nfe_sim {
     size_t fields_planes = 0;
     size_t device_bytes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int variant = -1;                 // tile shape; -1 until the autotuner has run
     bool profiling = false;
     std::vector<TimedLaunch> timed;
     std::vector<cudaEvent_t> event_pool;
@@ -164,23 +165,45 @@ cudaEvent_t get_event(nfe_sim *s) {
 }
 
 // one time step from buffer `cur`, optionally with events around each kernel
-nfe_status launch_step(nfe_sim *s, int cur, bool timed) {
-    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
-    if (timed) { e0 = get_event(s); e1 = get_event(s); e2 = get_event(s); CK(cudaEventRecord(e0, s->stream)); }
-    CK(s->ops->collide(s->geom, s->coef, s->buf, cur, s->stream));
-    cudaEvent_t e1b = nullptr;
-    if (timed) {
-        // the second interval starts where the first ends, with its own event
-        e1b = get_event(s);
-        CK(cudaEventRecord(e1, s->stream));
-        CK(cudaEventRecord(e1b, s->stream));
+nfe_status launch_step(nfe_sim *s, int cur, bool timed, int variant) {
+    for (int i = 0; i < s->ops->nk; ++i) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timed) { a = get_event(s); b = get_event(s); CK(cudaEventRecord(a, s->stream)); }
+        CK(s->ops->kern[i](s->geom, s->coef, s->buf, cur, s->stream, variant));
+        if (timed) {
+            CK(cudaEventRecord(b, s->stream));
+            s->timed.push_back({s->ops->kinds[i], a, b});
+        }
     }
-    CK(s->ops->ch_update(s->geom, s->coef, s->buf, cur, s->stream));
-    if (timed) {
-        CK(cudaEventRecord(e2, s->stream));
-        s->timed.push_back({K_COLLIDE, e0, e1});
-        s->timed.push_back({K_CH, e1b, e2});
+    return NFE_OK;
+}
+
+// Pick the fastest tile shape by timing each variant on the current state.  A
+// step reads buffer cur and writes buffer 1 - cur, so the state is untouched.
+nfe_status autotune(nfe_sim *s) {
+    if (s->variant >= 0) return NFE_OK;
+    if (s->ops->nvariants <= 1) { s->variant = 0; return NFE_OK; }
+    cudaEvent_t a = get_event(s), b = get_event(s);
+    double best = 1e300;
+    int best_v = 0;
+    const int reps = s->geom.n > (1 << 22) ? 3 : 10;
+    for (int v = 0; v < s->ops->nvariants; ++v) {
+        nfe_status st;
+        for (int r = 0; r < 2; ++r)
+            if ((st = launch_step(s, s->buf.cur, false, v)) != NFE_OK) return st;
+        CK(cudaEventRecord(a, s->stream));
+        for (int r = 0; r < reps; ++r)
+            if ((st = launch_step(s, s->buf.cur, false, v)) != NFE_OK) return st;
+        CK(cudaEventRecord(b, s->stream));
+        CK(cudaEventSynchronize(b));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, a, b));
+        if (ms < best) { best = ms; best_v = v; }
     }
+    s->event_pool.push_back(a);
+    s->event_pool.push_back(b);
+    CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
+    s->variant = best_v;
     return NFE_OK;
 }
 
@@ -188,8 +211,8 @@ nfe_status ensure_graph(nfe_sim *s, int cur) {
     if (s->graph[cur]) return NFE_OK;
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal));
-    nfe_status st = launch_step(s, cur, false);
-    if (st == NFE_OK) st = launch_step(s, 1 - cur, false);
+    nfe_status st = launch_step(s, cur, false, s->variant);
+    if (st == NFE_OK) st = launch_step(s, 1 - cur, false, s->variant);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
     if (st != NFE_OK) { if (g) cudaGraphDestroy(g); return st; }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
@@ -374,9 +397,10 @@ nfe_status nfe_step(nfe_sim *s, int64_t nsteps) {
     nfe_status st = check_sim(s);
     if (st != NFE_OK) return st;
     if (nsteps < 0) return fail(NFE_EINVAL, "nsteps < 0");
+    if (nsteps > 0 && (st = autotune(s)) != NFE_OK) return st;
     if (s->profiling) {
         for (int64_t i = 0; i < nsteps; ++i) {
-            if ((st = launch_step(s, s->buf.cur, true)) != NFE_OK) return st;
+            if ((st = launch_step(s, s->buf.cur, true, s->variant)) != NFE_OK) return st;
             s->buf.cur ^= 1;
             s->step++;
         }
@@ -389,7 +413,7 @@ nfe_status nfe_step(nfe_sim *s, int64_t nsteps) {
         s->step += 2;
     }
     if (nsteps == 1) {
-        if ((st = launch_step(s, s->buf.cur, false)) != NFE_OK) return st;
+        if ((st = launch_step(s, s->buf.cur, false, s->variant)) != NFE_OK) return st;
         s->buf.cur ^= 1;
         s->step++;
     }
@@ -473,7 +497,9 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
     out->sites = s->geom.n;
     out->omega_stab = s->tab.omega;
     out->factor_residual = s->tab.residual;
-    out->kernels_per_step = 2;
+    out->kernels_per_step = s->ops->nk;
+    out->variant = s->variant;
+    out->nvariants = s->ops->nvariants;
     out->min_bytes_per_site = 2.0 * ((s->ops->Q - 1) * s->ops->f_elem_bytes + (s->N - 1) * s->ops->c_elem_bytes);
     out->state_bytes = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
     out->device_bytes = s->device_bytes;
@@ -508,6 +534,16 @@ nfe_status nfe_set_state(nfe_sim *s, const void *host, size_t bytes) {
                        cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_set_variant(nfe_sim *s, int variant) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (variant >= s->ops->nvariants) return fail(NFE_EINVAL, "variant %d >= %d", variant, s->ops->nvariants);
+    CK(cudaStreamSynchronize(s->stream));
+    for (auto &g : s->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    s->variant = variant < 0 ? -1 : variant;
     return NFE_OK;
 }
 

@@ -63,12 +63,18 @@ struct Buffers {
 
 // Launchers exported by the lattice translation units.  Each returns
 // cudaSuccess or the launch error.
+using StepKernel = cudaError_t (*)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t,
+                                   int variant);
+constexpr int kMaxVariants = 4;
 struct Ops {
     int Q, D, N, prec;
-    // one time step: state in buffers cur -> 1 - cur (does not flip cur);
-    // `kind` receives the kernel kinds launched (for profiling), in order.
-    cudaError_t (*collide)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
-    cudaError_t (*ch_update)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
+    // one time step = nk kernels, state in buffers cur -> 1 - cur (cur is not flipped);
+    // `variant` selects a tile shape (0 .. nvariants-1)
+    int nk;
+    int kinds[2];
+    StepKernel kern[2];
+    int nvariants;
+    const char *variant_names[kMaxVariants];
     // fields (C, v, P, Fs in FP64) of the state in buffer cur
     cudaError_t (*moments)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
     // FP64 reductions of bufs.fields (+ f and C finiteness) into bufs.diag

@@ -489,14 +489,14 @@ inline unsigned blocks_for(long long n, int bs) { return unsigned((n + bs - 1) /
 
 template <class L, int N, typename T, typename SF>
 struct Launch {
-    static cudaError_t collide(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
+    static cudaError_t collide(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_collide<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
             g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
             static_cast<const T *>(b.C[cur]), static_cast<T *>(b.v), static_cast<T *>(b.S));
         return cudaGetLastError();
     }
-    static cudaError_t ch_update(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
+    static cudaError_t ch_update(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_ch<L, N, T><<<blocks_for(g.n, 256), 256, 0, st>>>(
             g, cf, static_cast<const T *>(b.C[cur]), static_cast<const T *>(b.v),
@@ -529,9 +529,11 @@ struct Launch {
         k_pack_C<T><<<blocks_for(total, 256), 256, 0, st>>>(total, in, static_cast<T *>(b.C[cur]));
         return cudaGetLastError();
     }
+    // generic two-kernel step (collide+stream, then the Cahn-Hilliard gather)
     static const Ops *ops(int prec) {
-        static const Ops o = {L::Q, L::D, N, prec, &collide, &ch_update, &moments, &reduce,
-                              &init_f, &unpack_f, &pack_C, int(sizeof(SF)), int(sizeof(T))};
+        static const Ops o = {L::Q, L::D, N, prec, 2, {K_COLLIDE, K_CH}, {&collide, &ch_update}, 1,
+                              {"two-kernel", nullptr, nullptr, nullptr},
+                              &moments, &reduce, &init_f, &unpack_f, &pack_C, int(sizeof(SF)), int(sizeof(T))};
         return &o;
     }
 };

@@ -177,8 +177,25 @@ def test_checkpoint_roundtrip_and_graph_replay_are_bitwise():
         c = s.get_state()
         prof = s.profile_read()
     assert np.array_equal(a, b) and np.array_equal(a, c)
-    assert set(prof) == {"collide_stream", "ch_update"}
-    assert prof["collide_stream"][0] == 11
+    assert set(prof) == {"fused_step"}
+    assert prof["fused_step"][0] == 11
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tile_variants_are_bitwise_identical(precision):
+    # every tile shape of the fused D2Q9 step computes each site the same way
+    for p in (W.lens_2d(nx=70, ny=45, radius=9), W.spinodal_2d(nx=33, ny=29, seed=8)):
+        states = []
+        with nfe.Sim(p, precision) as s:
+            nv = s.info()["nvariants"]
+            assert nv == 3
+            for v in range(nv):
+                s.set_fields(p["C0"])
+                s.set_variant(v)
+                s.step(25)
+                states.append(s.get_state())
+        for st in states[1:]:
+            assert np.array_equal(st, states[0])
 
 
 def test_nonfinite_flag_reported():
