@@ -189,9 +189,9 @@ def run_nfe(args):
         K = args.steps if prec == "fp32" else max(1, args.steps // 4)
         sim = nfe.Sim(p, prec, stream=stream.cuda_stream)
         sim.set_fields(p["C0"])
-        info = sim.info()
         clocks = Clocks(local) if prec == "fp32" else None
         ms_total, wall = timed_steps(sim, K, args.warmup, clocks)
+        info = sim.info()
         ms_total = max_over_ranks(ms_total)
         ms_step = ms_total / K
         kt = kernel_times(sim, min(K, 500))
@@ -225,12 +225,14 @@ def run_nfe(args):
         # dominant kernel and its compulsory bytes per site (each array it touches once)
         dom = max(kt, key=lambda k: kt[k][1])
         Q, D = 9, 2
-        if dom == "collide_stream":
+        if dom == "fused_step":
+            bps = r["info"]["min_bytes_per_site"]
+        elif dom == "collide_stream":
             bps = prec_bytes * ((Q - 1) + (N - 1) + (Q - 1) + D + (N - 1))
         else:
             bps = prec_bytes * ((N - 1) + D + (N - 1) + (N - 1))
         ach = bps * n / (kt[dom][1] * 1e-3) / 1e9
-        return dict(bound="hbm", kernel=dom, bytes_per_site=bps, achieved=round(ach, 1), peak=hbm,
+        return dict(bound="hbm", kernel=dom, variant=r["info"]["variant"], bytes_per_site=bps, achieved=round(ach, 1), peak=hbm,
                     unit="GB/s", frac=round(ach / hbm, 4), peak_source=peak_kind, traffic=None,
                     kernel_ms=round(kt[dom][1], 5))
 
