@@ -171,27 +171,68 @@ __device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N],
     vx = jx + T(0.5) * Fx;
     vy = jy + T(0.5) * Fy;
     const T w0 = T(4) / T(9);
-    P = (sumf - T(1.5) * w0 * (vx * vx + vy * vy)) / (T(3) * (T(1) - w0));
+    P = (sumf - T(1.5) * w0 * (vx * vx + vy * vy)) * T(1.0 / (3.0 * (1.0 - 4.0 / 9.0)));
 }
 
+// One tile of the fused step (phases 1-4 above).  `smem` holds
+// Fused2DShape<N, T, TX, TY>::BYTES bytes; all TX * TY threads of the CTA call it.
 template <int N, typename T, typename SF, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
-k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag) {
+__device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, const SF *__restrict__ fin,
+                                             SF *__restrict__ fout, const T *__restrict__ Cin,
+                                             T *__restrict__ Cout, int *__restrict__ flag,
+                                             int x0, int y0, unsigned char *smem) {
     using Sh = Fused2DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     using RB = typename Sh::RB;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sA = reinterpret_cast<T *>(smem_raw);
+    static_assert(Sh::NHALO <= TX * TY, "one ring site per thread at most");
+    T *sA = reinterpret_cast<T *>(smem);
     T *sB = sA + Sh::A_VALUES;
     const int nx = g.nx, ny = g.ny;
-    const size_t n = size_t(g.n);
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int n = int(g.n);
     const int tid = threadIdx.x;
     // uniform per CTA: does the tile plus its 2-ring cross the domain edge?
     const bool edge = (x0 - 2 < 0) || (x0 + TX + 2 > nx) || (y0 - 2 < 0) || (y0 + TY + 2 > ny);
 
+    // ---- own site and ring site of this thread; start their f loads first ----
+    const int tx = tid % TX, ty = tid / TX;
+    const int gx0 = x0 + tx, gy0 = y0 + ty;
+    const bool own = gx0 < nx && gy0 < ny;             // ragged far edge: duplicates only
+    const int sx = edge ? imod(gx0, nx) : gx0;         // wrapped (periodic duplicates)
+    const int sy = edge ? imod(gy0, ny) : gy0;
+    const int s0 = sx + nx * sy;
+    T f[9];
+    f[0] = T(0);
+#pragma unroll
+    for (int k = 1; k < 9; ++k) f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv);
+
+    // ring of the tile+1 region: top row, bottom row, then left and right columns
+    int bx = 0, by = 0;
+    const bool has_ring = tid < Sh::NHALO;
+    if (tid < Sh::BX) { bx = tid; by = 0; }
+    else if (tid < 2 * Sh::BX) { bx = tid - Sh::BX; by = Sh::BY - 1; }
+    else { const int r = tid - 2 * Sh::BX; by = 1 + (r >> 1); bx = (r & 1) ? Sh::BX - 1 : 0; }
+    const int hx = x0 + bx - 1, hy = y0 + by - 1;
+    bool ring_ok = has_ring;
+    unsigned hwall = 0;
+    int hs = hx + nx * hy;
+    if (edge && has_ring) {
+        if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) ring_ok = false;
+        hs = imod(hx, nx) + nx * imod(hy, ny);
+#pragma unroll
+        for (int k = 1; k < 9; ++k) {
+            const int xx = hx + LD2Q9::ex(k), yy = hy + LD2Q9::ey(k);
+            if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) hwall |= 1u << k;
+        }
+    }
+    T hf[9];
+    hf[0] = T(0);
+    if (ring_ok) {
+#pragma unroll
+        for (int k = 1; k < 9; ++k) hf[k] = FStore<SF, T>::load(fin + (k - 1) * n + hs, LD2Q9::w(k), cf.finv);
+    }
+
     // ---- phase 1: C and E_B on tile + 2-ring ---------------------------------
+#pragma unroll 1
     for (int i = tid; i < Sh::ACOUNT; i += TX * TY) {
         const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
         int gx = x0 + lx - 2, gy = y0 + ly - 2;
@@ -216,12 +257,6 @@ k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
     __syncthreads();
 
     // ---- phase 2a: own site ---------------------------------------------------
-    const int tx = tid % TX, ty = tid / TX;
-    const int gx0 = x0 + tx, gy0 = y0 + ty;
-    const bool own = gx0 < nx && gy0 < ny;             // ragged far edge: duplicates only
-    const int sx = edge ? imod(gx0, nx) : gx0;         // wrapped (periodic duplicates)
-    const int sy = edge ? imod(gy0, ny) : gy0;
-    const int s0 = sx + nx * sy;
     // wall mask of the own site: bit k set when x + e_k is beyond a wall
     unsigned wall0 = 0;
     if (edge) {
@@ -231,16 +266,12 @@ k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
             if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) wall0 |= 1u << k;
         }
     }
-    T f[9];
     T c[N], lap[N], gxv[N], gyv[N], gEx, gEy;
     T S[N - 1], Fx, Fy, vx, vy, P, sumf;
     {
         const int ia = (ty + 2) * Sh::AX + (tx + 2);
         if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
         else      stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
-        f[0] = T(0);
-#pragma unroll
-        for (int k = 1; k < 9; ++k) f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv);
         site_physics<N, T>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
         T rec[RB::NVP];
 #pragma unroll
@@ -251,37 +282,13 @@ k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         srec_store<T, 2 * N>(sB, Sh::BCOUNT, (ty + 1) * Sh::BX + (tx + 1), rec);
     }
 
-    // ---- phase 2b: the 1-ring around the tile ---------------------------------
-    for (int h = tid; h < Sh::NHALO; h += TX * TY) {
-        // enumerate the ring: top row, bottom row, then left and right columns
-        int bx, by;
-        if (h < Sh::BX) { bx = h; by = 0; }
-        else if (h < 2 * Sh::BX) { bx = h - Sh::BX; by = Sh::BY - 1; }
-        else { const int r = h - 2 * Sh::BX; by = 1 + (r >> 1); bx = (r & 1) ? Sh::BX - 1 : 0; }
-        const int hx = x0 + bx - 1, hy = y0 + by - 1;
-        bool beyond = false;
-        unsigned wall = 0;
-        int wx_ = hx, wy_ = hy;
-        if (edge) {
-            if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) beyond = true;
-            wx_ = imod(hx, nx);
-            wy_ = imod(hy, ny);
-#pragma unroll
-            for (int k = 1; k < 9; ++k) {
-                const int xx = hx + LD2Q9::ex(k), yy = hy + LD2Q9::ey(k);
-                if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) wall |= 1u << k;
-            }
-        }
-        if (beyond) continue;          // sources beyond a wall are replaced by bounce-back
-        const int s = wx_ + nx * wy_;
+    // ---- phase 2b: the 1-ring around the tile (sites beyond a wall are skipped:
+    //      sources there are replaced by bounce-back) ---------------------------
+    if (ring_ok) {
         T hc[N], hl[N], hgx[N], hgy[N], hEx, hEy;
         const int ia = (by + 1) * Sh::AX + (bx + 1);
-        if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall, hc, hl, hgx, hgy, hEx, hEy);
+        if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
         else      stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
-        T hf[9];
-        hf[0] = T(0);
-#pragma unroll
-        for (int k = 1; k < 9; ++k) hf[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD2Q9::w(k), cf.finv);
         T hS[N - 1], hFx, hFy, hvx, hvy, hP, hsum;
         site_physics<N, T>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
         T rec[RB::NVP];
@@ -299,13 +306,14 @@ k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         relaxation<N, T>(cf, c, op, om);
         const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
         const T vv = vx * vx + vy * vy, vF = vx * Fx + vy * Fy;
+        const T base = T(3) * P - T(1.5) * vv;
 #pragma unroll
         for (int k = 1; k < 9; k += 2) {
             const int kb = k + 1;
             const T wk = T(LD2Q9::w(k));
             const T eu = T(LD2Q9::ex(k)) * vx + T(LD2Q9::ey(k)) * vy;
             const T eF = T(LD2Q9::ex(k)) * Fx + T(LD2Q9::ey(k)) * Fy;
-            const T eqp = wk * (T(3) * P + T(4.5) * eu * eu - T(1.5) * vv);
+            const T eqp = wk * (base + T(4.5) * eu * eu);
             const T eqm = wk * (T(3) * eu);
             const T Fp = wk * (T(9) * eu * eF - T(3) * vF);
             const T Fm = wk * (T(3) * eF);
@@ -317,15 +325,15 @@ k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
             const T pkb = f[kb] + sym - anti;
             if (!edge) {
                 const int dk = LD2Q9::ex(k) + nx * LD2Q9::ey(k);
-                FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), pk, LD2Q9::w(k), cf.finv);
-                FStore<SF, T>::store(fout + (kb - 1) * n + (s0 - dk), pkb, LD2Q9::w(kb), cf.finv);
+                FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), pk, LD2Q9::w(k), cf.fscale);
+                FStore<SF, T>::store(fout + (kb - 1) * n + (s0 - dk), pkb, LD2Q9::w(kb), cf.fscale);
             } else {
-                if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, pk, LD2Q9::w(kb), cf.finv);
+                if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, pk, LD2Q9::w(kb), cf.fscale);
                 else FStore<SF, T>::store(fout + (k - 1) * n + (wrap(sx + LD2Q9::ex(k), nx) + nx * wrap(sy + LD2Q9::ey(k), ny)),
-                                          pk, LD2Q9::w(k), cf.finv);
-                if ((wall0 >> kb) & 1u) FStore<SF, T>::store(fout + (k - 1) * n + s0, pkb, LD2Q9::w(k), cf.finv);
+                                          pk, LD2Q9::w(k), cf.fscale);
+                if ((wall0 >> kb) & 1u) FStore<SF, T>::store(fout + (k - 1) * n + s0, pkb, LD2Q9::w(k), cf.fscale);
                 else FStore<SF, T>::store(fout + (kb - 1) * n + (wrap(sx - LD2Q9::ex(k), nx) + nx * wrap(sy - LD2Q9::ey(k), ny)),
-                                          pkb, LD2Q9::w(kb), cf.finv);
+                                          pkb, LD2Q9::w(kb), cf.fscale);
             }
         }
     }
@@ -372,6 +380,14 @@ k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         }
         if (bad) atomicOr(flag, 1);
     }
+}
+
+template <int N, typename T, typename SF, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
+          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused2d_tile<N, T, SF, TX, TY>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
 }
 
 template <int N, typename T, typename SF, int TX, int TY>

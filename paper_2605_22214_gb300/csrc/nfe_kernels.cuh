@@ -75,7 +75,7 @@ template <typename T> struct FStore<float, T> {
 };
 template <> struct FStore<__half, float> {
     __device__ static float load(const __half *p, double w, float finv) { return __half2float(*p) * (float(w) * finv); }
-    __device__ static void store(__half *p, float v, double w, float finv) { *p = __float2half_rn(v * (float(1.0 / w) / finv)); }
+    __device__ static void store(__half *p, float v, double w, float fscale) { *p = __float2half_rn(v * (float(1.0 / w) * fscale)); }
 };
 template <> struct FStore<__nv_bfloat16, float> {
     __device__ static float load(const __nv_bfloat16 *p, double w, float) { return __bfloat162float(*p) * float(w); }
@@ -306,7 +306,7 @@ k_collide(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
     const T v0 = j0 + T(0.5) * F0, v1 = j1 + T(0.5) * F1, v2 = j2 + T(0.5) * F2;
     const T vv = v0 * v0 + v1 * v1 + v2 * v2;
     const T w0 = T(L::w(0));
-    const T P = (sumf - T(1.5) * w0 * vv) / (T(3) * (T(1) - w0));
+    const T P = (sumf - T(1.5) * w0 * vv) * T(1.0 / (3.0 * (1.0 - L::w(0))));
     const T vF = v0 * F0 + v1 * F1 + v2 * F2;
     T op, om;
     relaxation<N, T>(cf, st.c, op, om);
@@ -331,10 +331,10 @@ k_collide(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         const T pkb = f[kb] + sym - anti;    // post-collision f_kbar
         // push: f_k(x + e_k, t+1) = pk, or bounce-back into f_kbar(x) at a wall (Eq. 44)
         const int jk = st.nb[k], jkb = st.nb[kb];
-        if (jk >= 0) FStore<SF, T>::store(fout + (k - 1) * n + jk, pk, L::w(k), cf.finv);
-        else         FStore<SF, T>::store(fout + (kb - 1) * n + s, pk, L::w(kb), cf.finv);
-        if (jkb >= 0) FStore<SF, T>::store(fout + (kb - 1) * n + jkb, pkb, L::w(kb), cf.finv);
-        else          FStore<SF, T>::store(fout + (k - 1) * n + s, pkb, L::w(k), cf.finv);
+        if (jk >= 0) FStore<SF, T>::store(fout + (k - 1) * n + jk, pk, L::w(k), cf.fscale);
+        else         FStore<SF, T>::store(fout + (kb - 1) * n + s, pk, L::w(kb), cf.fscale);
+        if (jkb >= 0) FStore<SF, T>::store(fout + (kb - 1) * n + jkb, pkb, L::w(kb), cf.fscale);
+        else          FStore<SF, T>::store(fout + (k - 1) * n + s, pkb, L::w(k), cf.fscale);
     }
     vout[s] = v0;
     vout[n + s] = v1;
@@ -426,7 +426,7 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     const T v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1]);
     const T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2]);
     const T w0 = T(L::w(0));
-    const T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) / (T(3) * (T(1) - w0));
+    const T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) * T(1.0 / (3.0 * (1.0 - L::w(0))));
 #pragma unroll
     for (int a = 0; a < N; ++a) {
         out[size_t(cf.uidx[a]) * n + s] = double(st.c[a]);
@@ -454,7 +454,7 @@ __global__ void k_init_f(Geom g, Coef<T> cf, const double *__restrict__ v, SF *_
     for (int k = 1; k < L::Q; ++k) {
         const double eu = L::ex(k) * a0 + L::ey(k) * a1 + L::ez(k) * a2;
         const double sk = L::w(k) * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu);
-        FStore<SF, T>::store(f + (k - 1) * n + s, T(sk), L::w(k), cf.finv);
+        FStore<SF, T>::store(f + (k - 1) * n + s, T(sk), L::w(k), cf.fscale);
     }
 }
 
