@@ -245,6 +245,43 @@ def run_nfe(args):
                     kernels={k: dict(launches=c, avg_ms=round(t, 5)) for k, (c, t) in r["kt"].items()},
                     )
 
+    # the same time step on other sizes and storage formats (context for the roofline)
+    extras = []
+    if not args.no_extras:
+        cases = [("spinodal 512x512 N=4", W.spinodal_2d(seed=1002), "f16", args.steps // 4, True),
+                 ("spinodal 512x512 N=4", W.spinodal_2d(seed=1002), "bf16", args.steps // 4, True),
+                 ("spinodal 4096x4096 N=4", W.spinodal_2d(nx=4096, ny=4096, seed=1012), "fp32", 60, False),
+                 ("spinodal 4096x4096 N=4", W.spinodal_2d(nx=4096, ny=4096, seed=1012), "f16", 60, False),
+                 ("spinodal 4096x4096 N=4", W.spinodal_2d(nx=4096, ny=4096, seed=1012), "fp64", 10, False),
+                 ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "fp32", 20, False),
+                 ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "bf16", 20, False)]
+        for name, q, prec, K, fl in cases:
+            nq = q["nx"] * q["ny"] * q["nz"]
+            with nfe.Sim(q, prec, stream=stream.cuda_stream, scale_exp=10) as sx:
+                sx.set_fields(q["C0"])
+                if fl:
+                    ms_total, _ = timed_steps(sx, K, 5)
+                    ms = ms_total / K
+                else:
+                    with torch.cuda.stream(stream):
+                        sx.step(3)
+                        a = torch.cuda.Event(enable_timing=True)
+                        bb = torch.cuda.Event(enable_timing=True)
+                        a.record(stream)
+                        sx.step(K)
+                        bb.record(stream)
+                    bb.synchronize()
+                    ms = a.elapsed_time(bb) / K
+                inf = sx.info()
+            mlups = nq / (ms * 1e-3) / 1e6
+            eff = inf["min_bytes_per_site"] * nq / (ms * 1e-3) / 1e9
+            extras.append(dict(workload=name, precision=prec, sites=nq, ms_per_step=round(ms, 4),
+                               mlups=round(mlups, 1), mlups_x_n=round(mlups * q["N"], 1),
+                               min_bytes_per_site=inf["min_bytes_per_site"], effective_gbs=round(eff, 1),
+                               effective_frac=round(eff / hbm, 4), kernels_per_step=inf["kernels_per_step"],
+                               l2="flushed before every step" if fl else "working set > L2, steps back to back"))
+            del q
+
     s32 = path_summary(r32)
     s64 = path_summary(results["fp64"])
     s64["roofline"] = roofline(results["fp64"])
@@ -274,6 +311,7 @@ def run_nfe(args):
                 "d2h_bytes_per_step": nbytes, "steps": Ke,
                 "how": "nfe_set_state (pinned host -> device), nfe_step(1), nfe_get_state (device -> pinned host)"},
         "gpu_launches": r32["info"]["kernels_per_step"] * r32["K"],
+        "extras": extras,
         "clocks": r32["clocks"].summary() if r32["clocks"] is not None else None,
     }
     for r in results.values():
@@ -360,6 +398,7 @@ def main():
     ap.add_argument("--impl", choices=["nfe", "reference"], default="nfe")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other sizes and storage formats")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -232,27 +232,42 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     }
 
     // ---- phase 1: C and E_B on tile + 2-ring ---------------------------------
-#pragma unroll 1
-    for (int i = tid; i < Sh::ACOUNT; i += TX * TY) {
-        const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
-        int gx = x0 + lx - 2, gy = y0 + ly - 2;
-        if (edge) {
-            // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
-            // such entries are never used by a real site's stencil
-            gx = g.wx ? min(max(gx, 0), nx - 1) : imod(gx, nx);
-            gy = g.wy ? min(max(gy, 0), ny - 1) : imod(gy, ny);
+    // every load of the phase is issued before any of them is used
+    constexpr int NT = TX * TY;
+    constexpr int ITER = (Sh::ACOUNT + NT - 1) / NT;
+    T cl[ITER][N - 1];
+#pragma unroll
+    for (int it = 0; it < ITER; ++it) {
+        const int i = tid + it * NT;
+        if (i < Sh::ACOUNT) {
+            const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
+            int gx = x0 + lx - 2, gy = y0 + ly - 2;
+            if (edge) {
+                // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
+                // such entries are never used by a real site's stencil
+                gx = g.wx ? min(max(gx, 0), nx - 1) : imod(gx, nx);
+                gy = g.wy ? min(max(gy, 0), ny - 1) : imod(gy, ny);
+            }
+            const int s = gx + nx * gy;
+#pragma unroll
+            for (int a = 0; a < N - 1; ++a) cl[it][a] = Cin[a * n + s];
         }
-        const int s = gx + nx * gy;
-        T rec[RA::NVP];
-        T cc[N];
-        T rest = T(0);
+    }
 #pragma unroll
-        for (int a = 0; a < N - 1; ++a) { cc[a] = Cin[a * n + s]; rec[a] = cc[a]; rest += cc[a]; }
-        cc[N - 1] = T(1) - rest;
-        rec[N - 1] = bulk_energy<N, T>(cc, cf);
+    for (int it = 0; it < ITER; ++it) {
+        const int i = tid + it * NT;
+        if (i < Sh::ACOUNT) {
+            T rec[RA::NVP];
+            T cc[N];
+            T rest = T(0);
 #pragma unroll
-        for (int a = N; a < RA::NVP; ++a) rec[a] = T(0);
-        srec_store<T, N>(sA, Sh::ACOUNT, i, rec);
+            for (int a = 0; a < N - 1; ++a) { cc[a] = cl[it][a]; rec[a] = cc[a]; rest += cc[a]; }
+            cc[N - 1] = T(1) - rest;
+            rec[N - 1] = bulk_energy<N, T>(cc, cf);
+#pragma unroll
+            for (int a = N; a < RA::NVP; ++a) rec[a] = T(0);
+            srec_store<T, N>(sA, Sh::ACOUNT, i, rec);
+        }
     }
     __syncthreads();
 
@@ -382,8 +397,11 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     }
 }
 
+// Minimum resident CTAs per SM requested from the register allocator.
+template <typename T, int NT> struct Fused2DOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 8 : NT <= 256 ? 4 : 2) : 1; };
+
 template <int N, typename T, typename SF, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+__global__ void __launch_bounds__(TX * TY, (Fused2DOcc<T, TX * TY>::value))
 k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
           const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
