@@ -207,6 +207,35 @@ nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double 
 const char *nfe_status_string(nfe_status s);
 const char *nfe_last_error(void);
 
+/* Allocation-free FP64 statistics of device-resident fields.  The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc, such
+ * as code running inside another runtime's memory pool or a fixed arena, where
+ * an extra device allocation would fail or escape the owner's accounting.
+ *
+ * d_planes: device, nplanes x n doubles, plane p at d_planes[p * n] (for
+ * example the C, v or P arrays of nfe_fields copied to the device).  d_out:
+ * device, 4 x nplanes doubles; for plane p it receives the sum, the sum of
+ * absolute values, the largest absolute value and the smallest value, at
+ * d_out[4 p + 0 .. 3].  Work is queued on cuda_stream (NULL = legacy default
+ * stream) and the call returns without waiting.
+ *
+ * It allocates nothing: the per-block partial sums live in one static device
+ * array of the library (512 blocks x NFE_STATS_MAX_PLANES planes x 4 doubles,
+ * 256 KiB), held by every GPU that loads the library until the process
+ * exits.  Every call writes all the partials it later reads, so nothing has
+ * to start at zero, but all calls share that array: calls whose work overlaps
+ * on one GPU (for example calls queued on two different streams) race and
+ * may return wrong results.  Each GPU has its own copy of the array.  The
+ * first call on each device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.
+ * Errors: NFE_EINVAL when nplanes is outside 1..NFE_STATS_MAX_PLANES, n < 1
+ * or a pointer is NULL (nothing is launched); NFE_ECUDA when the address
+ * lookup or a launch fails.  The message is in nfe_last_error(). */
+#define NFE_STATS_MAX_PLANES 16
+nfe_status nfe_field_stats_static(int nplanes, int64_t n, const double *d_planes, double *d_out,
+                                  void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,7 +33,7 @@ STATUS = {0: "NFE_OK", 1: "NFE_EINVAL", 2: "NFE_ENOMEM", 3: "NFE_ECUDA", 4: "NFE
 EXPORTS = ["nfe_create", "nfe_set_fields", "nfe_step", "nfe_sync", "nfe_fields", "nfe_populations",
            "nfe_diagnostics", "nfe_get_state", "nfe_set_state", "nfe_get_info", "nfe_profile_enable",
            "nfe_profile_read", "nfe_destroy", "nfe_status_string", "nfe_last_error",
-           "nfe_bulk_potential_host", "nfe_set_variant"]
+           "nfe_bulk_potential_host", "nfe_set_variant", "nfe_field_stats_static"]
 
 
 class nfe_grid(C.Structure):
@@ -97,6 +97,7 @@ def load():
         "nfe_get_info": ([P, C.POINTER(nfe_info)], C.c_int),
         "nfe_profile_enable": ([P, C.c_int], C.c_int),
         "nfe_set_variant": ([P, C.c_int], C.c_int),
+        "nfe_field_stats_static": ([C.c_int, C.c_int64, P, P, P], C.c_int),
         "nfe_profile_read": ([P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_char_p),
                               C.POINTER(C.c_int64), dp], C.c_int),
         "nfe_destroy": ([P], None),
@@ -242,6 +243,12 @@ def nfe_profile_read(h):
 def nfe_destroy(h):
     if h:
         load().nfe_destroy(h)
+
+
+def nfe_field_stats_static(nplanes, n, d_planes_ptr, d_out_ptr, stream=None):
+    """Allocation-free FP64 sum / sum|.| / max|.| / min of device planes (raw device pointers)."""
+    _check(load().nfe_field_stats_static(int(nplanes), int(n), C.c_void_p(d_planes_ptr),
+                                         C.c_void_p(d_out_ptr), stream))
 
 
 def nfe_status_string(status):

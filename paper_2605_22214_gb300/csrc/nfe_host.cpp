@@ -60,6 +60,15 @@ const Ops *select_ops(int lattice, int N, int prec) {
     return nullptr;
 }
 
+}  // namespace
+
+nfe_status nfe::set_error(nfe_status s, const char *msg) {
+    g_err = msg ? msg : "";
+    return s;
+}
+
+namespace {
+
 struct TimedLaunch {
     int kind;
     cudaEvent_t a, b;

@@ -103,6 +103,9 @@ const Ops *ops_d3q19_bf16(int N);
 //  [0, N) mass, [N, N+3) momentum, [N+3, N+6) force sum, [N+6, N+9) |force| sum,
 //  [N+9, 2N+9) max |C|, [2N+9, 3N+9) min C, 3N+9 max speed, 3N+10 nonfinite.
 __host__ __device__ constexpr int diag_count(int N) { return 3 * N + 11; }
+
+// Records `msg` as the calling thread's last error (nfe_last_error) and returns s.
+nfe_status set_error(nfe_status s, const char *msg);
 constexpr int kReduceBlocks = 1024;
 
 }  // namespace nfe
