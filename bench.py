@@ -282,6 +282,10 @@ def run_nfe(args):
                                l2="flushed before every step" if fl else "working set > L2, steps back to back"))
             del q
 
+    batched = None
+    if not args.no_extras:
+        batched = batch_sweep_measure(nfe, torch, stream, args.batch_steps)
+
     s32 = path_summary(r32)
     s64 = path_summary(results["fp64"])
     s64["roofline"] = roofline(results["fp64"])
@@ -312,6 +316,7 @@ def run_nfe(args):
                 "how": "nfe_set_state (pinned host -> device), nfe_step(1), nfe_get_state (device -> pinned host)"},
         "gpu_launches": r32["info"]["kernels_per_step"] * r32["K"],
         "extras": extras,
+        "batched": batched,
         "clocks": r32["clocks"].summary() if r32["clocks"] is not None else None,
     }
     for r in results.values():
@@ -322,6 +327,59 @@ def run_nfe(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def batch_sweep_measure(nfe, torch, stream, steps):
+    """The 512-simulation lens/Janus sweep (D2Q9, N in {3,4,5}, FP32): one persistent launch
+    for all steps, one batched launch per step, and one launch per simulation per step."""
+    sims = W.batch_sweep(512, seed=1005)
+    sites = sum(p["nx"] * p["ny"] for p in sims)
+    site_n = sum(p["nx"] * p["ny"] * p["N"] for p in sims)
+    out = {"workload": "512 D2Q9 lens/Janus simulations, edge in {64,96,128,192,256}, N in {3,4,5}, "
+                       "sigma ~ U(0.004, 0.012), seed 1005+i, FP32", "sites": sites, "steps": steps}
+    with nfe.Batch(sims, "fp32", stream=stream.cuda_stream) as bt:
+        for i, p in enumerate(sims):
+            bt.set_fields(i, p["C0"])
+        for mode, name in ((nfe.NFE_BATCH_PERSISTENT, "persistent"), (nfe.NFE_BATCH_PER_STEP, "per_step")):
+            bt.set_mode(mode)
+            with torch.cuda.stream(stream):
+                bt.step(4)
+                a = torch.cuda.Event(enable_timing=True)
+                e = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                bt.step(steps)
+                e.record(stream)
+            e.synchronize()
+            bt.sync()
+            ms = a.elapsed_time(e) / steps
+            out[name] = {"ms_per_step": round(ms, 4), "mlups": round(sites / (ms * 1e-3) / 1e6, 1),
+                         "mlups_x_n": round(site_n / (ms * 1e-3) / 1e6, 1)}
+        out["info"] = bt.info()
+    # the same jobs, one launch per simulation per step
+    singles = []
+    for p in sims:
+        s = nfe.Sim(p, "fp32", stream=stream.cuda_stream)
+        s.set_fields(p["C0"])
+        s.set_variant(1)
+        singles.append(s)
+    k = max(2, steps // 10)
+    with torch.cuda.stream(stream):
+        for s in singles:
+            s.step(1)
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            for s in singles:
+                s.step(1)
+        e.record(stream)
+    e.synchronize()
+    ms = a.elapsed_time(e) / k
+    out["one_launch_per_simulation"] = {"ms_per_step": round(ms, 4), "mlups": round(sites / (ms * 1e-3) / 1e6, 1),
+                                        "mlups_x_n": round(site_n / (ms * 1e-3) / 1e6, 1), "steps": k}
+    for s in singles:
+        s.close()
+    return out
 
 
 class _Null:
@@ -399,6 +457,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other sizes and storage formats")
+    ap.add_argument("--batch-steps", type=int, default=100)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

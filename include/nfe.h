@@ -207,6 +207,54 @@ nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double 
 const char *nfe_status_string(nfe_status s);
 const char *nfe_last_error(void);
 
+/* ---- Batched sweep of independent D2Q9 simulations (one persistent launch) ----
+ * Many small simulations of different grid sizes and component counts (the
+ * parameter sweeps of the lens and Janus benchmarks, Sec. IV A) advanced
+ * together.  Every simulation is a full nfe_sim internally; nfe_batch_step
+ * advances all of them by nsteps with ONE cooperative kernel launch (replayed
+ * from a CUDA graph) whose CTAs walk the (simulation, tile) work list and meet
+ * at a grid barrier between steps.  The barrier's wait is bounded: when it
+ * runs out (NFE_ETIMEOUT from nfe_batch_sync) the kernel returns early and the
+ * states are undefined, but the GPU context stays usable.
+ * Constraints: D2Q9 grids, N = 2..5, one precision for the whole batch
+ * (NFE_FP32 or NFE_FP64), params[i].cuda_stream ignored (params[0]'s is used). */
+typedef struct nfe_batch nfe_batch;
+
+typedef struct {
+    int nsims;
+    int64_t sites;                   /* total over all simulations */
+    int nitems;                      /* (simulation, tile) work items per step */
+    int grid;                        /* CTAs of the persistent launch */
+    int tile_x, tile_y;              /* tile shape chosen by the autotuner (0 before the first step) */
+    int graphs;                      /* 1 when launches are replayed from CUDA graphs */
+} nfe_batch_info;
+
+enum { NFE_BATCH_PERSISTENT = 0,   /* one cooperative launch for all nsteps (default) */
+       NFE_BATCH_PER_STEP = 1 };   /* one batched launch per step */
+
+/* grids, N and params are arrays of nsims entries (host).  Errors as nfe_create
+ * for each simulation, plus NFE_EUNSUPPORTED for D3Q19 or N > 5. */
+nfe_status nfe_batch_create(int nsims, const nfe_grid *grids, const int *N, const nfe_params *params,
+                            nfe_batch **out);
+/* As nfe_set_fields for simulation `sim` (0 .. nsims-1).  Resets its step counter. */
+nfe_status nfe_batch_set_fields(nfe_batch *b, int sim, const double *C, const double *v);
+/* Queue nsteps time steps of every simulation (asynchronous). */
+nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps);
+nfe_status nfe_batch_set_mode(nfe_batch *b, int mode);
+/* Wait; NFE_ETIMEOUT if a barrier wait ran out, NFE_ENONFINITE if a volume fraction
+ * of any simulation became NaN/Inf. */
+nfe_status nfe_batch_sync(nfe_batch *b);
+/* As nfe_fields / nfe_diagnostics for simulation `sim`.  Synchronise. */
+nfe_status nfe_batch_fields(nfe_batch *b, int sim, double *C, double *v, double *P);
+nfe_status nfe_batch_diagnostics(nfe_batch *b, int sim, nfe_diag *out);
+nfe_status nfe_batch_get_info(const nfe_batch *b, nfe_batch_info *out);
+/* Fault-injection hook for tests of the timeout path: the next persistent launch
+ * uses at most `spins` polls per barrier wait and its barriers wait for
+ * `extra` more CTAs than the grid has (extra > 0 makes every wait run out).
+ * spins <= 0 restores the default limit (about a second or more). */
+nfe_status nfe_batch_set_barrier_test(nfe_batch *b, int64_t spins, int extra);
+void nfe_batch_destroy(nfe_batch *b);
+
 /* Allocation-free FP64 statistics of device-resident fields.  The paper has no
  * counterpart: this is a service for callers that cannot call cudaMalloc, such
  * as code running inside another runtime's memory pool or a fixed arena, where

@@ -33,7 +33,11 @@ STATUS = {0: "NFE_OK", 1: "NFE_EINVAL", 2: "NFE_ENOMEM", 3: "NFE_ECUDA", 4: "NFE
 EXPORTS = ["nfe_create", "nfe_set_fields", "nfe_step", "nfe_sync", "nfe_fields", "nfe_populations",
            "nfe_diagnostics", "nfe_get_state", "nfe_set_state", "nfe_get_info", "nfe_profile_enable",
            "nfe_profile_read", "nfe_destroy", "nfe_status_string", "nfe_last_error",
-           "nfe_bulk_potential_host", "nfe_set_variant", "nfe_field_stats_static"]
+           "nfe_bulk_potential_host", "nfe_set_variant", "nfe_field_stats_static",
+           "nfe_batch_create", "nfe_batch_set_fields", "nfe_batch_step", "nfe_batch_set_mode",
+           "nfe_batch_sync", "nfe_batch_fields", "nfe_batch_diagnostics", "nfe_batch_get_info",
+           "nfe_batch_set_barrier_test", "nfe_batch_destroy"]
+NFE_BATCH_PERSISTENT, NFE_BATCH_PER_STEP = 0, 1
 
 
 class nfe_grid(C.Structure):
@@ -62,6 +66,11 @@ class nfe_info(C.Structure):
                 ("kernels_per_step", C.c_int), ("variant", C.c_int), ("nvariants", C.c_int),
                 ("min_bytes_per_site", C.c_double),
                 ("state_bytes", C.c_size_t), ("device_bytes", C.c_size_t)]
+
+
+class nfe_batch_info(C.Structure):
+    _fields_ = [("nsims", C.c_int), ("sites", C.c_int64), ("nitems", C.c_int), ("grid", C.c_int),
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("graphs", C.c_int)]
 
 
 class NfeError(RuntimeError):
@@ -98,6 +107,17 @@ def load():
         "nfe_profile_enable": ([P, C.c_int], C.c_int),
         "nfe_set_variant": ([P, C.c_int], C.c_int),
         "nfe_field_stats_static": ([C.c_int, C.c_int64, P, P, P], C.c_int),
+        "nfe_batch_create": ([C.c_int, C.POINTER(nfe_grid), C.POINTER(C.c_int), C.POINTER(nfe_params),
+                              C.POINTER(P)], C.c_int),
+        "nfe_batch_set_fields": ([P, C.c_int, dp, dp], C.c_int),
+        "nfe_batch_step": ([P, C.c_int64], C.c_int),
+        "nfe_batch_set_mode": ([P, C.c_int], C.c_int),
+        "nfe_batch_sync": ([P], C.c_int),
+        "nfe_batch_fields": ([P, C.c_int, dp, dp, dp], C.c_int),
+        "nfe_batch_diagnostics": ([P, C.c_int, C.POINTER(nfe_diag)], C.c_int),
+        "nfe_batch_get_info": ([P, C.POINTER(nfe_batch_info)], C.c_int),
+        "nfe_batch_set_barrier_test": ([P, C.c_int64, C.c_int], C.c_int),
+        "nfe_batch_destroy": ([P], None),
         "nfe_profile_read": ([P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_char_p),
                               C.POINTER(C.c_int64), dp], C.c_int),
         "nfe_destroy": ([P], None),
@@ -325,6 +345,80 @@ class Sim:
     def close(self):
         if self.h:
             nfe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Many independent D2Q9 simulations advanced by one persistent kernel launch."""
+
+    def __init__(self, plist, precision="fp32", stream=None):
+        self.plist = list(plist)
+        n = len(self.plist)
+        grids = (nfe_grid * n)(*[make_grid(p) for p in self.plist])
+        Ns = (C.c_int * n)(*[int(p["N"]) for p in self.plist])
+        self._params = [make_params(p, precision, stream) for p in self.plist]
+        params = (nfe_params * n)(*self._params)
+        h = C.c_void_p()
+        _check(load().nfe_batch_create(n, grids, Ns, params, C.byref(h)))
+        self.h = h
+        self._keep = (grids, Ns, params)
+
+    def _size(self, i):
+        p = self.plist[i]
+        return int(p["N"]), int(p["nx"]) * int(p["ny"]) * int(p["nz"]), (int(p["nz"]), int(p["ny"]), int(p["nx"]))
+
+    def set_fields(self, i, Cf, v=None):
+        N, n, _ = self._size(i)
+        Cf = np.ascontiguousarray(np.asarray(Cf, dtype=np.float64).reshape(N, n))
+        v = None if v is None else np.ascontiguousarray(np.asarray(v, dtype=np.float64).reshape(3, n))
+        _check(load().nfe_batch_set_fields(self.h, int(i), _dptr(Cf), _dptr(v)))
+
+    def step(self, nsteps=1):
+        _check(load().nfe_batch_step(self.h, int(nsteps)))
+
+    def set_mode(self, mode):
+        _check(load().nfe_batch_set_mode(self.h, int(mode)))
+
+    def sync(self):
+        _check(load().nfe_batch_sync(self.h))
+
+    def fields(self, i):
+        N, n, shape = self._size(i)
+        Cf, v, P = np.empty((N, n)), np.empty((3, n)), np.empty(n)
+        _check(load().nfe_batch_fields(self.h, int(i), _dptr(Cf), _dptr(v), _dptr(P)))
+        return Cf.reshape((N,) + shape), v.reshape((3,) + shape), P.reshape(shape)
+
+    def diagnostics(self, i):
+        d = nfe_diag()
+        _check(load().nfe_batch_diagnostics(self.h, int(i), C.byref(d)))
+        N = d.N
+        return dict(step=d.step, mass=np.array(d.mass[:N]), momentum=np.array(d.momentum[:]),
+                    force_sum=np.array(d.force_sum[:]), max_abs_C=np.array(d.max_abs_C[:N]),
+                    min_C=np.array(d.min_C[:N]), max_speed=d.max_speed, nonfinite=d.nonfinite)
+
+    def info(self):
+        i = nfe_batch_info()
+        _check(load().nfe_batch_get_info(self.h, C.byref(i)))
+        return {name: getattr(i, name) for name, _ in nfe_batch_info._fields_}
+
+    def set_barrier_test(self, spins, extra):
+        _check(load().nfe_batch_set_barrier_test(self.h, int(spins), int(extra)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().nfe_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,159 @@
+// Batched sweep: many independent D2Q9 simulations (mixed grid sizes and
+// component counts) advanced by ONE persistent kernel launch for many time
+// steps.  Each CTA walks a static share of the (simulation, tile) work list,
+// running the fused tile step of nfe_fused2d.cuh with that simulation's
+// coefficients (read from global memory), and all CTAs meet at a grid barrier
+// between time steps.  The launch is cooperative (all CTAs co-resident), and
+// the barrier's wait is bounded: after `spin_limit` polls a CTA records a
+// timeout in the error word and every CTA leaves the step loop, so a fault in
+// the barrier can never hang the GPU.
+#include <cuda_runtime.h>
+
+#include "nfe_batch.h"
+#include "nfe_fused2d.cuh"
+
+namespace nfe {
+
+// Returns false when the barrier timed out (or another CTA reported an error).
+__device__ __forceinline__ bool grid_barrier(BatchSync *sync, unsigned nblocks, long long spin_limit) {
+    // nblocks: arrivals that release the barrier (the grid size; larger in the timeout test)
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &sync->generation;
+        volatile int *err = &sync->error;
+        const unsigned g = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&sync->count, 1u) + 1u;
+        if (arrived == nblocks) {
+            sync->count = 0u;
+            __threadfence();
+            atomicAdd(&sync->generation, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g && *err == 0) {
+                if (++spins > spin_limit) { atomicExch(&sync->error, NFE_BATCH_ERR_TIMEOUT); break; }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        ok = (*err == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+template <typename T, typename SF, int TX, int TY>
+__device__ __forceinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, int y0, unsigned char *smem) {
+    // the tile's simulation descriptor (geometry, coefficients, pointers) -> shared memory
+    __shared__ __align__(16) BatchSim<T> d;
+    {
+        static_assert(sizeof(BatchSim<T>) % 16 == 0, "16-byte copies");
+        const int4 *src = reinterpret_cast<const int4 *>(&dg);
+        int4 *dst = reinterpret_cast<int4 *>(&d);
+        for (int i = threadIdx.x; i < int(sizeof(BatchSim<T>) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    const SF *fin = static_cast<const SF *>(d.f[cur]);
+    SF *fout = static_cast<SF *>(d.f[1 - cur]);
+    const T *Cin = static_cast<const T *>(d.C[cur]);
+    T *Cout = static_cast<T *>(d.C[1 - cur]);
+    switch (d.N) {
+        // L2-only loads: inside one launch, other CTAs' writes of the previous step must not be
+        // read from a stale L1 line
+        case 2: fused2d_tile<2, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 3: fused2d_tile<3, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 4: fused2d_tile<4, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        default: fused2d_tile<5, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+    }
+}
+
+// registers per thread are bounded so that several CTAs share an SM
+template <typename T, int NT> struct BatchOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 6 : 3) : (NT <= 128 ? 4 : 2); };
+
+template <typename T, typename SF, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (BatchOcc<T, TX * TY>::value))
+k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ items, int nitems,
+                   int nsteps, int parity0, BatchSync *sync, long long spin_limit, unsigned expected) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (int t = 0; t < nsteps; ++t) {
+        const int cur = (parity0 + t) & 1;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const int4 w = items[it];
+            batch_tile<T, SF, TX, TY>(sims[w.x], cur, w.y, w.z, smem_raw);
+            __syncthreads();      // shared memory is reused by the next tile
+        }
+        if (t + 1 < nsteps && !grid_barrier(sync, expected, spin_limit)) return;
+    }
+}
+
+// One launch per step, one CTA per work item (the non-persistent batched form).
+template <typename T, typename SF, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (BatchOcc<T, TX * TY>::value))
+k_batch_step(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ items, int parity) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int4 w = items[blockIdx.x];
+    batch_tile<T, SF, TX, TY>(sims[w.x], parity, w.y, w.z, smem_raw);
+}
+
+template <typename T, int TX, int TY>
+constexpr size_t batch_smem() { return Fused2DShape<5, T, TX, TY>::BYTES; }
+
+template <typename T, typename SF, int TX, int TY>
+struct BatchKernels {
+    static cudaError_t setup(int *blocks_per_sm) {
+        const size_t smem = batch_smem<T, TX, TY>();
+        cudaError_t e = cudaFuncSetAttribute(k_batch_persistent<T, SF, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_batch_step<T, SF, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_persistent<T, SF, TX, TY>,
+                                                             TX * TY, smem);
+    }
+    static cudaError_t persistent(const BatchLaunch &L, cudaStream_t st) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(L.grid);
+        cfg.blockDim = dim3(TX * TY);
+        cfg.dynamicSmemBytes = batch_smem<T, TX, TY>();
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, k_batch_persistent<T, SF, TX, TY>,
+                                  static_cast<const BatchSim<T> *>(L.sims), L.items, L.nitems, L.nsteps,
+                                  L.parity, L.sync, L.spin_limit, L.expected);
+    }
+    static cudaError_t per_step(const BatchLaunch &L, cudaStream_t st) {
+        for (int t = 0; t < L.nsteps; ++t) {
+            k_batch_step<T, SF, TX, TY><<<L.nitems, TX * TY, batch_smem<T, TX, TY>(), st>>>(
+                static_cast<const BatchSim<T> *>(L.sims), L.items, (L.parity + t) & 1);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+};
+
+template <typename T, typename SF>
+const BatchOps *batch_ops_for() {
+    static const BatchOps o = {
+        {4, 8},
+        {&BatchKernels<T, SF, 32, 4>::setup, &BatchKernels<T, SF, 32, 8>::setup},
+        {&BatchKernels<T, SF, 32, 4>::persistent, &BatchKernels<T, SF, 32, 8>::persistent},
+        {&BatchKernels<T, SF, 32, 4>::per_step, &BatchKernels<T, SF, 32, 8>::per_step},
+    };
+    return &o;
+}
+
+const BatchOps *batch_ops(int prec) {
+    switch (prec) {
+        case NFE_FP64: return batch_ops_for<double, double>();
+        case NFE_FP32: return batch_ops_for<float, float>();
+        default: return nullptr;
+    }
+}
+
+}  // namespace nfe

@@ -1,0 +1,55 @@
+// Internal interface of the batched persistent kernel (nfe_batch.cu) and its host side.
+#pragma once
+
+#include "nfe_internal.h"
+
+#define NFE_BATCH_ERR_TIMEOUT 1
+
+namespace nfe {
+
+// One simulation as the batched kernel sees it (device memory, read-only).
+template <typename T>
+struct __align__(16) BatchSim {
+    Geom geom;
+    int N;
+    int pad_;
+    Coef<T> coef;
+    void *f[2];
+    void *C[2];
+    int *flag;
+};
+
+// Grid-barrier state (device memory): arrival count, generation, error word.
+struct BatchSync {
+    unsigned count;
+    unsigned generation;
+    int error;
+    int pad_;
+};
+
+struct BatchLaunch {
+    const void *sims;       // BatchSim<T>[nsims]
+    const int4 *items;      // (sim, x0, y0, 0) work items
+    int nitems;
+    int nsteps;
+    int parity;             // buffer holding the current state of every simulation
+    BatchSync *sync;
+    long long spin_limit;   // polls before a barrier wait gives up
+    unsigned expected;      // CTAs a barrier waits for (normally the grid size)
+    int grid;
+};
+
+using BatchSetup = cudaError_t (*)(int *blocks_per_sm);
+using BatchLauncher = cudaError_t (*)(const BatchLaunch &, cudaStream_t);
+
+constexpr int kBatchVariants = 2;
+struct BatchOps {
+    int ty[kBatchVariants];                     // tile heights (TX = 32)
+    BatchSetup setup[kBatchVariants];
+    BatchLauncher persistent[kBatchVariants];   // one cooperative launch for all steps
+    BatchLauncher per_step[kBatchVariants];     // one launch per step
+};
+
+const BatchOps *batch_ops(int prec);
+
+}  // namespace nfe

@@ -176,7 +176,25 @@ __device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N],
 
 // One tile of the fused step (phases 1-4 above).  `smem` holds
 // Fused2DShape<N, T, TX, TY>::BYTES bytes; all TX * TY threads of the CTA call it.
-template <int N, typename T, typename SF, int TX, int TY>
+// Global loads of the step's inputs: plain, or L2-only (ld.global.cg) when the
+// inputs were written earlier in the same launch by other CTAs.
+template <bool L2ONLY, typename X>
+__device__ __forceinline__ X ldin(const X *p) {
+    if constexpr (L2ONLY) return __ldcg(p);
+    else return *p;
+}
+
+template <bool L2ONLY, typename SF, typename T>
+__device__ __forceinline__ T fload(const SF *p, double w, T finv) {
+    if constexpr (L2ONLY) {
+        static_assert(sizeof(SF) >= 4, "L2-only loads are used with FP32 / FP64 storage");
+        return T(__ldcg(p));
+    } else {
+        return FStore<SF, T>::load(p, w, finv);
+    }
+}
+
+template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY = false>
 __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, const SF *__restrict__ fin,
                                              SF *__restrict__ fout, const T *__restrict__ Cin,
                                              T *__restrict__ Cout, int *__restrict__ flag,
@@ -203,7 +221,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     T f[9];
     f[0] = T(0);
 #pragma unroll
-    for (int k = 1; k < 9; ++k) f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv);
+    for (int k = 1; k < 9; ++k) f[k] = fload<L2ONLY, SF, T>(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv);
 
     // ring of the tile+1 region: top row, bottom row, then left and right columns
     int bx = 0, by = 0;
@@ -228,7 +246,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     hf[0] = T(0);
     if (ring_ok) {
 #pragma unroll
-        for (int k = 1; k < 9; ++k) hf[k] = FStore<SF, T>::load(fin + (k - 1) * n + hs, LD2Q9::w(k), cf.finv);
+        for (int k = 1; k < 9; ++k) hf[k] = fload<L2ONLY, SF, T>(fin + (k - 1) * n + hs, LD2Q9::w(k), cf.finv);
     }
 
     // ---- phase 1: C and E_B on tile + 2-ring ---------------------------------
@@ -250,7 +268,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             }
             const int s = gx + nx * gy;
 #pragma unroll
-            for (int a = 0; a < N - 1; ++a) cl[it][a] = Cin[a * n + s];
+            for (int a = 0; a < N - 1; ++a) cl[it][a] = ldin<L2ONLY>(Cin + a * n + s);
         }
     }
 #pragma unroll

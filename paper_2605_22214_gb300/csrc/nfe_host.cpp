@@ -12,6 +12,10 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <utility>
+
+#include "nfe_batch.h"
 #include "nfe_internal.h"
 #include "nfe_tables.h"
 
@@ -635,6 +639,342 @@ nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double 
             out[uidx[e]] = c[e] * q;
         }
     }
+    return NFE_OK;
+}
+
+}  // extern "C"
+
+// ============================================================================
+// Batched sweep (nfe_batch_*): many nfe_sim advanced by one persistent launch
+// ============================================================================
+
+struct nfe_batch {
+    int nsims = 0;
+    int prec = 0;
+    std::vector<nfe_sim *> sims;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    const BatchOps *ops = nullptr;
+    void *d_sims = nullptr;           // BatchSim<T>[nsims]
+    size_t sim_bytes = 0;             // sizeof(BatchSim<T>)
+    int4 *d_items = nullptr;
+    size_t items_cap = 0;
+    BatchSync *d_sync = nullptr;
+    int variant = -1;
+    int grid = 0;
+    int nitems = 0;
+    int parity = 0;
+    int mode = NFE_BATCH_PERSISTENT;
+    long long spin_default = 20000000LL;   // polls (~100 ns each plus the poll itself)
+    long long spin_next = 0;               // test hook: limit for the next launch
+    unsigned extra_next = 0;               // test hook: phantom CTAs for the next launch
+    int64_t sites = 0;
+    bool graphs_ok = true;
+    std::map<std::pair<int64_t, int>, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+template <typename T>
+void fill_batch_sim(const nfe_sim *s, BatchSim<T> &d) {
+    std::memset(&d, 0, sizeof d);
+    d.geom = s->geom;
+    d.N = s->N;
+    d.coef = *static_cast<const Coef<T> *>(s->coef);
+    d.f[0] = s->buf.f[0];
+    d.f[1] = s->buf.f[1];
+    d.C[0] = s->buf.C[0];
+    d.C[1] = s->buf.C[1];
+    d.flag = s->buf.flag;
+}
+
+nfe_status upload_batch_sim(nfe_batch *b, int i) {
+    std::vector<unsigned char> tmp(b->sim_bytes);
+    if (b->prec == NFE_FP64) fill_batch_sim<double>(b->sims[i], *reinterpret_cast<BatchSim<double> *>(tmp.data()));
+    else fill_batch_sim<float>(b->sims[i], *reinterpret_cast<BatchSim<float> *>(tmp.data()));
+    CK(cudaMemcpyAsync(static_cast<char *>(b->d_sims) + size_t(i) * b->sim_bytes, tmp.data(), b->sim_bytes,
+                       cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    return NFE_OK;
+}
+
+nfe_status batch_items(nfe_batch *b, int v) {
+    const int TX = 32, TY = b->ops->ty[v];
+    std::vector<int4> items;
+    for (int i = 0; i < b->nsims; ++i) {
+        const Geom &g = b->sims[i]->geom;
+        for (int y0 = 0; y0 < g.ny; y0 += TY)
+            for (int x0 = 0; x0 < g.nx; x0 += TX) items.push_back(make_int4(i, x0, y0, 0));
+    }
+    if (items.size() > b->items_cap) {
+        if (b->d_items) cudaFree(b->d_items);
+        b->d_items = nullptr;
+        cudaError_t e = cudaMalloc(&b->d_items, items.size() * sizeof(int4));
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(NFE_ENOMEM, "batch work list: %s", cudaGetErrorString(e)); }
+        b->items_cap = items.size();
+    }
+    CK(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    b->nitems = int(items.size());
+    int bps = 0;
+    CK(b->ops->setup[v](&bps));
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (bps < 1) return fail(NFE_EUNSUPPORTED, "batched kernel does not fit on an SM");
+    b->grid = std::min(bps * sms, b->nitems);
+    return NFE_OK;
+}
+
+BatchLaunch batch_launch_args(const nfe_batch *b, int64_t nsteps, long long spins, unsigned extra) {
+    BatchLaunch L;
+    L.sims = b->d_sims;
+    L.items = b->d_items;
+    L.nitems = b->nitems;
+    L.nsteps = int(nsteps);
+    L.parity = b->parity;
+    L.sync = b->d_sync;
+    L.spin_limit = spins;
+    L.expected = unsigned(b->grid) + extra;
+    L.grid = b->grid;
+    return L;
+}
+
+nfe_status batch_autotune(nfe_batch *b) {
+    if (b->variant >= 0) return NFE_OK;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_v = 0;
+    for (int v = 0; v < kBatchVariants; ++v) {
+        nfe_status st = batch_items(b, v);
+        if (st != NFE_OK) return st;
+        // one step reads buffer `parity` and writes the other one: the state is untouched
+        BatchLaunch L = batch_launch_args(b, 1, b->spin_default, 0);
+        CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+        CK(b->ops->persistent[v](L, b->stream));
+        CK(cudaEventRecord(e0, b->stream));
+        for (int r = 0; r < 3; ++r) CK(b->ops->persistent[v](L, b->stream));
+        CK(cudaEventRecord(e1, b->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    nfe_status st = batch_items(b, best_v);
+    if (st != NFE_OK) return st;
+    for (nfe_sim *s : b->sims) CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), b->stream));
+    b->variant = best_v;
+    return NFE_OK;
+}
+
+void batch_free(nfe_batch *b) {
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+    for (nfe_sim *s : b->sims) {
+        if (!s) continue;
+        s->stream = nullptr;          // the batch owns the stream
+        s->own_stream = false;
+        free_all(s);
+        delete s;
+    }
+    b->sims.clear();
+    if (b->d_sims) cudaFree(b->d_sims);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_sync) cudaFree(b->d_sync);
+    b->d_sims = nullptr;
+    b->d_items = nullptr;
+    b->d_sync = nullptr;
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    b->stream = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+nfe_status nfe_batch_create(int nsims, const nfe_grid *grids, const int *N, const nfe_params *params,
+                            nfe_batch **out) {
+    if (!out) return fail(NFE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nsims < 1 || !grids || !N || !params) return fail(NFE_EINVAL, "nsims < 1 or NULL array");
+    const int prec = params[0].precision;
+    if (prec != NFE_FP32 && prec != NFE_FP64)
+        return fail(NFE_EUNSUPPORTED, "batched sweeps run in NFE_FP32 or NFE_FP64");
+    for (int i = 0; i < nsims; ++i) {
+        if (grids[i].lattice != NFE_D2Q9) return fail(NFE_EUNSUPPORTED, "batched sweeps are D2Q9 (simulation %d)", i);
+        if (N[i] < 2 || N[i] > 5) return fail(NFE_EUNSUPPORTED, "batched sweeps take N = 2..5 (simulation %d)", i);
+        if (params[i].precision != prec) return fail(NFE_EINVAL, "all simulations of a batch share one precision");
+    }
+    nfe_batch *b = new (std::nothrow) nfe_batch();
+    if (!b) return fail(NFE_ENOMEM, "host allocation failed");
+    b->nsims = nsims;
+    b->prec = prec;
+    b->ops = batch_ops(prec);
+    if (params[0].cuda_stream) {
+        b->stream = static_cast<cudaStream_t>(params[0].cuda_stream);
+    } else {
+        cudaError_t e = cudaStreamCreate(&b->stream);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+        b->own_stream = true;
+    }
+    b->sims.assign(nsims, nullptr);
+    for (int i = 0; i < nsims; ++i) {
+        nfe_params p = params[i];
+        p.cuda_stream = b->stream;
+        nfe_status st = nfe_create(&grids[i], N[i], &p, &b->sims[i]);
+        if (st != NFE_OK) {
+            std::string msg = g_err;
+            batch_free(b);
+            delete b;
+            return fail(st, "simulation %d: %s", i, msg.c_str());
+        }
+        b->sites += b->sims[i]->geom.n;
+    }
+    b->sim_bytes = prec == NFE_FP64 ? sizeof(BatchSim<double>) : sizeof(BatchSim<float>);
+    cudaError_t e = cudaMalloc(&b->d_sims, b->sim_bytes * nsims);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_sync, sizeof(BatchSync));
+    if (e != cudaSuccess) { cudaGetLastError(); batch_free(b); delete b; return fail(NFE_ENOMEM, "batch descriptors"); }
+    for (int i = 0; i < nsims; ++i) {
+        nfe_status st = upload_batch_sim(b, i);
+        if (st != NFE_OK) { batch_free(b); delete b; return st; }
+    }
+    e = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) { batch_free(b); delete b; return cuda_fail(e, "batch init"); }
+    *out = b;
+    return NFE_OK;
+}
+
+void nfe_batch_destroy(nfe_batch *b) {
+    if (!b) return;
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
+}
+
+nfe_status nfe_batch_set_fields(nfe_batch *b, int sim, const double *C, const double *v) {
+    if (!b || sim < 0 || sim >= b->nsims) return fail(NFE_EINVAL, "bad batch or simulation index");
+    nfe_sim *s = b->sims[sim];
+    nfe_status st = nfe_set_fields(s, C, v);          // state in buffer 0
+    if (st != NFE_OK) return st;
+    if (b->parity == 1) {
+        // the batch's current buffer is 1 for every simulation: swap this one's buffers
+        std::swap(s->buf.f[0], s->buf.f[1]);
+        std::swap(s->buf.C[0], s->buf.C[1]);
+        s->buf.cur = 1;
+        for (auto &g : s->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+        return upload_batch_sim(b, sim);
+    }
+    return NFE_OK;
+}
+
+nfe_status nfe_batch_set_mode(nfe_batch *b, int mode) {
+    if (!b || (mode != NFE_BATCH_PERSISTENT && mode != NFE_BATCH_PER_STEP)) return fail(NFE_EINVAL, "bad mode");
+    b->mode = mode;
+    return NFE_OK;
+}
+
+nfe_status nfe_batch_set_barrier_test(nfe_batch *b, int64_t spins, int extra) {
+    if (!b || extra < 0) return fail(NFE_EINVAL, "bad arguments");
+    b->spin_next = spins > 0 ? spins : 0;
+    b->extra_next = unsigned(extra);
+    return NFE_OK;
+}
+
+nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
+    if (!b) return fail(NFE_EINVAL, "batch is NULL");
+    if (nsteps < 0 || nsteps > (1LL << 30)) return fail(NFE_EINVAL, "nsteps out of range");
+    if (nsteps == 0) return NFE_OK;
+    nfe_status st = batch_autotune(b);
+    if (st != NFE_OK) return st;
+    const int v = b->variant;
+    if (b->mode == NFE_BATCH_PER_STEP) {
+        BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
+        CK(b->ops->per_step[v](L, b->stream));
+    } else if (b->spin_next > 0 || b->extra_next > 0) {
+        // fault-injection launch (direct, not captured)
+        BatchLaunch L = batch_launch_args(b, nsteps, b->spin_next > 0 ? b->spin_next : b->spin_default, b->extra_next);
+        CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+        CK(b->ops->persistent[v](L, b->stream));
+        b->spin_next = 0;
+        b->extra_next = 0;
+    } else {
+        const auto key = std::make_pair(nsteps, b->parity);
+        auto it = b->graphs.find(key);
+        if (it == b->graphs.end() && b->graphs_ok) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
+            cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t e1 = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
+                cudaError_t e2 = e1 == cudaSuccess ? b->ops->persistent[v](L, b->stream) : e1;
+                e = cudaStreamEndCapture(b->stream, &g);
+                if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+                else if (e == cudaSuccess) e = e2;
+                if (g) cudaGraphDestroy(g);
+            }
+            if (e == cudaSuccess && ex) {
+                it = b->graphs.emplace(key, ex).first;
+            } else {
+                cudaGetLastError();
+                b->graphs_ok = false;          // cooperative launches not capturable: launch directly
+            }
+        }
+        if (it != b->graphs.end()) {
+            CK(cudaGraphLaunch(it->second, b->stream));
+        } else {
+            BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
+            CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+            CK(b->ops->persistent[v](L, b->stream));
+        }
+    }
+    b->parity ^= int(nsteps & 1);
+    for (nfe_sim *s : b->sims) {
+        s->buf.cur = b->parity;
+        s->step += nsteps;
+    }
+    return NFE_OK;
+}
+
+nfe_status nfe_batch_sync(nfe_batch *b) {
+    if (!b) return fail(NFE_EINVAL, "batch is NULL");
+    CK(cudaStreamSynchronize(b->stream));
+    BatchSync sync;
+    CK(cudaMemcpy(&sync, b->d_sync, sizeof sync, cudaMemcpyDeviceToHost));
+    if (sync.error) return fail(NFE_ETIMEOUT, "a grid-barrier wait of the batched kernel ran out of spins");
+    for (int i = 0; i < b->nsims; ++i) {
+        int flag = 0;
+        CK(cudaMemcpy(&flag, b->sims[i]->buf.flag, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) return fail(NFE_ENONFINITE, "simulation %d: a volume fraction became NaN or Inf", i);
+    }
+    return NFE_OK;
+}
+
+nfe_status nfe_batch_fields(nfe_batch *b, int sim, double *C, double *v, double *P) {
+    if (!b || sim < 0 || sim >= b->nsims) return fail(NFE_EINVAL, "bad batch or simulation index");
+    return nfe_fields(b->sims[sim], C, v, P);
+}
+
+nfe_status nfe_batch_diagnostics(nfe_batch *b, int sim, nfe_diag *out) {
+    if (!b || sim < 0 || sim >= b->nsims) return fail(NFE_EINVAL, "bad batch or simulation index");
+    return nfe_diagnostics(b->sims[sim], out);
+}
+
+nfe_status nfe_batch_get_info(const nfe_batch *b, nfe_batch_info *out) {
+    if (!b || !out) return fail(NFE_EINVAL, "NULL argument");
+    std::memset(out, 0, sizeof *out);
+    out->nsims = b->nsims;
+    out->sites = b->sites;
+    out->nitems = b->nitems;
+    out->grid = b->grid;
+    out->tile_x = b->variant >= 0 ? 32 : 0;
+    out->tile_y = b->variant >= 0 ? b->ops->ty[b->variant] : 0;
+    out->graphs = (b->graphs_ok && !b->graphs.empty()) ? 1 : 0;
     return NFE_OK;
 }
 
