@@ -44,7 +44,7 @@ __device__ __forceinline__ bool grid_barrier(BatchSync *sync, unsigned nblocks, 
 }
 
 template <typename T, typename SF, int TX, int TY>
-__device__ __forceinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, int y0, unsigned char *smem) {
+__device__ __noinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, int y0, unsigned char *smem) {
     // the tile's simulation descriptor (geometry, coefficients, pointers) -> shared memory
     __shared__ __align__(16) BatchSim<T> d;
     {
@@ -71,17 +71,32 @@ __device__ __forceinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x
 // registers per thread are bounded so that several CTAs share an SM
 template <typename T, int NT> struct BatchOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 6 : 3) : (NT <= 128 ? 4 : 2); };
 
+// the persistent kernel keeps its loop state live across the (non-inlined) tile
+// call, so it gets a larger register budget than the one-launch-per-step form
+template <typename T, int NT> struct PersistOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 4 : 2) : (NT <= 128 ? 3 : 1); };
+
 template <typename T, typename SF, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (BatchOcc<T, TX * TY>::value))
+__global__ void __launch_bounds__(TX * TY, (PersistOcc<T, TX * TY>::value))
 k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ items, int nitems,
                    int nsteps, int parity0, BatchSync *sync, long long spin_limit, unsigned expected) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    // Work is handed out dynamically by one counter that only grows: step t owns the
+    // indices [t * nitems, (t + 1) * nitems).  A CTA that draws an index of the next
+    // step keeps it and starts the next step with it.
+    __shared__ long long next;
+    if (threadIdx.x == 0) next = (long long)atomicAdd(&sync->ticket, 1ull);
+    __syncthreads();
     for (int t = 0; t < nsteps; ++t) {
         const int cur = (parity0 + t) & 1;
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-            const int4 w = items[it];
+        const long long end = (long long)(t + 1) * nitems;
+        long long idx = next;
+        while (idx < end) {
+            const int4 w = items[idx - (long long)t * nitems];
             batch_tile<T, SF, TX, TY>(sims[w.x], cur, w.y, w.z, smem_raw);
             __syncthreads();      // shared memory is reused by the next tile
+            if (threadIdx.x == 0) next = (long long)atomicAdd(&sync->ticket, 1ull);
+            __syncthreads();
+            idx = next;
         }
         if (t + 1 < nsteps && !grid_barrier(sync, expected, spin_limit)) return;
     }

@@ -25,6 +25,7 @@ struct BatchSync {
     unsigned generation;
     int error;
     int pad_;
+    unsigned long long ticket;   // work-item counter of the persistent kernel
 };
 
 struct BatchLaunch {
