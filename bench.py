@@ -340,7 +340,8 @@ def batch_sweep_measure(nfe, torch, stream, steps):
     with nfe.Batch(sims, "fp32", stream=stream.cuda_stream) as bt:
         for i, p in enumerate(sims):
             bt.set_fields(i, p["C0"])
-        for mode, name in ((nfe.NFE_BATCH_PERSISTENT, "persistent"), (nfe.NFE_BATCH_PER_STEP, "per_step")):
+        for mode, name in ((nfe.NFE_BATCH_PERSISTENT, "persistent"), (nfe.NFE_BATCH_PER_STEP, "per_step"),
+                           (nfe.NFE_BATCH_AUTO, "autotuned")):
             bt.set_mode(mode)
             with torch.cuda.stream(stream):
                 bt.step(4)
@@ -352,8 +353,10 @@ def batch_sweep_measure(nfe, torch, stream, steps):
             e.synchronize()
             bt.sync()
             ms = a.elapsed_time(e) / steps
+            inf = bt.info()
             out[name] = {"ms_per_step": round(ms, 4), "mlups": round(sites / (ms * 1e-3) / 1e6, 1),
-                         "mlups_x_n": round(site_n / (ms * 1e-3) / 1e6, 1)}
+                         "mlups_x_n": round(site_n / (ms * 1e-3) / 1e6, 1), "tile_y": inf["tile_y"],
+                         "form": inf["form"], "grid": inf["grid"]}
         out["info"] = bt.info()
     # the same jobs, one launch per simulation per step
     singles = []

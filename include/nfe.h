@@ -227,10 +227,13 @@ typedef struct {
     int grid;                        /* CTAs of the persistent launch */
     int tile_x, tile_y;              /* tile shape chosen by the autotuner (0 before the first step) */
     int graphs;                      /* 1 when launches are replayed from CUDA graphs */
+    int form;                        /* launch form in use (NFE_BATCH_PERSISTENT or _PER_STEP), -1 before tuning */
 } nfe_batch_info;
 
-enum { NFE_BATCH_PERSISTENT = 0,   /* one cooperative launch for all nsteps (default) */
-       NFE_BATCH_PER_STEP = 1 };   /* one batched launch per step */
+enum { NFE_BATCH_PERSISTENT = 0,   /* one cooperative launch for all nsteps */
+       NFE_BATCH_PER_STEP = 1,     /* one batched launch per step (all captured in one graph) */
+       NFE_BATCH_AUTO = 2 };       /* default: the autotuner times both forms and every tile
+                                      shape at the first step and keeps the fastest */
 
 /* grids, N and params are arrays of nsims entries (host).  Errors as nfe_create
  * for each simulation, plus NFE_EUNSUPPORTED for D3Q19 or N > 5. */
@@ -248,7 +251,7 @@ nfe_status nfe_batch_sync(nfe_batch *b);
 nfe_status nfe_batch_fields(nfe_batch *b, int sim, double *C, double *v, double *P);
 nfe_status nfe_batch_diagnostics(nfe_batch *b, int sim, nfe_diag *out);
 nfe_status nfe_batch_get_info(const nfe_batch *b, nfe_batch_info *out);
-/* Fault-injection hook for tests of the timeout path: the next persistent launch
+/* Fault-injection hook for tests of the timeout path: the next launch (persistent form)
  * uses at most `spins` polls per barrier wait and its barriers wait for
  * `extra` more CTAs than the grid has (extra > 0 makes every wait run out).
  * spins <= 0 restores the default limit (about a second or more). */

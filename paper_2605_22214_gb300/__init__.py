@@ -37,7 +37,7 @@ EXPORTS = ["nfe_create", "nfe_set_fields", "nfe_step", "nfe_sync", "nfe_fields",
            "nfe_batch_create", "nfe_batch_set_fields", "nfe_batch_step", "nfe_batch_set_mode",
            "nfe_batch_sync", "nfe_batch_fields", "nfe_batch_diagnostics", "nfe_batch_get_info",
            "nfe_batch_set_barrier_test", "nfe_batch_destroy"]
-NFE_BATCH_PERSISTENT, NFE_BATCH_PER_STEP = 0, 1
+NFE_BATCH_PERSISTENT, NFE_BATCH_PER_STEP, NFE_BATCH_AUTO = 0, 1, 2
 
 
 class nfe_grid(C.Structure):
@@ -70,7 +70,7 @@ class nfe_info(C.Structure):
 
 class nfe_batch_info(C.Structure):
     _fields_ = [("nsims", C.c_int), ("sites", C.c_int64), ("nitems", C.c_int), ("grid", C.c_int),
-                ("tile_x", C.c_int), ("tile_y", C.c_int), ("graphs", C.c_int)]
+                ("tile_x", C.c_int), ("tile_y", C.c_int), ("graphs", C.c_int), ("form", C.c_int)]
 
 
 class NfeError(RuntimeError):

@@ -664,7 +664,8 @@ struct nfe_batch {
     int grid = 0;
     int nitems = 0;
     int parity = 0;
-    int mode = NFE_BATCH_PERSISTENT;
+    int mode = NFE_BATCH_AUTO;        // requested form
+    int form = -1;                    // form in use (persistent or per-step) after tuning
     long long spin_default = 20000000LL;   // polls (~100 ns each plus the poll itself)
     long long spin_next = 0;               // test hook: limit for the next launch
     unsigned extra_next = 0;               // test hook: phantom CTAs for the next launch
@@ -740,27 +741,36 @@ BatchLaunch batch_launch_args(const nfe_batch *b, int64_t nsteps, long long spin
     return L;
 }
 
+// Time every (launch form, tile shape) the requested mode allows on the current
+// state and keep the fastest.  One step reads buffer `parity` and writes the
+// other one, so the state is untouched.
 nfe_status batch_autotune(nfe_batch *b) {
     if (b->variant >= 0) return NFE_OK;
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = 1e300;
-    int best_v = 0;
-    for (int v = 0; v < kBatchVariants; ++v) {
-        nfe_status st = batch_items(b, v);
-        if (st != NFE_OK) return st;
-        // one step reads buffer `parity` and writes the other one: the state is untouched
-        BatchLaunch L = batch_launch_args(b, 1, b->spin_default, 0);
-        CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
-        CK(b->ops->persistent[v](L, b->stream));
-        CK(cudaEventRecord(e0, b->stream));
-        for (int r = 0; r < 3; ++r) CK(b->ops->persistent[v](L, b->stream));
-        CK(cudaEventRecord(e1, b->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; best_v = v; }
+    int best_v = 0, best_form = NFE_BATCH_PERSISTENT;
+    for (int form = NFE_BATCH_PERSISTENT; form <= NFE_BATCH_PER_STEP; ++form) {
+        if (b->mode != NFE_BATCH_AUTO && b->mode != form) continue;
+        for (int v = 0; v < kBatchVariants; ++v) {
+            nfe_status st = batch_items(b, v);
+            if (st != NFE_OK) return st;
+            BatchLaunch L = batch_launch_args(b, 1, b->spin_default, 0);
+            const BatchLauncher launch = form == NFE_BATCH_PERSISTENT ? b->ops->persistent[v] : b->ops->per_step[v];
+            CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+            CK(launch(L, b->stream));
+            CK(cudaEventRecord(e0, b->stream));
+            for (int r = 0; r < 3; ++r) {
+                CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+                CK(launch(L, b->stream));
+            }
+            CK(cudaEventRecord(e1, b->stream));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) { best = ms; best_v = v; best_form = form; }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -768,6 +778,7 @@ nfe_status batch_autotune(nfe_batch *b) {
     if (st != NFE_OK) return st;
     for (nfe_sim *s : b->sims) CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), b->stream));
     b->variant = best_v;
+    b->form = best_form;
     return NFE_OK;
 }
 
@@ -873,8 +884,14 @@ nfe_status nfe_batch_set_fields(nfe_batch *b, int sim, const double *C, const do
 }
 
 nfe_status nfe_batch_set_mode(nfe_batch *b, int mode) {
-    if (!b || (mode != NFE_BATCH_PERSISTENT && mode != NFE_BATCH_PER_STEP)) return fail(NFE_EINVAL, "bad mode");
+    if (!b || (mode != NFE_BATCH_PERSISTENT && mode != NFE_BATCH_PER_STEP && mode != NFE_BATCH_AUTO))
+        return fail(NFE_EINVAL, "bad mode");
+    CK(cudaStreamSynchronize(b->stream));
     b->mode = mode;
+    b->variant = -1;                 // re-tune for the new mode
+    b->form = -1;
+    for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
     return NFE_OK;
 }
 
@@ -892,10 +909,7 @@ nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
     nfe_status st = batch_autotune(b);
     if (st != NFE_OK) return st;
     const int v = b->variant;
-    if (b->mode == NFE_BATCH_PER_STEP) {
-        BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
-        CK(b->ops->per_step[v](L, b->stream));
-    } else if (b->spin_next > 0 || b->extra_next > 0) {
+    if (b->spin_next > 0 || b->extra_next > 0) {
         // fault-injection launch (direct, not captured)
         BatchLaunch L = batch_launch_args(b, nsteps, b->spin_next > 0 ? b->spin_next : b->spin_default, b->extra_next);
         CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
@@ -909,10 +923,11 @@ nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
             cudaGraph_t g = nullptr;
             cudaGraphExec_t ex = nullptr;
             BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
+            const BatchLauncher launch = b->form == NFE_BATCH_PER_STEP ? b->ops->per_step[v] : b->ops->persistent[v];
             cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
                 cudaError_t e1 = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
-                cudaError_t e2 = e1 == cudaSuccess ? b->ops->persistent[v](L, b->stream) : e1;
+                cudaError_t e2 = e1 == cudaSuccess ? launch(L, b->stream) : e1;
                 e = cudaStreamEndCapture(b->stream, &g);
                 if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
                 else if (e == cudaSuccess) e = e2;
@@ -930,7 +945,7 @@ nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
         } else {
             BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
             CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
-            CK(b->ops->persistent[v](L, b->stream));
+            CK((b->form == NFE_BATCH_PER_STEP ? b->ops->per_step[v] : b->ops->persistent[v])(L, b->stream));
         }
     }
     b->parity ^= int(nsteps & 1);
@@ -975,6 +990,7 @@ nfe_status nfe_batch_get_info(const nfe_batch *b, nfe_batch_info *out) {
     out->tile_x = b->variant >= 0 ? 32 : 0;
     out->tile_y = b->variant >= 0 ? b->ops->ty[b->variant] : 0;
     out->graphs = (b->graphs_ok && !b->graphs.empty()) ? 1 : 0;
+    out->form = b->form;
     return NFE_OK;
 }
 

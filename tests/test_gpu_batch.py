@@ -94,6 +94,7 @@ def test_barrier_timeout_is_reported_and_gpu_stays_usable():
         b.step(2)
         b.sync()
         # the next launch's barriers wait for one CTA more than exist, with a short limit
+        b.set_mode(nfe.NFE_BATCH_PERSISTENT)
         b.set_barrier_test(20000, 1)
         b.step(4)
         with pytest.raises(nfe.NfeError) as e:
