@@ -198,6 +198,41 @@ def test_tile_variants_are_bitwise_identical(precision):
             assert np.array_equal(st, states[0])
 
 
+def _mixture3d(nx, ny, nz, N, seed, walls):
+    rng = np.random.default_rng(seed)
+    sig = W.random_sigma(rng, N)
+    C = 1.0 / N + rng.uniform(-0.05, 0.05, size=(N, nz, ny, nx))
+    C /= C.sum(axis=0, keepdims=True)
+    p = W.base_params(19, nx, ny, nz, N, sig, rng.uniform(0.7, 1.2, N), walls=walls, lambda_trt=3 / 16,
+                      m=0.05, body_force=(1e-6, 0, -2e-6))
+    p["C0"] = C
+    return p
+
+
+@pytest.mark.parametrize("shape,walls,N", [((20, 13, 17), (False, False, True), 3),
+                                           ((5, 3, 4), (False, False, False), 2),
+                                           ((35, 9, 10), (True, True, False), 4),
+                                           ((6, 7, 12), (True, False, True), 5)])
+def test_d3q19_ragged_and_walls_fp64(shape, walls, N):
+    nx, ny, nz = shape
+    compare(_mixture3d(nx, ny, nz, N, 40 + N, walls), 25, "fp64")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_d3q19_variants_are_bitwise_identical(precision):
+    p = _mixture3d(37, 11, 19, 4, 9, (False, True, True))
+    states = []
+    with nfe.Sim(p, precision) as s:
+        nv = s.info()["nvariants"]
+        assert nv == 2
+        for v in range(nv):
+            s.set_fields(p["C0"])
+            s.set_variant(v)
+            s.step(13)
+            states.append(s.get_state())
+    assert np.array_equal(states[0], states[1])
+
+
 def test_nonfinite_flag_reported():
     p = W.spinodal_2d(nx=16, ny=16, seed=4)
     C0 = p["C0"].copy()
