@@ -173,12 +173,12 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
     const int hxy = edge ? imod(hx, nx) + nx * imod(hy, ny) : hx + nx * hy;
 
     // ---- A-plane za: C and E_B on the tile + 2-ring ----------------------------
-    auto fill_A = [&](int za) {
-        if (g.wz && (za < 0 || za >= nz)) return;      // beyond a wall: never read
+    // Loads are issued one plane ahead (load_A / load_F) and consumed by fill_A /
+    // fill_B in the next iteration, so HBM latency overlaps the previous plane's work.
+    constexpr int ITER = (Sh::APLANE + NT - 1) / NT;
+    auto load_A = [&](int za, T (&cl)[ITER][N - 1]) {
+        if (g.wz && (za < 0 || za >= nz)) return;
         const int zw = imod(za, nz);
-        T *base = sA + slotA(za) * Sh::A_SLOT;
-        constexpr int ITER = (Sh::APLANE + NT - 1) / NT;
-        T cl[ITER][N - 1];
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
             const int i = tid + it * NT;
@@ -194,6 +194,10 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                 for (int a = 0; a < N - 1; ++a) cl[it][a] = Cin[a * n + s];
             }
         }
+    };
+    auto fill_A = [&](int za, const T (&cl)[ITER][N - 1]) {
+        if (g.wz && (za < 0 || za >= nz)) return;      // beyond a wall: never read
+        T *base = sA + slotA(za) * Sh::A_SLOT;
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
             const int i = tid + it * NT;
@@ -211,9 +215,23 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
             }
         }
     };
+    // f of the own site and of the ring site of plane zb
+    auto load_F = [&](int zb, T (&fo)[19], T (&fr)[19]) {
+        fo[0] = fr[0] = T(0);
+        if (g.wz && (zb < 0 || zb >= nz)) return;
+        const int zw = imod(zb, nz);
+        const int s0 = sxy + nxy * zw;
+#pragma unroll
+        for (int k = 1; k < 19; ++k) fo[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD3Q19::w(k), cf.finv);
+        if (ring_xy_ok) {
+            const int s = hxy + nxy * zw;
+#pragma unroll
+            for (int k = 1; k < 19; ++k) fr[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD3Q19::w(k), cf.finv);
+        }
+    };
 
     // ---- B-plane zb: S, v (and, for own planes, collide + push-stream) --------
-    auto fill_B = [&](int zb, bool collide) {
+    auto fill_B = [&](int zb, bool collide, const T (&fo)[19], const T (&fr)[19]) {
         if (g.wz && (zb < 0 || zb >= nz)) return;      // sources beyond a wall bounce back
         const int zw = imod(zb, nz);
         const T *pm = sA + slotA(zb - 1) * Sh::A_SLOT;
@@ -225,10 +243,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         // own site
         {
             const int s0 = sxy + nxy * zw;
-            T f[19];
-            f[0] = T(0);
-#pragma unroll
-            for (int k = 1; k < 19; ++k) f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD3Q19::w(k), cf.finv);
+            const T (&f)[19] = fo;
             const unsigned wall0 = check ? wall_mask3(g, gx0, gy0, zb) : 0u;
             T c[N], lap[N], gr[N][3], gE[3];
             const int ia = (ty + 2) * Sh::AX + (tx + 2);
@@ -292,11 +307,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         }
         // ring site
         if (ring_xy_ok) {
-            const int s = hxy + nxy * zw;
-            T f[19];
-            f[0] = T(0);
-#pragma unroll
-            for (int k = 1; k < 19; ++k) f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD3Q19::w(k), cf.finv);
+            const T (&f)[19] = fr;
             const unsigned wall = check ? wall_mask3(g, hx, hy, zb) : 0u;
             T c[N], lap[N], gr[N][3], gE[3];
             const int ia = (by + 1) * Sh::AX + (bx + 1);
@@ -362,16 +373,31 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
     };
 
     // warm-up: A-planes z_lo-2 .. z_lo+1, B-planes z_lo-1 and z_lo
-    for (int za = z_lo - 2; za <= z_lo + 1; ++za) fill_A(za);
+    T cl[ITER][N - 1];
+    T fo[19], fr[19];
+#pragma unroll 1
+    for (int za = z_lo - 2; za <= z_lo + 1; ++za) {
+        load_A(za, cl);
+        fill_A(za, cl);
+    }
     __syncthreads();
-    fill_B(z_lo - 1, false);
-    fill_B(z_lo, true);
+    load_F(z_lo - 1, fo, fr);
+    fill_B(z_lo - 1, false, fo, fr);
+    load_F(z_lo, fo, fr);
+    fill_B(z_lo, true, fo, fr);
+    load_A(z_lo + 2, cl);
+    load_F(z_lo + 1, fo, fr);
     __syncthreads();
+#pragma unroll 1
     for (int zc = z_lo; zc < z_hi; ++zc) {
-        fill_A(zc + 2);
+        fill_A(zc + 2, cl);
         __syncthreads();
-        fill_B(zc + 1, zc + 1 < z_hi);
+        fill_B(zc + 1, zc + 1 < z_hi, fo, fr);
         __syncthreads();
+        if (zc + 1 < z_hi) {               // next plane's loads fly while this plane is gathered
+            load_A(zc + 3, cl);
+            load_F(zc + 2, fo, fr);
+        }
         ch(zc);
     }
 }
