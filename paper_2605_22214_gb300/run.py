@@ -1,0 +1,70 @@
+"""Run one of the synthetic workloads through the C ABI and print its throughput.
+
+    python -m paper_2605_22214_gb300.run WORKLOAD [--precision fp32] [--steps 50] [--size N]
+
+WORKLOAD is one of: spinodal (D2Q9, N = 4, size^2), janus3d (D3Q19, N = 4, size^3),
+lens (D2Q9, N = 3, size^2, walls in y), poiseuille3d (D3Q19, N = 7, 32 x 32 x 192).
+The time is taken with CUDA events around the steps, after three warm-up steps.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def make(name, size):
+    import nfe_workloads as W
+    if name == "spinodal":
+        return W.spinodal_2d(nx=size, ny=size)
+    if name == "janus3d":
+        return W.janus_3d(n=size, radius=32.0 * size / 256.0)
+    if name == "lens":
+        return W.lens_2d(nx=size, ny=size, radius=12.0 * size / 64.0)
+    if name == "poiseuille3d":
+        return W.layered_poiseuille()
+    raise SystemExit(f"unknown workload {name}")
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("workload")
+    ap.add_argument("--precision", default="fp32", choices=["fp64", "fp32", "f16", "bf16"])
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--variant", type=int, default=-1, help="tile shape (-1: autotune)")
+    args = ap.parse_args()
+    import torch
+
+    import paper_2605_22214_gb300 as nfe
+    from paper_2605_22214_gb300 import build
+    build.build()
+    p = make(args.workload, args.size)
+    stream = torch.cuda.Stream()
+    with nfe.Sim(p, args.precision, stream=stream.cuda_stream, scale_exp=10) as s:
+        s.set_fields(p["C0"])
+        s.set_variant(args.variant)
+        with torch.cuda.stream(stream):
+            s.step(3)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(args.steps)
+            b.record(stream)
+        b.synchronize()
+        s.sync()
+        ms = a.elapsed_time(b) / args.steps
+        info = s.info()
+    n = info["sites"]
+    print(json.dumps({"workload": p["name"], "precision": args.precision, "sites": n, "ms_per_step": round(ms, 5),
+                      "mlups": round(n / ms / 1e3, 1), "variant": info["variant"],
+                      "effective_gbs": round(info["min_bytes_per_site"] * n / ms / 1e6, 1)}))
+
+
+if __name__ == "__main__":
+    main()
