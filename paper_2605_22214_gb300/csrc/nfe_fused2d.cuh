@@ -92,8 +92,8 @@ __device__ __forceinline__ void stencil2d(const T *sA, int acount, int ia, unsig
     srec_load<T, N>(sA, acount, ia, r0);
     T d[9][N];            // d[k][a]: neighbour minus centre, a < N-1 volume fractions, a = N-1 bulk energy
     constexpr int off[9] = {0, 1, -1, AX, -AX, AX + 1, -AX - 1, -AX + 1, AX - 1};
-#pragma unroll
-    for (int k = 1; k < 9; ++k) {
+    sfor<1, 9, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
         if (CHECK && ((wall >> k) & 1u)) {
 #pragma unroll
             for (int a = 0; a < N; ++a) d[k][a] = T(0);
@@ -103,7 +103,7 @@ __device__ __forceinline__ void stencil2d(const T *sA, int acount, int ia, unsig
 #pragma unroll
             for (int a = 0; a < N; ++a) d[k][a] = r[a] - r0[a];
         }
-    }
+    });
     const T third = T(1) / T(3), twelfth = T(1) / T(12), two3 = T(2) / T(3), sixth = T(1) / T(6);
     T sl = T(0), sgx = T(0), sgy = T(0);
 #pragma unroll
@@ -220,8 +220,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     const int s0 = sx + nx * sy;
     T f[9];
     f[0] = T(0);
-#pragma unroll
-    for (int k = 1; k < 9; ++k) f[k] = fload<L2ONLY, SF, T>(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv);
+    sfor<1, 9, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; f[k] = fload<L2ONLY, SF, T>(fin + (k - 1) * n + s0, LD2Q9::w(k), cf.finv); });
 
     // ring of the tile+1 region: top row, bottom row, then left and right columns
     int bx = 0, by = 0;
@@ -236,17 +235,16 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     if (edge && has_ring) {
         if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) ring_ok = false;
         hs = imod(hx, nx) + nx * imod(hy, ny);
-#pragma unroll
-        for (int k = 1; k < 9; ++k) {
+        sfor<1, 9, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
             const int xx = hx + LD2Q9::ex(k), yy = hy + LD2Q9::ey(k);
             if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) hwall |= 1u << k;
-        }
+        });
     }
     T hf[9];
     hf[0] = T(0);
     if (ring_ok) {
-#pragma unroll
-        for (int k = 1; k < 9; ++k) hf[k] = fload<L2ONLY, SF, T>(fin + (k - 1) * n + hs, LD2Q9::w(k), cf.finv);
+        sfor<1, 9, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; hf[k] = fload<L2ONLY, SF, T>(fin + (k - 1) * n + hs, LD2Q9::w(k), cf.finv); });
     }
 
     // ---- phase 1: C and E_B on tile + 2-ring ---------------------------------
@@ -293,11 +291,11 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     // wall mask of the own site: bit k set when x + e_k is beyond a wall
     unsigned wall0 = 0;
     if (edge) {
-#pragma unroll
-        for (int k = 1; k < 9; ++k) {
+        sfor<1, 9, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
             const int xx = gx0 + LD2Q9::ex(k), yy = gy0 + LD2Q9::ey(k);
             if ((g.wx && (xx < 0 || xx >= nx)) || (g.wy && (yy < 0 || yy >= ny))) wall0 |= 1u << k;
-        }
+        });
     }
     T c[N], lap[N], gxv[N], gyv[N], gEx, gEy;
     T S[N - 1], Fx, Fy, vx, vy, P, sumf;
@@ -340,8 +338,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
         const T vv = vx * vx + vy * vy, vF = vx * Fx + vy * Fy;
         const T base = T(3) * P - T(1.5) * vv;
-#pragma unroll
-        for (int k = 1; k < 9; k += 2) {
+        sfor<1, 9, 2>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
             const int kb = k + 1;
             const T wk = T(LD2Q9::w(k));
             const T eu = T(LD2Q9::ex(k)) * vx + T(LD2Q9::ey(k)) * vy;
@@ -368,7 +366,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
                 else FStore<SF, T>::store(fout + (kb - 1) * n + (wrap(sx - LD2Q9::ex(k), nx) + nx * wrap(sy - LD2Q9::ey(k), ny)),
                                           pkb, LD2Q9::w(kb), cf.fscale);
             }
-        }
+        });
     }
     __syncthreads();
 
@@ -384,8 +382,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (T(1) - T(1.5) * w0 * vv0); lapS[e] = T(0); }
         constexpr int offB[9] = {0, 1, -1, TX + 2, -(TX + 2), TX + 3, -(TX + 3), -(TX + 2) + 1, (TX + 2) - 1};
-#pragma unroll
-        for (int k = 1; k < 9; ++k) {
+        sfor<1, 9, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
             const T wk = T(LD2Q9::w(k));
             // source x - e_k is the neighbour in direction kbar
             const int kb = opp(k);
@@ -403,7 +401,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
 #pragma unroll
                 for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * r[N + 1 + e]; }
             }
-        }
+        });
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) {

@@ -44,9 +44,9 @@ __device__ __forceinline__ void stencil3d(const T *pm, const T *p0, const T *pp,
     T acc[N][4];          // lap, gx, gy, gz sums (N-1 = bulk energy: gradient only)
 #pragma unroll
     for (int a = 0; a < N; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = T(0);
-#pragma unroll
-    for (int k = 1; k < 19; ++k) {
-        if (CHECK && ((wall >> k) & 1u)) continue;     // psi beyond a wall := psi(x)
+    sfor<1, 19, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
+        if (CHECK && ((wall >> k) & 1u)) return;     // psi beyond a wall := psi(x)
         const T *pl = LD3Q19::ez(k) > 0 ? pp : (LD3Q19::ez(k) < 0 ? pm : p0);
         T r[RA::NVP];
         srec_load<T, N>(pl, count, ia + LD3Q19::ex(k) + AX * LD3Q19::ey(k), r);
@@ -59,7 +59,7 @@ __device__ __forceinline__ void stencil3d(const T *pm, const T *p0, const T *pp,
             if (LD3Q19::ey(k)) acc[a][2] += (LD3Q19::ey(k) > 0 ? wk : -wk) * d;
             if (LD3Q19::ez(k)) acc[a][3] += (LD3Q19::ez(k) > 0 ? wk : -wk) * d;
         }
-    }
+    });
     T sl = T(0), sx = T(0), sy = T(0), sz = T(0), rest = T(0);
 #pragma unroll
     for (int a = 0; a < N - 1; ++a) {
@@ -109,13 +109,13 @@ __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
     T j0 = T(0), j1 = T(0), j2 = T(0), sumf = T(0);
-#pragma unroll
-    for (int k = 1; k < 19; ++k) {
+    sfor<1, 19, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
         sumf += f[k];
         if (LD3Q19::ex(k)) j0 += LD3Q19::ex(k) > 0 ? f[k] : -f[k];
         if (LD3Q19::ey(k)) j1 += LD3Q19::ey(k) > 0 ? f[k] : -f[k];
         if (LD3Q19::ez(k)) j2 += LD3Q19::ez(k) > 0 ? f[k] : -f[k];
-    }
+    });
     v[0] = j0 + T(0.5) * F[0];
     v[1] = j1 + T(0.5) * F[1];
     v[2] = j2 + T(0.5) * F[2];
@@ -126,12 +126,12 @@ __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N
 // Bit k set when x + e_k lies beyond a wall.
 __device__ __forceinline__ unsigned wall_mask3(const Geom &g, int x, int y, int z) {
     unsigned m = 0;
-#pragma unroll
-    for (int k = 1; k < 19; ++k) {
+    sfor<1, 19, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
         const int xx = x + LD3Q19::ex(k), yy = y + LD3Q19::ey(k), zz = z + LD3Q19::ez(k);
         if ((g.wx && (xx < 0 || xx >= g.nx)) || (g.wy && (yy < 0 || yy >= g.ny)) || (g.wz && (zz < 0 || zz >= g.nz)))
             m |= 1u << k;
-    }
+    });
     return m;
 }
 
@@ -221,12 +221,10 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         if (g.wz && (zb < 0 || zb >= nz)) return;
         const int zw = imod(zb, nz);
         const int s0 = sxy + nxy * zw;
-#pragma unroll
-        for (int k = 1; k < 19; ++k) fo[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD3Q19::w(k), cf.finv);
+        sfor<1, 19, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; fo[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD3Q19::w(k), cf.finv); });
         if (ring_xy_ok) {
             const int s = hxy + nxy * zw;
-#pragma unroll
-            for (int k = 1; k < 19; ++k) fr[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD3Q19::w(k), cf.finv);
+            sfor<1, 19, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; fr[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD3Q19::w(k), cf.finv); });
         }
     };
 
@@ -266,8 +264,8 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                 const T vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
                 const T base = T(3) * P - T(1.5) * vv;
                 const bool fast = !check && !edge && zb >= 1 && zb <= nz - 2;
-#pragma unroll
-                for (int k = 1; k < 19; k += 2) {
+                sfor<1, 19, 2>([&](auto kc_) {
+                    constexpr int k = decltype(kc_)::value;
                     const int kb = k + 1;
                     const T wk = T(LD3Q19::w(k));
                     const T eu = T(LD3Q19::ex(k)) * v[0] + T(LD3Q19::ey(k)) * v[1] + T(LD3Q19::ez(k)) * v[2];
@@ -302,7 +300,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                             FStore<SF, T>::store(fout + (kb - 1) * n + t, pkb, LD3Q19::w(kb), cf.fscale);
                         }
                     }
-                }
+                });
             }
         }
         // ring site
@@ -341,8 +339,8 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         T acc[N - 1], lapS[N - 1];
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (T(1) - T(1.5) * w0 * vv0); lapS[e] = T(0); }
-#pragma unroll
-        for (int k = 1; k < 19; ++k) {
+        sfor<1, 19, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
             const T wk = T(LD3Q19::w(k));
             const int kb = opp(k);                  // source x - e_k = x + e_kbar
             if (check && ((wall0 >> kb) & 1u)) {
@@ -360,7 +358,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
 #pragma unroll
                 for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * r[N + 2 + e]; }
             }
-        }
+        });
         const int s0 = sxy + nxy * zc;
         bool bad = false;
 #pragma unroll

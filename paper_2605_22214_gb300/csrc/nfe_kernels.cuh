@@ -18,6 +18,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "nfe_internal.h"
 
 namespace nfe {
@@ -58,6 +60,16 @@ struct LD3Q19 {
 };
 
 __host__ __device__ constexpr int opp(int k) { return k == 0 ? 0 : ((k & 1) ? k + 1 : k - 1); }
+
+// Compile-time loop: calls f(std::integral_constant<int, i>) for i = B, B + S, ... < E, so that
+// the lattice direction is a constant expression in the body.
+template <int B, int E, int S, typename F>
+__device__ __forceinline__ void sfor(F &&f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        sfor<B + S, E, S>(f);
+    }
+}
 
 // ----------------------------------------------------------------------------
 // Storage of f.  FP16 keeps f_k / w_k * 2^scale_exp, BF16 keeps f_k / w_k:
