@@ -1,0 +1,151 @@
+"""The reference workloads (lens, spinodal, layered Poiseuille, Janus precision study)
+on the GPU against the oracle and against what the paper fixes."""
+import math
+
+import numpy as np
+import pytest
+
+import nfe_workloads as W
+import paper_2605_22214_gb300 as nfe
+from oracle import lbm, observables
+
+from ._lib import lib, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    lib()
+
+
+def test_lens_c1_parity_and_neumann_angle():
+    # 64 x 64 lens, FP64, 2000 steps: GPU vs oracle fields, and the lens angle of both against
+    # each other (1 %) and against the Neumann triangle of Eq. 51 (102.64 deg; the 64^2 grid with a
+    # radius-12 lens and 2000 steps is far from the paper's converged 300 x 150 runs, so the
+    # theory check is loose).
+    p = W.lens_2d()
+    steps = 2000
+    prm = lbm.Params(p)
+    st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), steps, flux_form="factored")
+    Co, vo, Po, _ = lbm.fields(prm, st, flux_form="factored")
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        s.step(steps)
+        Cg, vg, Pg = s.fields()
+    assert rel(Cg, Co) < 1e-10
+    assert rel(vg, vo) < 1e-8
+    ang_o = observables.lens_angle(Co[2, 0])
+    ang_g = observables.lens_angle(Cg[2, 0])
+    theory = observables.neumann_angle(0.01, 0.008, 0.008)
+    print(f"lens c1: GPU angle {ang_g:.2f}, oracle {ang_o:.2f}, theory {theory:.2f}, "
+          f"rel C {rel(Cg, Co):.2e}, rel v {rel(vg, vo):.2e}")
+    assert abs(ang_g - ang_o) / ang_o < 0.01
+    assert abs(ang_g - theory) < 15.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_spinodal_c2_conservation_over_long_run(precision):
+    # 512 x 512, N = 4: per-component mass constant and no momentum from the surface-tension
+    # force (Eq. 34 sums to zero on a periodic grid), checked every 100 steps over 5000 steps.
+    p = W.spinodal_2d()
+    tol_m = 1e-12 if precision == "fp64" else 2e-6
+    with nfe.Sim(p, precision) as s:
+        s.set_fields(p["C0"])
+        d0 = s.diagnostics()
+        for _ in range(50):
+            s.step(100)
+            d = s.diagnostics()
+            np.testing.assert_allclose(d["mass"], d0["mass"], rtol=tol_m)
+            fabs = d["force_abs_sum"].sum()
+            assert np.abs(d["force_sum"]).max() <= (1e-13 if precision == "fp64" else 1e-5) * fabs
+            assert np.abs(d["momentum"]).max() <= (1e-12 if precision == "fp64" else 1e-4) * max(fabs, 1e-30) * 100
+            assert d["nonfinite"] == 0
+
+
+def test_spinodal_c2_parity_window_fp64():
+    # The c2 physics on a 128 x 128 window of the seeded field, 200 steps, against the oracle.
+    full = W.spinodal_2d()
+    p = dict(full)
+    p["nx"] = p["ny"] = 128
+    C = full["C0"][:, :, :128, :128]
+    p["C0"] = C / C.sum(axis=0, keepdims=True)
+    prm = lbm.Params(p)
+    st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), 200, flux_form="factored")
+    Co, vo, Po, _ = lbm.fields(prm, st, flux_form="factored")
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        s.step(200)
+        Cg, vg, Pg = s.fields()
+    assert rel(Cg, Co) < 1e-12
+    assert rel(vg, vo) < 1e-10
+
+
+def _poiseuille_column(nz=192):
+    # the layered flow depends on z only: a 2 x 2 column carries the 32 x 32 x 192 dynamics
+    return W.layered_poiseuille(nx=2, ny=2, nz=nz)
+
+
+def test_poiseuille_c3_parity_with_oracle():
+    p = _poiseuille_column()
+    steps = 1000
+    prm = lbm.Params(p)
+    st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), steps, flux_form="factored")
+    Co, vo, Po, _ = lbm.fields(prm, st, flux_form="factored")
+    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+        with nfe.Sim(p, precision) as s:
+            s.set_fields(p["C0"])
+            s.step(steps)
+            Cg, vg, Pg = s.fields()
+        print(f"poiseuille c3 column {precision}: rel C {rel(Cg, Co):.2e} rel vx {rel(vg[0], vo[0]):.2e}")
+        assert rel(Cg, Co) < tol
+        assert rel(vg[0], vo[0]) < tol
+        assert (Cg[6] == 0.0).all()          # the absent seventh component
+
+
+def test_poiseuille_c3_full_size_against_analytic_profile():
+    # 32 x 32 x 192 (FP32): after 2e5 steps the centre profile matches the piecewise parabola of
+    # Eq. 56 with eta_i v'' = -F (the physical sign) within 2 % of its maximum; the seventh
+    # component stays exactly zero; every column carries the same profile.
+    p = W.layered_poiseuille()
+    with nfe.Sim(p, "fp32") as s:
+        s.set_fields(p["C0"])
+        s.step(200000)
+        s.sync()
+        C, v, P = s.fields()
+    assert (C[6] == 0.0).all()
+    vx = v[0]
+    prof = vx.mean(axis=(1, 2))
+    assert np.abs(vx - prof[:, None, None]).max() <= 1e-5 * np.abs(prof).max()
+    nz = p["nz"]
+    eta = (np.array([0.6, 0.7, 0.8, 0.9, 1.0, 1.2]) - 0.5) / 3.0
+    width = nz / 6
+    zs = np.arange(nz) + 0.5              # halfway walls at z = -1/2 and nz - 1/2
+    ref = observables.poiseuille_profile(zs, [width * b for b in range(1, 6)], eta, 1e-6, nz, sign=-1.0)
+    err = np.abs(prof - ref).max() / np.abs(ref).max()
+    print(f"poiseuille c3 full size: max |v - analytic| / max|analytic| = {err:.4f}, vmax {np.abs(prof).max():.4e}")
+    assert err < 0.02, err
+
+
+@pytest.mark.parametrize("precision", ["fp32", "f16", "bf16"])
+def test_janus_c4_precision_study_small(precision):
+    # Four Janus drops (c4 layout at 64^3, radius 8), 300 steps: FP32 compute with three
+    # storage formats against the FP64 path.  Bounds: C error, momentum drift per site.
+    p = W.janus_3d(n=64, radius=8.0)
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        s.step(300)
+        C64, v64, P64 = s.fields()
+    with nfe.Sim(p, precision, scale_exp=10) as s:
+        s.set_fields(p["C0"])
+        s.step(300)
+        C, v, Pp = s.fields()
+        d = s.diagnostics()
+    errC = np.abs(C - C64).max()
+    n = C.shape[1] * C.shape[2] * C.shape[3]
+    print(f"janus c4 64^3 {precision}: max|C - C_fp64| {errC:.3e}, momentum/site {np.abs(d['momentum']).max() / n:.3e}")
+    bound = {"fp32": 1e-5, "f16": 2e-3, "bf16": 1e-2}[precision]
+    assert errC < bound, errC
+    n = C.shape[1] * C.shape[2] * C.shape[3]
+    drift = np.abs(d["momentum"]).max() / n
+    assert drift < {"fp32": 1e-9, "f16": 1e-6, "bf16": 1e-5}[precision], drift
