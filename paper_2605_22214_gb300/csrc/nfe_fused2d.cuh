@@ -388,24 +388,26 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             // source x - e_k is the neighbour in direction kbar
             const int kb = opp(k);
             if (edge && ((wall0 >> kb) & 1u)) {
-                // bounce-back: g_k(x, t+1) = g^eq_kbar(x, t)
+                // bounce-back: g_k(x, t+1) = g^eq_kbar(x, t); its S difference is zero
                 const T eu = -(T(LD2Q9::ex(k)) * r0[N - 1] + T(LD2Q9::ey(k)) * r0[N]);
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
 #pragma unroll
-                for (int e = 0; e < N - 1; ++e) { acc[e] += r0[e] * sk; lapS[e] += wk * r0[N + 1 + e]; }
+                for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;
             } else {
                 T r[RB::NVP];
                 srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib + offB[kb], r);
                 const T eu = T(LD2Q9::ex(k)) * r[N - 1] + T(LD2Q9::ey(k)) * r[N];
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (r[N - 1] * r[N - 1] + r[N] * r[N]));
 #pragma unroll
-                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * r[N + 1 + e]; }
+                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 1 + e] - r0[N + 1 + e]); }
             }
         });
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) {
-            const T out = acc[e] + m * ((T(1) - w0) * r0[N + 1 + e] - lapS[e]);
+            // m [(1 - w_0) S(x) - sum_k w_k S(x - e_k)] written as differences: every link's
+            // two contributions are exact negatives, so the FP32 update conserves mass
+            const T out = acc[e] - m * lapS[e];
             Cout[e * n + s0] = out;
             bad |= !isfinite(out);
         }

@@ -347,7 +347,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                 const T eu = -(T(LD3Q19::ex(k)) * r0[N - 1] + T(LD3Q19::ey(k)) * r0[N] + T(LD3Q19::ez(k)) * r0[N + 1]);
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
 #pragma unroll
-                for (int e = 0; e < N - 1; ++e) { acc[e] += r0[e] * sk; lapS[e] += wk * r0[N + 2 + e]; }
+                for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;      // S difference is zero
             } else {
                 const T *pl = LD3Q19::ez(kb) > 0 ? bp : (LD3Q19::ez(kb) < 0 ? bm : b0);
                 T r[RB::NVP];
@@ -356,14 +356,14 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                 const T uu = r[N - 1] * r[N - 1] + r[N] * r[N] + r[N + 1] * r[N + 1];
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
 #pragma unroll
-                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * r[N + 2 + e]; }
+                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
             }
         });
         const int s0 = sxy + nxy * zc;
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) {
-            const T out = acc[e] + cf.m * ((T(1) - w0) * r0[N + 2 + e] - lapS[e]);
+            const T out = acc[e] - cf.m * lapS[e];     // S Laplacian as link differences (mass-exact)
             Cout[e * n + s0] = out;
             bad |= !isfinite(out);
         }

@@ -145,7 +145,7 @@ nfe_status free_all(nfe_sim *s) {
     s->timed.clear();
     for (auto e : s->event_pool) cudaEventDestroy(e);
     s->event_pool.clear();
-    void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1], s->buf.v, s->buf.S,
+    void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
                     s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&s->buf, 0, sizeof s->buf);
@@ -345,8 +345,6 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     ALLOC(s->buf.f[1], s->fplanes_bytes);
     ALLOC(s->buf.C[0], s->cplanes_bytes);
     ALLOC(s->buf.C[1], s->cplanes_bytes);
-    ALLOC(s->buf.v, size_t(s->ops->D) * n * ce);
-    ALLOC(s->buf.S, size_t(N - 1) * n * ce);
     ALLOC(s->buf.flag, sizeof(int));
     if (!s->tab.q4.empty()) ALLOC(s->q4dev, s->tab.q4.size() * ce);
 #undef ALLOC

@@ -45,15 +45,13 @@ struct Coef {
 };
 
 // One kernel kind for profiling.
-enum KernelKind { K_COLLIDE = 0, K_CH = 1, K_FUSED = 2, K_MOMENTS = 3, K_REDUCE = 4, K_NKINDS = 5 };
+enum KernelKind { K_FUSED = 0, K_MOMENTS = 1, K_REDUCE = 2, K_NKINDS = 3 };
 extern const char *kKernelNames[K_NKINDS];
 
 // Device buffers of one simulation.
 struct Buffers {
     void *f[2];           // populations k = 1..Q-1, planar, storage type
     void *C[2];           // evolved volume fractions, planar, compute type
-    void *v;              // scratch: velocity (D planes), compute type
-    void *S;              // scratch: flux potential (N-1 planes), compute type
     double *fields;       // moments output: C (N), v (3), P, Fs (3) planes, FP64
     double *partials;     // reduction partials
     double *diag;         // reduction result

@@ -1,18 +1,9 @@
-// Device code of the N-component free-energy LBM time step (arXiv 2605.22214).
-//
-// One time step is two kernels on planar (SoA) arrays, one thread per site:
-//   k_collide : C on the 1-ring -> isotropic grad / Laplacian of every C_i
-//               (Eqs. 35-36), E_B (Eq. 5) and grad E_B, the factored flux
-//               potential S_i = C_i q_i(C) + (3D/4) lap C_i (Eq. 12), the force
-//               F = grad E_B + sum_{a != b} kappa_ab lap C_b grad C_a + F_b
-//               (Eq. 34); f_k(x) -> v, P (Eqs. 37-38); TRT collision with the
-//               forcing split (Eqs. 23-30); push-streaming with halfway
-//               bounce-back (Eqs. 44-45).  Writes v and S for the second kernel.
-//   k_ch      : C_i(x, t+1) = sum_k g^eq_{i,k}(x - e_k, t), the Cahn-Hilliard LBE
-//               of Eq. 39 with tau_g = 1 (so the post-collision g is g^eq and no
-//               g population needs storing), bounce-back for sources in a wall.
-// Both kernels are templated on the lattice, on N and on the arithmetic type;
-// k_collide also on the storage type of f.
+// Shared device code of the N-component free-energy LBM (arXiv 2605.22214):
+// lattices (D2Q9, D3Q19), storage formats of f, the bulk energy E_B (Eq. 5), the
+// factored flux potential S_i = C_i q_i(C) + (3D/4) lap C_i (Eq. 12), a generic
+// site stencil, the viscosity rule (Eq. 42), and the non-step kernels: fields of
+// the current state (moments), initialisation, (un)packing and FP64 reductions.
+// The time-step kernels are in nfe_fused2d.cuh (D2Q9) and nfe_fused3d.cuh (D3Q19).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -286,127 +277,6 @@ __device__ __forceinline__ void relaxation(const Coef<T> &cf, const T (&c)[N], T
 // Kernels
 // ----------------------------------------------------------------------------
 
-template <class L, int N, typename T, typename SF>
-__global__ void __launch_bounds__(256)
-k_collide(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-          const T *__restrict__ C, T *__restrict__ vout, T *__restrict__ Sout) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.n) return;
-    const int x = s % g.nx;
-    const int r = s / g.nx;
-    const int y = r % g.ny;
-    const int z = r / g.ny;
-    const size_t n = size_t(g.n);
-
-    Stencil<L, N, T> st;
-    stencil<L, N, T>(g, cf, C, s, x, y, z, st);
-    T Fs[3], S[N - 1];
-    force_and_potential<L, N, T>(cf, st, Fs, S);
-    const T F0 = Fs[0] + cf.fb[0], F1 = Fs[1] + cf.fb[1], F2 = Fs[2] + cf.fb[2];
-
-    T f[L::Q];
-    T sumf = T(0), j0 = T(0), j1 = T(0), j2 = T(0);
-#pragma unroll
-    for (int k = 1; k < L::Q; ++k) {
-        f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, L::w(k), cf.finv);
-        sumf += f[k];
-        if (L::ex(k)) j0 += L::ex(k) > 0 ? f[k] : -f[k];
-        if (L::ey(k)) j1 += L::ey(k) > 0 ? f[k] : -f[k];
-        if (L::ez(k)) j2 += L::ez(k) > 0 ? f[k] : -f[k];
-    }
-    // Eq. 37 with rho = 1, and Eq. 38 with s_0(v) = -w_0 v.v / (2 c_s^2)
-    const T v0 = j0 + T(0.5) * F0, v1 = j1 + T(0.5) * F1, v2 = j2 + T(0.5) * F2;
-    const T vv = v0 * v0 + v1 * v1 + v2 * v2;
-    const T w0 = T(L::w(0));
-    const T P = (sumf - T(1.5) * w0 * vv) * T(1.0 / (3.0 * (1.0 - L::w(0))));
-    const T vF = v0 * F0 + v1 * F1 + v2 * F2;
-    T op, om;
-    relaxation<N, T>(cf, st.c, op, om);
-    const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
-
-#pragma unroll
-    for (int k = 1; k < L::Q; k += 2) {
-        const int kb = k + 1;
-        const T wk = T(L::w(k));
-        const T eu = T(L::ex(k)) * v0 + T(L::ey(k)) * v1 + T(L::ez(k)) * v2;
-        const T eF = T(L::ex(k)) * F0 + T(L::ey(k)) * F1 + T(L::ez(k)) * F2;
-        // symmetric / antisymmetric parts of f^eq (Eq. 27) and of F_k (Eq. 30)
-        const T eqp = wk * (T(3) * P + T(4.5) * eu * eu - T(1.5) * vv);
-        const T eqm = wk * (T(3) * eu);
-        const T Fp = wk * (T(9) * eu * eF - T(3) * vF);
-        const T Fm = wk * (T(3) * eF);
-        const T fp = T(0.5) * (f[k] + f[kb]);
-        const T fm = T(0.5) * (f[k] - f[kb]);
-        const T sym = -op * (fp - eqp) + ap * Fp;
-        const T anti = -om * (fm - eqm) + am * Fm;
-        const T pk = f[k] + sym + anti;      // post-collision f_k
-        const T pkb = f[kb] + sym - anti;    // post-collision f_kbar
-        // push: f_k(x + e_k, t+1) = pk, or bounce-back into f_kbar(x) at a wall (Eq. 44)
-        const int jk = st.nb[k], jkb = st.nb[kb];
-        if (jk >= 0) FStore<SF, T>::store(fout + (k - 1) * n + jk, pk, L::w(k), cf.fscale);
-        else         FStore<SF, T>::store(fout + (kb - 1) * n + s, pk, L::w(kb), cf.fscale);
-        if (jkb >= 0) FStore<SF, T>::store(fout + (kb - 1) * n + jkb, pkb, L::w(kb), cf.fscale);
-        else          FStore<SF, T>::store(fout + (k - 1) * n + s, pkb, L::w(k), cf.fscale);
-    }
-    vout[s] = v0;
-    vout[n + s] = v1;
-    if (L::D == 3) vout[2 * n + s] = v2;
-#pragma unroll
-    for (int e = 0; e < N - 1; ++e) Sout[e * n + s] = S[e];
-}
-
-template <class L, int N, typename T>
-__global__ void __launch_bounds__(256)
-k_ch(Geom g, Coef<T> cf, const T *__restrict__ C, const T *__restrict__ V, const T *__restrict__ S,
-     T *__restrict__ Cout, int *__restrict__ flag) {
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= g.n) return;
-    const int x = s % g.nx;
-    const int r = s / g.nx;
-    const int y = r % g.ny;
-    const int z = r / g.ny;
-    const size_t n = size_t(g.n);
-    const T m = cf.m;
-
-    T c0[N - 1], S0[N - 1], acc[N - 1];
-    const T u0 = V[s], u1 = V[n + s], u2 = (L::D == 3) ? V[2 * n + s] : T(0);
-    const T uu = u0 * u0 + u1 * u1 + u2 * u2;
-    const T w0 = T(L::w(0));
-    const T s0 = -T(1.5) * w0 * uu;
-#pragma unroll
-    for (int e = 0; e < N - 1; ++e) {
-        c0[e] = C[e * n + s];
-        S0[e] = S[e * n + s];
-        // g^eq_{e,0}(x) = C (1 + s_0(v)) + (1 - w_0) m S (Eq. 40)
-        acc[e] = c0[e] * (T(1) + s0) + (T(1) - w0) * m * S0[e];
-    }
-#pragma unroll
-    for (int k = 1; k < L::Q; ++k) {
-        const T wk = T(L::w(k));
-        const int j = neighbour<L>(g, x, y, z, opp(k));      // source x - e_k
-        if (j >= 0) {
-            const T a0 = V[j], a1 = V[n + j], a2 = (L::D == 3) ? V[2 * n + j] : T(0);
-            const T eu = T(L::ex(k)) * a0 + T(L::ey(k)) * a1 + T(L::ez(k)) * a2;
-            const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (a0 * a0 + a1 * a1 + a2 * a2));
-#pragma unroll
-            for (int e = 0; e < N - 1; ++e) acc[e] += C[e * n + j] * sk - wk * m * S[e * n + j];
-        } else {
-            // bounce-back: g_k(x, t+1) = g*_kbar(x, t) = g^eq_kbar(x, t)
-            const T eu = -(T(L::ex(k)) * u0 + T(L::ey(k)) * u1 + T(L::ez(k)) * u2);
-            const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
-#pragma unroll
-            for (int e = 0; e < N - 1; ++e) acc[e] += c0[e] * sk - wk * m * S0[e];
-        }
-    }
-    bool bad = false;
-#pragma unroll
-    for (int e = 0; e < N - 1; ++e) {
-        Cout[e * n + s] = acc[e];
-        bad |= !isfinite(acc[e]);
-    }
-    if (bad) atomicOr(flag, 1);
-}
-
 // Fields of the current state in FP64: C (N planes, user order), v (3), P, F_s (3).
 template <class L, int N, typename T, typename SF>
 __global__ void __launch_bounds__(256)
@@ -499,22 +369,9 @@ __global__ void k_reduce_final(int nblocks, int N, const double *__restrict__ pa
 
 inline unsigned blocks_for(long long n, int bs) { return unsigned((n + bs - 1) / bs); }
 
+// Launchers of the non-step kernels for one lattice, N and precision.
 template <class L, int N, typename T, typename SF>
 struct Launch {
-    static cudaError_t collide(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int) {
-        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
-        k_collide<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
-            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
-            static_cast<const T *>(b.C[cur]), static_cast<T *>(b.v), static_cast<T *>(b.S));
-        return cudaGetLastError();
-    }
-    static cudaError_t ch_update(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int) {
-        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
-        k_ch<L, N, T><<<blocks_for(g.n, 256), 256, 0, st>>>(
-            g, cf, static_cast<const T *>(b.C[cur]), static_cast<const T *>(b.v),
-            static_cast<const T *>(b.S), static_cast<T *>(b.C[1 - cur]), b.flag);
-        return cudaGetLastError();
-    }
     static cudaError_t moments(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
@@ -541,27 +398,6 @@ struct Launch {
         k_pack_C<T><<<blocks_for(total, 256), 256, 0, st>>>(total, in, static_cast<T *>(b.C[cur]));
         return cudaGetLastError();
     }
-    // generic two-kernel step (collide+stream, then the Cahn-Hilliard gather)
-    static const Ops *ops(int prec) {
-        static const Ops o = {L::Q, L::D, N, prec, 2, {K_COLLIDE, K_CH}, {&collide, &ch_update}, 1,
-                              {"two-kernel", nullptr, nullptr, nullptr},
-                              &moments, &reduce, &init_f, &unpack_f, &pack_C, int(sizeof(SF)), int(sizeof(T))};
-        return &o;
-    }
 };
-
-template <class L, typename T, typename SF>
-const Ops *ops_for_n(int N, int prec) {
-    switch (N) {
-        case 2: return Launch<L, 2, T, SF>::ops(prec);
-        case 3: return Launch<L, 3, T, SF>::ops(prec);
-        case 4: return Launch<L, 4, T, SF>::ops(prec);
-        case 5: return Launch<L, 5, T, SF>::ops(prec);
-        case 6: return Launch<L, 6, T, SF>::ops(prec);
-        case 7: return Launch<L, 7, T, SF>::ops(prec);
-        case 8: return Launch<L, 8, T, SF>::ops(prec);
-        default: return nullptr;
-    }
-}
 
 }  // namespace nfe
