@@ -380,7 +380,9 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T vv0 = r0[N - 1] * r0[N - 1] + r0[N] * r0[N];
         T acc[N - 1], lapS[N - 1];
 #pragma unroll
-        for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (T(1) - T(1.5) * w0 * vv0); lapS[e] = T(0); }
+        // acc gathers only the small advective increments; C(x) is added once at the end, so in
+        // FP32 the rest-population share C s_0 is not lost against 1 (mass-exact update)
+        for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * vv0); lapS[e] = T(0); }
         constexpr int offB[9] = {0, 1, -1, TX + 2, -(TX + 2), TX + 3, -(TX + 3), -(TX + 2) + 1, (TX + 2) - 1};
         sfor<1, 9, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
@@ -407,7 +409,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         for (int e = 0; e < N - 1; ++e) {
             // m [(1 - w_0) S(x) - sum_k w_k S(x - e_k)] written as differences: every link's
             // two contributions are exact negatives, so the FP32 update conserves mass
-            const T out = acc[e] - m * lapS[e];
+            const T out = r0[e] + (acc[e] - m * lapS[e]);
             Cout[e * n + s0] = out;
             bad |= !isfinite(out);
         }

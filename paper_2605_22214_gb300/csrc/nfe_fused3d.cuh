@@ -338,7 +338,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         const T w0 = T(1) / T(3);
         T acc[N - 1], lapS[N - 1];
 #pragma unroll
-        for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (T(1) - T(1.5) * w0 * vv0); lapS[e] = T(0); }
+        for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * vv0); lapS[e] = T(0); }   // increments only
         sfor<1, 19, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const T wk = T(LD3Q19::w(k));
@@ -363,7 +363,7 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) {
-            const T out = acc[e] - cf.m * lapS[e];     // S Laplacian as link differences (mass-exact)
+            const T out = r0[e] + (acc[e] - cf.m * lapS[e]);   // S Laplacian as link differences (mass-exact)
             Cout[e * n + s0] = out;
             bad |= !isfinite(out);
         }
