@@ -135,48 +135,71 @@ __device__ __forceinline__ unsigned wall_mask3(const Geom &g, int x, int y, int 
     return m;
 }
 
+// Per-thread state of one CTA of the fused D3Q19 step, and its phases.
 template <int N, typename T, typename SF, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
-k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag, int zchunk) {
+struct Fused3DTile {
     using Sh = Fused3DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     using RB = typename Sh::RB;
     static_assert(Sh::NHALO <= TX * TY, "one ring site per thread at most");
-    constexpr int NT = TX * TY;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sA = reinterpret_cast<T *>(smem_raw);
-    T *sB = sA + 5 * Sh::A_SLOT;
-    const int nx = g.nx, ny = g.ny, nz = g.nz;
-    const int nxy = nx * ny;
-    const int n = int(g.n);
-    const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z_lo = blockIdx.z * zchunk;
-    const int z_hi = min(z_lo + zchunk, nz);
-    const bool edge = (x0 - 2 < 0) || (x0 + TX + 2 > nx) || (y0 - 2 < 0) || (y0 + TY + 2 > ny);
+    static constexpr int NT = TX * TY;
+    static constexpr int ITER = (Sh::APLANE + NT - 1) / NT;
 
+    const Geom &g;
+    const Coef<T> &cf;
+    const SF *__restrict__ fin;
+    SF *__restrict__ fout;
+    const T *__restrict__ Cin;
+    T *__restrict__ Cout;
+    int *__restrict__ flag;
+    T *sA, *sB;
+    int nx, ny, nz, nxy, n, tid, x0, y0, z_lo, z_hi;
+    bool edge;
     // own site in the plane, and this thread's ring site
-    const int tx = tid % TX, ty = tid / TX;
-    const int gx0 = x0 + tx, gy0 = y0 + ty;
-    const bool own_xy = gx0 < nx && gy0 < ny;
-    const int sx = edge ? imod(gx0, nx) : gx0;
-    const int sy = edge ? imod(gy0, ny) : gy0;
-    const int sxy = sx + nx * sy;
-    int bx = 0, by = 0;
-    const bool has_ring = tid < Sh::NHALO;
-    if (tid < Sh::BX) { bx = tid; by = 0; }
-    else if (tid < 2 * Sh::BX) { bx = tid - Sh::BX; by = Sh::BY - 1; }
-    else { const int r = tid - 2 * Sh::BX; by = 1 + (r >> 1); bx = (r & 1) ? Sh::BX - 1 : 0; }
-    const int hx = x0 + bx - 1, hy = y0 + by - 1;
-    const bool ring_xy_ok = has_ring && !(edge && ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))));
-    const int hxy = edge ? imod(hx, nx) + nx * imod(hy, ny) : hx + nx * hy;
+    int tx, ty, gx0, gy0, sx, sy, sxy, bx, by, hx, hy, hxy;
+    bool own_xy, ring_xy_ok;
 
-    // ---- A-plane za: C and E_B on the tile + 2-ring ----------------------------
+    __device__ __forceinline__ Fused3DTile(const Geom &g_, const Coef<T> &cf_, const SF *fin_, SF *fout_,
+                                           const T *Cin_, T *Cout_, int *flag_, unsigned char *smem, int zchunk)
+        : g(g_), cf(cf_), fin(fin_), fout(fout_), Cin(Cin_), Cout(Cout_), flag(flag_) {
+        sA = reinterpret_cast<T *>(smem);
+        sB = sA + 5 * Sh::A_SLOT;
+        nx = g.nx; ny = g.ny; nz = g.nz;
+        nxy = nx * ny;
+        n = int(g.n);
+        tid = threadIdx.x;
+        x0 = blockIdx.x * TX;
+        y0 = blockIdx.y * TY;
+        z_lo = blockIdx.z * zchunk;
+        z_hi = min(z_lo + zchunk, nz);
+        edge = (x0 - 2 < 0) || (x0 + TX + 2 > nx) || (y0 - 2 < 0) || (y0 + TY + 2 > ny);
+        tx = tid % TX;
+        ty = tid / TX;
+        gx0 = x0 + tx;
+        gy0 = y0 + ty;
+        own_xy = gx0 < nx && gy0 < ny;
+        sx = edge ? imod(gx0, nx) : gx0;
+        sy = edge ? imod(gy0, ny) : gy0;
+        sxy = sx + nx * sy;
+        bx = 0;
+        by = 0;
+        const bool has_ring = tid < Sh::NHALO;
+        if (tid < Sh::BX) { bx = tid; by = 0; }
+        else if (tid < 2 * Sh::BX) { bx = tid - Sh::BX; by = Sh::BY - 1; }
+        else { const int r = tid - 2 * Sh::BX; by = 1 + (r >> 1); bx = (r & 1) ? Sh::BX - 1 : 0; }
+        hx = x0 + bx - 1;
+        hy = y0 + by - 1;
+        ring_xy_ok = has_ring && !(edge && ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))));
+        hxy = edge ? imod(hx, nx) + nx * imod(hy, ny) : hx + nx * hy;
+    }
+
     // Loads are issued one plane ahead (load_A / load_F) and consumed by fill_A /
     // fill_B in the next iteration, so HBM latency overlaps the previous plane's work.
-    constexpr int ITER = (Sh::APLANE + NT - 1) / NT;
-    auto load_A = [&](int za, T (&cl)[ITER][N - 1]) {
+    // load_A / fill_A: A-plane za (C and E_B on the tile + 2-ring).
+    // load_F: f of the own site and of the ring site of plane zb.
+    // fill_B: B-plane zb (S, v; for own planes also collide + push-stream).
+    // ch: Cahn-Hilliard update of plane zc from B-planes zc-1..zc+1.
+    __device__ __forceinline__ void load_A(int za, T (&cl)[ITER][N - 1]) {
         if (g.wz && (za < 0 || za >= nz)) return;
         const int zw = imod(za, nz);
 #pragma unroll
@@ -194,8 +217,9 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                 for (int a = 0; a < N - 1; ++a) cl[it][a] = Cin[a * n + s];
             }
         }
-    };
-    auto fill_A = [&](int za, const T (&cl)[ITER][N - 1]) {
+    }
+
+    __device__ __forceinline__ void fill_A(int za, const T (&cl)[ITER][N - 1]) {
         if (g.wz && (za < 0 || za >= nz)) return;      // beyond a wall: never read
         T *base = sA + slotA(za) * Sh::A_SLOT;
 #pragma unroll
@@ -214,9 +238,9 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                 srec_store<T, N>(base, Sh::APLANE, i, rec);
             }
         }
-    };
-    // f of the own site and of the ring site of plane zb
-    auto load_F = [&](int zb, T (&fo)[19], T (&fr)[19]) {
+    }
+
+    __device__ __forceinline__ void load_F(int zb, T (&fo)[19], T (&fr)[19]) {
         fo[0] = fr[0] = T(0);
         if (g.wz && (zb < 0 || zb >= nz)) return;
         const int zw = imod(zb, nz);
@@ -226,10 +250,9 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
             const int s = hxy + nxy * zw;
             sfor<1, 19, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; fr[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD3Q19::w(k), cf.finv); });
         }
-    };
+    }
 
-    // ---- B-plane zb: S, v (and, for own planes, collide + push-stream) --------
-    auto fill_B = [&](int zb, bool collide, const T (&fo)[19], const T (&fr)[19]) {
+    __device__ __forceinline__ void fill_B(int zb, bool collide, const T (&fo)[19], const T (&fr)[19]) {
         if (g.wz && (zb < 0 || zb >= nz)) return;      // sources beyond a wall bounce back
         const int zw = imod(zb, nz);
         const T *pm = sA + slotA(zb - 1) * Sh::A_SLOT;
@@ -321,10 +344,9 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
             for (int a = 2 * N + 1; a < RB::NVP; ++a) rec[a] = T(0);
             srec_store<T, 2 * N + 1>(bbase, Sh::BPLANE, by * Sh::BX + bx, rec);
         }
-    };
+    }
 
-    // ---- Cahn-Hilliard update of plane zc from B-planes zc-1..zc+1 ------------
-    auto ch = [&](int zc) {
+    __device__ __forceinline__ void ch(int zc) {
         if (!own_xy) return;
         const bool check = edge || (g.wz && (zc == 0 || zc == nz - 1));
         const unsigned wall0 = check ? wall_mask3(g, gx0, gy0, zc) : 0u;
@@ -368,36 +390,47 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
             bad |= !isfinite(out);
         }
         if (bad) atomicOr(flag, 1);
-    };
+    }
 
-    // warm-up: A-planes z_lo-2 .. z_lo+1, B-planes z_lo-1 and z_lo
-    T cl[ITER][N - 1];
-    T fo[19], fr[19];
+    __device__ __forceinline__ void march() {
+        // warm-up: A-planes z_lo-2 .. z_lo+1, B-planes z_lo-1 and z_lo
+        T cl[ITER][N - 1];
+        T fo[19], fr[19];
 #pragma unroll 1
-    for (int za = z_lo - 2; za <= z_lo + 1; ++za) {
-        load_A(za, cl);
-        fill_A(za, cl);
-    }
-    __syncthreads();
-    load_F(z_lo - 1, fo, fr);
-    fill_B(z_lo - 1, false, fo, fr);
-    load_F(z_lo, fo, fr);
-    fill_B(z_lo, true, fo, fr);
-    load_A(z_lo + 2, cl);
-    load_F(z_lo + 1, fo, fr);
-    __syncthreads();
-#pragma unroll 1
-    for (int zc = z_lo; zc < z_hi; ++zc) {
-        fill_A(zc + 2, cl);
-        __syncthreads();
-        fill_B(zc + 1, zc + 1 < z_hi, fo, fr);
-        __syncthreads();
-        if (zc + 1 < z_hi) {               // next plane's loads fly while this plane is gathered
-            load_A(zc + 3, cl);
-            load_F(zc + 2, fo, fr);
+        for (int za = z_lo - 2; za <= z_lo + 1; ++za) {
+            load_A(za, cl);
+            fill_A(za, cl);
         }
-        ch(zc);
+        __syncthreads();
+        load_F(z_lo - 1, fo, fr);
+        fill_B(z_lo - 1, false, fo, fr);
+        load_F(z_lo, fo, fr);
+        fill_B(z_lo, true, fo, fr);
+        load_A(z_lo + 2, cl);
+        load_F(z_lo + 1, fo, fr);
+        __syncthreads();
+#pragma unroll 1
+        for (int zc = z_lo; zc < z_hi; ++zc) {
+            fill_A(zc + 2, cl);
+            __syncthreads();
+            fill_B(zc + 1, zc + 1 < z_hi, fo, fr);
+            __syncthreads();
+            if (zc + 1 < z_hi) {               // next plane's loads fly while this plane is gathered
+                load_A(zc + 3, cl);
+                load_F(zc + 2, fo, fr);
+            }
+            ch(zc);
+        }
     }
+};
+
+template <int N, typename T, typename SF, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY)
+k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
+          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag, int zchunk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Fused3DTile<N, T, SF, TX, TY> t(g, cf, fin, fout, Cin, Cout, flag, smem_raw, zchunk);
+    t.march();
 }
 
 template <int N, typename T, typename SF, int TX, int TY>
