@@ -208,8 +208,11 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     const int nx = g.nx, ny = g.ny;
     const int n = int(g.n);
     const int tid = threadIdx.x;
-    // uniform per CTA: does the tile plus its 2-ring cross the domain edge?
+    // uniform per CTA: does the tile plus its 2-ring cross the domain edge (indices wrap or
+    // clamp), is that edge a wall (stencils need wall tests), is the domain narrower than a tile?
     const bool edge = (x0 - 2 < 0) || (x0 + TX + 2 > nx) || (y0 - 2 < 0) || (y0 + TY + 2 > ny);
+    const bool wallt = (g.wx && ((x0 - 2 < 0) || (x0 + TX + 2 > nx))) || (g.wy && ((y0 - 2 < 0) || (y0 + TY + 2 > ny)));
+    const bool tiny = nx < TX + 4 || ny < TY + 4;
 
     // ---- own site and ring site of this thread; start their f loads first ----
     const int tx = tid % TX, ty = tid / TX;
@@ -235,6 +238,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     if (edge && has_ring) {
         if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) ring_ok = false;
         hs = imod(hx, nx) + nx * imod(hy, ny);
+    }
+    if (wallt && has_ring) {
         sfor<1, 9, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int xx = hx + LD2Q9::ex(k), yy = hy + LD2Q9::ey(k);
@@ -261,8 +266,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             if (edge) {
                 // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
                 // such entries are never used by a real site's stencil
-                gx = g.wx ? min(max(gx, 0), nx - 1) : imod(gx, nx);
-                gy = g.wy ? min(max(gy, 0), ny - 1) : imod(gy, ny);
+                gx = g.wx ? min(max(gx, 0), nx - 1) : (tiny ? imod(gx, nx) : wrap(gx, nx));
+                gy = g.wy ? min(max(gy, 0), ny - 1) : (tiny ? imod(gy, ny) : wrap(gy, ny));
             }
             const int s = gx + nx * gy;
 #pragma unroll
@@ -290,7 +295,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     // ---- phase 2a: own site ---------------------------------------------------
     // wall mask of the own site: bit k set when x + e_k is beyond a wall
     unsigned wall0 = 0;
-    if (edge) {
+    if (wallt) {
         sfor<1, 9, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int xx = gx0 + LD2Q9::ex(k), yy = gy0 + LD2Q9::ey(k);
@@ -301,8 +306,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     T S[N - 1], Fx, Fy, vx, vy, P, sumf;
     {
         const int ia = (ty + 2) * Sh::AX + (tx + 2);
-        if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
-        else      stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
+        if (wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
+        else       stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
         site_physics<N, T>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
         T rec[RB::NVP];
 #pragma unroll
@@ -318,8 +323,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     if (ring_ok) {
         T hc[N], hl[N], hgx[N], hgy[N], hEx, hEy;
         const int ia = (by + 1) * Sh::AX + (bx + 1);
-        if (edge) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
-        else      stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
+        if (wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
+        else       stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
         T hS[N - 1], hFx, hFy, hvx, hvy, hP, hsum;
         site_physics<N, T>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
         T rec[RB::NVP];
@@ -338,6 +343,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
         const T vv = vx * vx + vy * vy, vF = vx * Fx + vy * Fy;
         const T base = T(3) * P - T(1.5) * vv;
+        // no wrap and no wall for any target: the site is inside the domain by one site
+        const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1;
         sfor<1, 9, 2>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int kb = k + 1;
@@ -354,7 +361,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             const T anti = -om * (fm - eqm) + am * Fm;
             const T pk = f[k] + sym + anti;
             const T pkb = f[kb] + sym - anti;
-            if (!edge) {
+            if (fast) {
                 const int dk = LD2Q9::ex(k) + nx * LD2Q9::ey(k);
                 FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), pk, LD2Q9::w(k), cf.fscale);
                 FStore<SF, T>::store(fout + (kb - 1) * n + (s0 - dk), pkb, LD2Q9::w(kb), cf.fscale);
@@ -389,7 +396,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             const T wk = T(LD2Q9::w(k));
             // source x - e_k is the neighbour in direction kbar
             const int kb = opp(k);
-            if (edge && ((wall0 >> kb) & 1u)) {
+            if (wallt && ((wall0 >> kb) & 1u)) {
                 // bounce-back: g_k(x, t+1) = g^eq_kbar(x, t); its S difference is zero
                 const T eu = -(T(LD2Q9::ex(k)) * r0[N - 1] + T(LD2Q9::ey(k)) * r0[N]);
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);

@@ -154,7 +154,9 @@ struct Fused3DTile {
     int *__restrict__ flag;
     T *sA, *sB;
     int nx, ny, nz, nxy, n, tid, x0, y0, z_lo, z_hi;
-    bool edge;
+    bool edge;      // the tile plus its 2-ring crosses a domain edge (indices wrap or clamp)
+    bool wallt;     // ... and that edge is a wall in x or y (stencils need wall tests)
+    bool tiny;      // the domain is narrower than a tile plus ring: wrap with a full modulo
     // own site in the plane, and this thread's ring site
     int tx, ty, gx0, gy0, sx, sy, sxy, bx, by, hx, hy, hxy;
     bool own_xy, ring_xy_ok;
@@ -173,6 +175,8 @@ struct Fused3DTile {
         z_lo = blockIdx.z * zchunk;
         z_hi = min(z_lo + zchunk, nz);
         edge = (x0 - 2 < 0) || (x0 + TX + 2 > nx) || (y0 - 2 < 0) || (y0 + TY + 2 > ny);
+        wallt = (g.wx && ((x0 - 2 < 0) || (x0 + TX + 2 > nx))) || (g.wy && ((y0 - 2 < 0) || (y0 + TY + 2 > ny)));
+        tiny = nx < TX + 4 || ny < TY + 4;
         tx = tid % TX;
         ty = tid / TX;
         gx0 = x0 + tx;
@@ -209,8 +213,8 @@ struct Fused3DTile {
                 const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
                 int gx = x0 + lx - 2, gy = y0 + ly - 2;
                 if (edge) {
-                    gx = g.wx ? min(max(gx, 0), nx - 1) : imod(gx, nx);
-                    gy = g.wy ? min(max(gy, 0), ny - 1) : imod(gy, ny);
+                    gx = g.wx ? min(max(gx, 0), nx - 1) : (tiny ? imod(gx, nx) : wrap(gx, nx));
+                    gy = g.wy ? min(max(gy, 0), ny - 1) : (tiny ? imod(gy, ny) : wrap(gy, ny));
                 }
                 const int s = gx + nx * gy + nxy * zw;
 #pragma unroll
@@ -260,7 +264,7 @@ struct Fused3DTile {
         const T *pp = sA + slotA(zb + 1) * Sh::A_SLOT;
         T *bbase = sB + slotB(zb) * Sh::B_SLOT;
         const bool zcheck = g.wz && (zb == 0 || zb == nz - 1);
-        const bool check = edge || zcheck;
+        const bool check = wallt || zcheck;
         // own site
         {
             const int s0 = sxy + nxy * zw;
@@ -286,7 +290,8 @@ struct Fused3DTile {
                 const T vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
                 const T vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
                 const T base = T(3) * P - T(1.5) * vv;
-                const bool fast = !check && !edge && zb >= 1 && zb <= nz - 2;
+                // no wrap and no wall for any target: the site is inside the domain by one site
+                const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && zw > 0 && zw < nz - 1;
                 sfor<1, 19, 2>([&](auto kc_) {
                     constexpr int k = decltype(kc_)::value;
                     const int kb = k + 1;
@@ -348,7 +353,7 @@ struct Fused3DTile {
 
     __device__ __forceinline__ void ch(int zc) {
         if (!own_xy) return;
-        const bool check = edge || (g.wz && (zc == 0 || zc == nz - 1));
+        const bool check = wallt || (g.wz && (zc == 0 || zc == nz - 1));
         const unsigned wall0 = check ? wall_mask3(g, gx0, gy0, zc) : 0u;
         const T *bm = sB + slotB(zc - 1) * Sh::B_SLOT;
         const T *b0 = sB + slotB(zc) * Sh::B_SLOT;
