@@ -53,6 +53,22 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+def max_over_ranks_of(x, world_size, device):
+    """Largest value of x over all ranks (the slowest replica sets the time)."""
+    if world_size == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(sites_per_rank, steps, n_components, world_size, ms_total_max):
+    """Whole-job MLUPS x N of independent replicas: all ranks' site updates / slowest rank's time."""
+    return world_size * sites_per_rank * steps * n_components / (ms_total_max * 1e-3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -134,11 +150,7 @@ def run_nfe(args):
             dist.barrier()
 
     def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks_of(x, ws, "cuda")
 
     def timed_steps(sim, K, W_, clocks=None):
         """Sum of per-step event times with an L2 flush before every step (ms)."""
@@ -283,8 +295,10 @@ def run_nfe(args):
             del q
 
     batched = None
+    precision = None
     if not args.no_extras:
         batched = batch_sweep_measure(nfe, torch, stream, args.batch_steps)
+        precision = precision_study(nfe, stream)
 
     s32 = path_summary(r32)
     s64 = path_summary(results["fp64"])
@@ -317,6 +331,7 @@ def run_nfe(args):
         "gpu_launches": r32["info"]["kernels_per_step"] * r32["K"],
         "extras": extras,
         "batched": batched,
+        "precision_study": precision,
         "clocks": r32["clocks"].summary() if r32["clocks"] is not None else None,
     }
     for r in results.values():
@@ -327,6 +342,37 @@ def run_nfe(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def precision_study(nfe, stream, n=128, steps=300):
+    """Four Janus drops (the 256^3 layout scaled to n^3), FP32 compute with FP32 / FP16 / BF16
+    storage of f against the FP64 path: volume-fraction error, Laplace-pressure error of each
+    drop (mean P inside minus mean P in the matrix) and momentum drift per site."""
+    p = W.janus_3d(n=n, radius=32.0 * n / 256.0, seed=1004)
+    R = p["radius"]
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    dists = [np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) for cx, cy, cz in p["centres"]]
+    matrix = np.all([d > R + 6 for d in dists], axis=0)
+
+    def run(prec):
+        with nfe.Sim(p, prec, stream=stream.cuda_stream, scale_exp=10) as s:
+            s.set_fields(p["C0"])
+            s.step(steps)
+            C, v, P = s.fields()
+            d = s.diagnostics()
+        dP = np.array([P[dd < R - 4].mean() - P[matrix].mean() for dd in dists])
+        return C, P, dP, np.abs(d["momentum"]).max() / n ** 3
+
+    C64, P64, dP64, m64 = run("fp64")
+    out = {"workload": f"4 Janus drops {n}^3 (radius {R:g}), {steps} steps, FP32 compute vs the FP64 path",
+           "fp64": {"momentum_per_site": m64, "laplace_dP": [float(v) for v in dP64]}}
+    for prec in ("fp32", "f16", "bf16"):
+        C, P, dP, m = run(prec)
+        out[prec] = {"max_abs_C_err": float(np.abs(C - C64).max()),
+                     "max_rel_P_err": float(np.abs(P - P64).max() / np.abs(P64).max()),
+                     "laplace_rel_err": float(np.abs(dP - dP64).max() / np.abs(dP64).max()),
+                     "momentum_per_site": m}
+    return out
 
 
 def batch_sweep_measure(nfe, torch, stream, steps):
