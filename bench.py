@@ -69,6 +69,25 @@ def replica_throughput(sites_per_rank, steps, n_components, world_size, ms_total
     return world_size * sites_per_rank * steps * n_components / (ms_total_max * 1e-3) / 1e6
 
 
+def _captured_traffic(variant):
+    """DRAM bytes per launch from the committed ncu capture of the fused D2Q9 kernel, or None
+    when the kernel sources changed since that capture or another tile shape is in use."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic_fused2d_spinodal512_N4.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        rec = json.load(fh)
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2605_22214_gb300", "csrc")
+    for f in ("nfe_fused2d.cuh", "nfe_kernels.cuh", "nfe_internal.h"):
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != rec["source_sha256"] or variant != rec["variant"]:
+        return None
+    return rec["dram_bytes_per_launch"]
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -244,9 +263,10 @@ def run_nfe(args):
         else:
             bps = prec_bytes * ((N - 1) + D + (N - 1) + (N - 1))
         ach = bps * n / (kt[dom][1] * 1e-3) / 1e9
+        traffic = _captured_traffic(r["info"]["variant"]) if r is r32 else None
         return dict(bound="hbm", kernel=dom, variant=r["info"]["variant"], bytes_per_site=bps, achieved=round(ach, 1), peak=hbm,
-                    unit="GB/s", frac=round(ach / hbm, 4), peak_source=peak_kind, traffic=None,
-                    kernel_ms=round(kt[dom][1], 5))
+                    unit="GB/s", frac=round(ach / hbm, 4), peak_source=peak_kind, traffic=traffic,
+                    kernel_ms=round(kt[dom][1], 5), algorithmic_bytes=bps * n)
 
     def path_summary(r):
         mlups = ws * n / (r["ms_step"] * 1e-3) / 1e6
