@@ -9,6 +9,8 @@
 // the barrier can never hang the GPU.
 #include <cuda_runtime.h>
 
+#include <cstddef>
+
 #include "nfe_batch.h"
 #include "nfe_fused2d.cuh"
 
@@ -49,22 +51,26 @@ __device__ __noinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, 
     __shared__ __align__(16) BatchSim<T> d;
     {
         static_assert(sizeof(BatchSim<T>) % 16 == 0, "16-byte copies");
+        constexpr size_t used = offsetof(BatchSim<T>, coef) + offsetof(Coef<T>, q4c);
+        constexpr int n16 = int((used + 15) / 16);
+        static_assert(n16 * 16 <= sizeof(BatchSim<T>), "copy inside the descriptor");
         const int4 *src = reinterpret_cast<const int4 *>(&dg);
         int4 *dst = reinterpret_cast<int4 *>(&d);
-        for (int i = threadIdx.x; i < int(sizeof(BatchSim<T>) / 16); i += blockDim.x) dst[i] = src[i];
+        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
     const SF *fin = static_cast<const SF *>(d.f[cur]);
     SF *fout = static_cast<SF *>(d.f[1 - cur]);
     const T *Cin = static_cast<const T *>(d.C[cur]);
     T *Cout = static_cast<T *>(d.C[1 - cur]);
+    // L2-only loads: inside one launch, other CTAs' writes of the previous step must not be
+    // read from a stale L1 line.  The degree-4 table is read from device memory: loop-invariant
+    // loads of it from the shared descriptor would be hoisted into registers.
     switch (d.N) {
-        // L2-only loads: inside one launch, other CTAs' writes of the previous step must not be
-        // read from a stale L1 line
-        case 2: fused2d_tile<2, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        case 3: fused2d_tile<3, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        case 4: fused2d_tile<4, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        default: fused2d_tile<5, T, SF, TX, TY, true>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 2: fused2d_tile<2, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 3: fused2d_tile<3, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 4: fused2d_tile<4, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        default: fused2d_tile<5, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
     }
 }
 

@@ -8,15 +8,17 @@
 namespace nfe {
 
 // One simulation as the batched kernel sees it (device memory, read-only).
+// The coefficients come last: the kernel copies the descriptor into shared memory
+// up to (not including) Coef::q4c, since it reads the degree-4 table from device memory.
 template <typename T>
 struct __align__(16) BatchSim {
     Geom geom;
     int N;
     int pad_;
-    Coef<T> coef;
     void *f[2];
     void *C[2];
     int *flag;
+    Coef<T> coef;
 };
 
 // Grid-barrier state (device memory): arrival count, generation, error word.

@@ -15,6 +15,9 @@
 // Only f (8 populations) and the N-1 evolved C are read from and written to
 // HBM; every other quantity lives in registers or shared memory.  CTAs whose
 // tile plus ring is inside the domain take a path without wrap or wall tests.
+// The Cahn-Hilliard gather with bounce-back is chosen from the site's own wall
+// mask, never from the tile: its wall-free form is compiled separately, and a
+// per-tile choice would let a site's arithmetic depend on the tile shape.
 #pragma once
 
 #include "nfe_kernels.cuh"
@@ -128,7 +131,7 @@ __device__ __forceinline__ void stencil2d(const T *sA, int acount, int ia, unsig
 }
 
 // Phase 2 at one site: S, F, v, P from the stencil and f.  f must hold f_1..f_8.
-template <int N, typename T>
+template <int N, typename T, int Q4>
 __device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N], const T (&lap)[N],
                                              const T (&gx)[N], const T (&gy)[N], T gEx, T gEy,
                                              const T (&f)[9], T (&S)[N - 1], T &Fx, T &Fy,
@@ -161,7 +164,7 @@ __device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N],
     }
     Fx += cf.fb[0]; Fy += cf.fb[1];
     T q[N - 1];
-    flux_poly<N, T>(c, cf, q);
+    flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
     // moments (Eqs. 37-38), rho = 1
@@ -194,7 +197,7 @@ __device__ __forceinline__ T fload(const SF *p, double w, T finv) {
     }
 }
 
-template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY = false>
+template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4>
 __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, const SF *__restrict__ fin,
                                              SF *__restrict__ fout, const T *__restrict__ Cin,
                                              T *__restrict__ Cout, int *__restrict__ flag,
@@ -308,7 +311,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const int ia = (ty + 2) * Sh::AX + (tx + 2);
         if (wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
         else       stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
-        site_physics<N, T>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
+        site_physics<N, T, Q4>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
         T rec[RB::NVP];
 #pragma unroll
         for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 1 + a] = S[a]; }
@@ -326,7 +329,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         if (wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
         else       stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
         T hS[N - 1], hFx, hFy, hvx, hvy, hP, hsum;
-        site_physics<N, T>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
+        site_physics<N, T, Q4>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
         T rec[RB::NVP];
 #pragma unroll
         for (int a = 0; a < N - 1; ++a) { rec[a] = hc[a]; rec[N + 1 + a] = hS[a]; }
@@ -359,21 +362,29 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             const T fm = T(0.5) * (f[k] - f[kb]);
             const T sym = -op * (fp - eqp) + ap * Fp;
             const T anti = -om * (fm - eqm) + am * Fm;
-            const T pk = f[k] + sym + anti;
-            const T pkb = f[kb] + sym - anti;
-            if (fast) {
-                const int dk = LD2Q9::ex(k) + nx * LD2Q9::ey(k);
-                FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), pk, LD2Q9::w(k), cf.fscale);
-                FStore<SF, T>::store(fout + (kb - 1) * n + (s0 - dk), pkb, LD2Q9::w(kb), cf.fscale);
-            } else {
-                if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, pk, LD2Q9::w(kb), cf.fscale);
-                else FStore<SF, T>::store(fout + (k - 1) * n + (wrap(sx + LD2Q9::ex(k), nx) + nx * wrap(sy + LD2Q9::ey(k), ny)),
-                                          pk, LD2Q9::w(k), cf.fscale);
-                if ((wall0 >> kb) & 1u) FStore<SF, T>::store(fout + (k - 1) * n + s0, pkb, LD2Q9::w(k), cf.fscale);
-                else FStore<SF, T>::store(fout + (kb - 1) * n + (wrap(sx - LD2Q9::ex(k), nx) + nx * wrap(sy - LD2Q9::ey(k), ny)),
-                                          pkb, LD2Q9::w(kb), cf.fscale);
-            }
+            // post-collision values replace f in place (each pair is read once)
+            f[k] = f[k] + sym + anti;
+            f[kb] = f[kb] + sym - anti;
         });
+        // one branch around the whole store block: inside the unrolled loop the compiler
+        // would predicate both forms for every site
+        if (fast) {
+            sfor<1, 9, 1>([&](auto kc_) {
+                constexpr int k = decltype(kc_)::value;
+                constexpr int dk0 = LD2Q9::ex(k);
+                const int dk = dk0 + nx * LD2Q9::ey(k);
+                FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), f[k], LD2Q9::w(k), cf.fscale);
+            });
+        } else {
+            sfor<1, 9, 1>([&](auto kc_) {
+                constexpr int k = decltype(kc_)::value;
+                constexpr int kb = opp(k);
+                // halfway bounce-back: f_kbar(x, t+1) = post_k(x)
+                if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k], LD2Q9::w(kb), cf.fscale);
+                else FStore<SF, T>::store(fout + (k - 1) * n + (wrap(sx + LD2Q9::ex(k), nx) + nx * wrap(sy + LD2Q9::ey(k), ny)),
+                                          f[k], LD2Q9::w(k), cf.fscale);
+            });
+        }
     }
     __syncthreads();
 
@@ -391,26 +402,33 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         // FP32 the rest-population share C s_0 is not lost against 1 (mass-exact update)
         for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * vv0); lapS[e] = T(0); }
         constexpr int offB[9] = {0, 1, -1, TX + 2, -(TX + 2), TX + 3, -(TX + 3), -(TX + 2) + 1, (TX + 2) - 1};
-        sfor<1, 9, 1>([&](auto kc_) {
-            constexpr int k = decltype(kc_)::value;
-            const T wk = T(LD2Q9::w(k));
-            // source x - e_k is the neighbour in direction kbar
-            const int kb = opp(k);
-            if (wallt && ((wall0 >> kb) & 1u)) {
-                // bounce-back: g_k(x, t+1) = g^eq_kbar(x, t); its S difference is zero
-                const T eu = -(T(LD2Q9::ex(k)) * r0[N - 1] + T(LD2Q9::ey(k)) * r0[N]);
-                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
+        // the wall-free form carries no bounce-back code (no predicated second path)
+        auto gather = [&](auto chk_) {
+            constexpr bool CHECK = decltype(chk_)::value;
+            sfor<1, 9, 1>([&](auto kc_) {
+                constexpr int k = decltype(kc_)::value;
+                const T wk = T(LD2Q9::w(k));
+                // source x - e_k is the neighbour in direction kbar
+                const int kb = opp(k);
+                if (CHECK && ((wall0 >> kb) & 1u)) {
+                    // bounce-back: g_k(x, t+1) = g^eq_kbar(x, t); its S difference is zero
+                    const T eu = -(T(LD2Q9::ex(k)) * r0[N - 1] + T(LD2Q9::ey(k)) * r0[N]);
+                    const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
 #pragma unroll
-                for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;
-            } else {
-                T r[RB::NVP];
-                srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib + offB[kb], r);
-                const T eu = T(LD2Q9::ex(k)) * r[N - 1] + T(LD2Q9::ey(k)) * r[N];
-                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (r[N - 1] * r[N - 1] + r[N] * r[N]));
+                    for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;
+                } else {
+                    T r[RB::NVP];
+                    srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib + offB[kb], r);
+                    const T eu = T(LD2Q9::ex(k)) * r[N - 1] + T(LD2Q9::ey(k)) * r[N];
+                    const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (r[N - 1] * r[N - 1] + r[N] * r[N]));
 #pragma unroll
-                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 1 + e] - r0[N + 1 + e]); }
-            }
-        });
+                    for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 1 + e] - r0[N + 1 + e]); }
+                }
+            });
+        };
+        // decided per site (not per tile), so a site runs the same code under every tile shape
+        if (wall0) gather(std::true_type{});
+        else gather(std::false_type{});
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) {
@@ -427,26 +445,26 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
 // Minimum resident CTAs per SM requested from the register allocator.
 template <typename T, int NT> struct Fused2DOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 8 : NT <= 256 ? 4 : 2) : 1; };
 
-template <int N, typename T, typename SF, int TX, int TY>
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
 __global__ void __launch_bounds__(TX * TY, (Fused2DOcc<T, TX * TY>::value))
 k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
           const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused2d_tile<N, T, SF, TX, TY>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
+    fused2d_tile<N, T, SF, TX, TY, false, Q4>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
 }
 
-template <int N, typename T, typename SF, int TX, int TY>
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
 cudaError_t launch_fused2d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Fused2DShape<N, T, TX, TY>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY, Q4>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused2d<N, T, SF, TX, TY><<<grid, TX * TY, Sh::BYTES, st>>>(
+    k_fused2d<N, T, SF, TX, TY, Q4><<<grid, TX * TY, Sh::BYTES, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
         static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]), b.flag);
     return cudaGetLastError();
@@ -462,9 +480,9 @@ struct Fused2DLaunch {
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         switch (variant) {
-            case 0: return launch_fused2d<N, T, SF, 32, 4>(g, cf, b, cur, st);
-            case 1: return launch_fused2d<N, T, SF, 32, 8>(g, cf, b, cur, st);
-            default: return launch_fused2d<N, T, SF, 32, 16>(g, cf, b, cur, st);
+            case 0: return launch_fused2d<N, T, SF, 32, 4, Q4_GLOBAL>(g, cf, b, cur, st);
+            case 1: return launch_fused2d<N, T, SF, 32, 8, Q4_GLOBAL>(g, cf, b, cur, st);
+            default: return launch_fused2d<N, T, SF, 32, 16, Q4_GLOBAL>(g, cf, b, cur, st);
         }
     }
     static const Ops *ops(int prec) {

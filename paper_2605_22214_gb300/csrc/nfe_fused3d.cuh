@@ -74,7 +74,7 @@ __device__ __forceinline__ void stencil3d(const T *pm, const T *p0, const T *pp,
     gE[0] = T(3) * acc[N - 1][1]; gE[1] = T(3) * acc[N - 1][2]; gE[2] = T(3) * acc[N - 1][3];
 }
 
-template <int N, typename T>
+template <int N, typename T, int Q4>
 __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N], const T (&lap)[N],
                                                const T (&g)[N][3], const T (&gE)[3], const T (&f)[19],
                                                T (&S)[N - 1], T (&F)[3], T (&v)[3], T &P) {
@@ -105,7 +105,7 @@ __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N
     }
     F[0] += cf.fb[0]; F[1] += cf.fb[1]; F[2] += cf.fb[2];
     T q[N - 1];
-    flux_poly<N, T>(c, cf, q);
+    flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
     T j0 = T(0), j1 = T(0), j2 = T(0), sumf = T(0);
@@ -136,7 +136,7 @@ __device__ __forceinline__ unsigned wall_mask3(const Geom &g, int x, int y, int 
 }
 
 // Per-thread state of one CTA of the fused D3Q19 step, and its phases.
-template <int N, typename T, typename SF, int TX, int TY>
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
 struct Fused3DTile {
     using Sh = Fused3DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
@@ -256,7 +256,8 @@ struct Fused3DTile {
         }
     }
 
-    __device__ __forceinline__ void fill_B(int zb, bool collide, const T (&fo)[19], const T (&fr)[19]) {
+    // fo is consumed: the collision leaves post-collision values in it
+    __device__ __forceinline__ void fill_B(int zb, bool collide, T (&fo)[19], const T (&fr)[19]) {
         if (g.wz && (zb < 0 || zb >= nz)) return;      // sources beyond a wall bounce back
         const int zw = imod(zb, nz);
         const T *pm = sA + slotA(zb - 1) * Sh::A_SLOT;
@@ -268,14 +269,14 @@ struct Fused3DTile {
         // own site
         {
             const int s0 = sxy + nxy * zw;
-            const T (&f)[19] = fo;
+            T (&f)[19] = fo;
             const unsigned wall0 = check ? wall_mask3(g, gx0, gy0, zb) : 0u;
             T c[N], lap[N], gr[N][3], gE[3];
             const int ia = (ty + 2) * Sh::AX + (tx + 2);
             if (check) stencil3d<N, T, Sh::AX, true>(pm, p0, pp, Sh::APLANE, ia, wall0, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::AX, false>(pm, p0, pp, Sh::APLANE, ia, 0u, c, lap, gr, gE);
             T S[N - 1], F[3], v[3], P;
-            site_physics3d<N, T>(cf, c, lap, gr, gE, f, S, F, v, P);
+            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, f, S, F, v, P);
             T rec[RB::NVP];
 #pragma unroll
             for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
@@ -306,29 +307,33 @@ struct Fused3DTile {
                     const T fm = T(0.5) * (f[k] - f[kb]);
                     const T sym = -op * (fp - eqp) + ap * Fp;
                     const T anti = -om * (fm - eqm) + am * Fm;
-                    const T pk = f[k] + sym + anti;
-                    const T pkb = f[kb] + sym - anti;
-                    if (fast) {
-                        const int dk = LD3Q19::ex(k) + nx * LD3Q19::ey(k) + nxy * LD3Q19::ez(k);
-                        FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), pk, LD3Q19::w(k), cf.fscale);
-                        FStore<SF, T>::store(fout + (kb - 1) * n + (s0 - dk), pkb, LD3Q19::w(kb), cf.fscale);
-                    } else {
+                    // post-collision values replace f in place (each pair is read once)
+                    f[k] = f[k] + sym + anti;
+                    f[kb] = f[kb] + sym - anti;
+                });
+                // one branch around the whole store block: inside the unrolled loop the
+                // compiler would predicate both forms for every site
+                if (fast) {
+                    sfor<1, 19, 1>([&](auto kc_) {
+                        constexpr int k = decltype(kc_)::value;
+                        constexpr int dk0 = LD3Q19::ex(k);
+                        const int dk = dk0 + nx * LD3Q19::ey(k) + nxy * LD3Q19::ez(k);
+                        FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), f[k], LD3Q19::w(k), cf.fscale);
+                    });
+                } else {
+                    sfor<1, 19, 1>([&](auto kc_) {
+                        constexpr int k = decltype(kc_)::value;
+                        constexpr int kb = opp(k);
                         if ((wall0 >> k) & 1u) {
-                            FStore<SF, T>::store(fout + (kb - 1) * n + s0, pk, LD3Q19::w(kb), cf.fscale);
+                            // halfway bounce-back: f_kbar(x, t+1) = post_k(x)
+                            FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k], LD3Q19::w(kb), cf.fscale);
                         } else {
                             const int t = wrap(sx + LD3Q19::ex(k), nx) + nx * wrap(sy + LD3Q19::ey(k), ny) +
                                           nxy * wrap(zw + LD3Q19::ez(k), nz);
-                            FStore<SF, T>::store(fout + (k - 1) * n + t, pk, LD3Q19::w(k), cf.fscale);
+                            FStore<SF, T>::store(fout + (k - 1) * n + t, f[k], LD3Q19::w(k), cf.fscale);
                         }
-                        if ((wall0 >> kb) & 1u) {
-                            FStore<SF, T>::store(fout + (k - 1) * n + s0, pkb, LD3Q19::w(k), cf.fscale);
-                        } else {
-                            const int t = wrap(sx - LD3Q19::ex(k), nx) + nx * wrap(sy - LD3Q19::ey(k), ny) +
-                                          nxy * wrap(zw - LD3Q19::ez(k), nz);
-                            FStore<SF, T>::store(fout + (kb - 1) * n + t, pkb, LD3Q19::w(kb), cf.fscale);
-                        }
-                    }
-                });
+                    });
+                }
             }
         }
         // ring site
@@ -340,7 +345,7 @@ struct Fused3DTile {
             if (check) stencil3d<N, T, Sh::AX, true>(pm, p0, pp, Sh::APLANE, ia, wall, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::AX, false>(pm, p0, pp, Sh::APLANE, ia, 0u, c, lap, gr, gE);
             T S[N - 1], F[3], v[3], P;
-            site_physics3d<N, T>(cf, c, lap, gr, gE, f, S, F, v, P);
+            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, f, S, F, v, P);
             T rec[RB::NVP];
 #pragma unroll
             for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
@@ -351,10 +356,8 @@ struct Fused3DTile {
         }
     }
 
-    __device__ __forceinline__ void ch(int zc) {
-        if (!own_xy) return;
-        const bool check = wallt || (g.wz && (zc == 0 || zc == nz - 1));
-        const unsigned wall0 = check ? wall_mask3(g, gx0, gy0, zc) : 0u;
+    template <bool CHECK>
+    __device__ __forceinline__ void ch_impl(int zc, unsigned wall0) {
         const T *bm = sB + slotB(zc - 1) * Sh::B_SLOT;
         const T *b0 = sB + slotB(zc) * Sh::B_SLOT;
         const T *bp = sB + slotB(zc + 1) * Sh::B_SLOT;
@@ -370,7 +373,7 @@ struct Fused3DTile {
             constexpr int k = decltype(kc_)::value;
             const T wk = T(LD3Q19::w(k));
             const int kb = opp(k);                  // source x - e_k = x + e_kbar
-            if (check && ((wall0 >> kb) & 1u)) {
+            if (CHECK && ((wall0 >> kb) & 1u)) {
                 const T eu = -(T(LD3Q19::ex(k)) * r0[N - 1] + T(LD3Q19::ey(k)) * r0[N] + T(LD3Q19::ez(k)) * r0[N + 1]);
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
 #pragma unroll
@@ -395,6 +398,15 @@ struct Fused3DTile {
             bad |= !isfinite(out);
         }
         if (bad) atomicOr(flag, 1);
+    }
+
+    // the wall-free form carries no bounce-back code (no predicated second path); the form is
+    // decided per site (not per tile), so a site runs the same code under every tile shape
+    __device__ __forceinline__ void ch(int zc) {
+        if (!own_xy) return;
+        const unsigned wall0 = (wallt || (g.wz && (zc == 0 || zc == nz - 1))) ? wall_mask3(g, gx0, gy0, zc) : 0u;
+        if (wall0) ch_impl<true>(zc, wall0);
+        else ch_impl<false>(zc, 0u);
     }
 
     __device__ __forceinline__ void march() {
@@ -429,21 +441,30 @@ struct Fused3DTile {
     }
 };
 
-template <int N, typename T, typename SF, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY)
+// Minimum resident CTAs per SM for the register allocator: as many as the shared
+// memory admits, at most 512 threads per SM in FP32 (128 registers a thread).
+template <int N, typename T, int TX, int TY>
+struct Fused3DOcc {
+    static constexpr int by_smem = int((227 * 1024) / (Fused3DShape<N, T, TX, TY>::BYTES + 1024));
+    static constexpr int by_regs = sizeof(T) == 4 ? 512 / (TX * TY) : 256 / (TX * TY);
+    static constexpr int value = by_smem < 1 ? 1 : (by_smem < by_regs ? by_smem : by_regs);
+};
+
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
+__global__ void __launch_bounds__(TX * TY, (Fused3DOcc<N, T, TX, TY>::value))
 k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
           const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag, int zchunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Fused3DTile<N, T, SF, TX, TY> t(g, cf, fin, fout, Cin, Cout, flag, smem_raw, zchunk);
+    Fused3DTile<N, T, SF, TX, TY, Q4> t(g, cf, fin, fout, Cin, Cout, flag, smem_raw, zchunk);
     t.march();
 }
 
-template <int N, typename T, typename SF, int TX, int TY>
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
 cudaError_t launch_fused3d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Fused3DShape<N, T, TX, TY>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused3d<N, T, SF, TX, TY>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused3d<N, T, SF, TX, TY, Q4>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
         attr_done = true;
@@ -455,7 +476,7 @@ cudaError_t launch_fused3d(const Geom &g, const Coef<T> &cf, const Buffers &b, i
     const int zchunk = (g.nz + chunks - 1) / chunks;
     chunks = (g.nz + zchunk - 1) / zchunk;
     const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
-    k_fused3d<N, T, SF, TX, TY><<<grid, TX * TY, Sh::BYTES, st>>>(
+    k_fused3d<N, T, SF, TX, TY, Q4><<<grid, TX * TY, Sh::BYTES, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
         static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk);
     return cudaGetLastError();
@@ -469,9 +490,9 @@ struct Fused3DLaunch {
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         if constexpr (kWideFits) {
-            if (variant == 1) return launch_fused3d<N, T, SF, 32, 8>(g, cf, b, cur, st);
+            if (variant == 1) return launch_fused3d<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
         }
-        return launch_fused3d<N, T, SF, 32, 4>(g, cf, b, cur, st);
+        return launch_fused3d<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
     }
     static const Ops *ops(int prec) {
         using B = Launch<LD3Q19, N, T, SF>;

@@ -137,6 +137,8 @@ void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
     c.has_q4 = s.tab.omega != 0.0 ? 1 : 0;
     c.nonconservative = (p.flags & NFE_NONCONSERVATIVE_FORCE) ? 1 : 0;
     c.q4 = static_cast<const T *>(s.q4dev);
+    if (N <= kQ4InlineMaxN)
+        for (size_t j = 0; j < s.tab.q4.size(); ++j) c.q4c[j] = T(s.tab.q4[j]);
 }
 
 nfe_status free_all(nfe_sim *s) {

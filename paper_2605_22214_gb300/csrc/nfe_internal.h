@@ -16,6 +16,10 @@ constexpr int kMaxMono2 = kMaxN * (kMaxN + 1) / 2;   // degree-2 monomials in 8 
 // Degree-4 monomials a <= b <= c <= d in N variables: C(N+3, 4).
 __host__ __device__ constexpr int mono4_count(int n) { return n * (n + 1) * (n + 2) * (n + 3) / 24; }
 
+// Up to N = 5 the degree-4 coefficients also travel with the kernel parameters (constant bank).
+constexpr int kQ4InlineMaxN = 5;
+constexpr int kQ4Inline = (kQ4InlineMaxN - 1) * mono4_count(kQ4InlineMaxN);   // 280
+
 // Grid geometry as the kernels see it.
 struct Geom {
     int nx, ny, nz;
@@ -41,7 +45,8 @@ struct Coef {
     T finv;                       // 1 / fscale
     int has_q4;                   // Omega != 0: degree-4 part present
     int nonconservative;          // force of Eq. 31 instead of Eq. 34
-    const T *q4;                  // (N-1) x mono4_count(N), device memory, or nullptr
+    const T *q4;                  // (N-1) x mono4_count(N), device memory, or nullptr (Omega = 0)
+    T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 5); last member
 };
 
 // One kernel kind for profiling.

@@ -126,7 +126,13 @@ __device__ __forceinline__ T bulk_energy(const T (&c)[N], const Coef<T> &cf) {
     return E;
 }
 
-template <int N, typename T>
+// Where the coefficients of the degree-4 (stabiliser) part of q are read (the part is
+// skipped when cf.has_q4 is 0): device memory, or the kernel's parameter block when
+// N <= kQ4InlineMaxN (saves a load per term; the D3Q19 step gains, while in the D2Q9 step
+// the extra register pressure costs more than it saves).
+enum Q4Source { Q4_GLOBAL = 0, Q4_PARAM = 1 };
+
+template <int N, typename T, int Q4 = Q4_GLOBAL>
 __device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T (&q)[N - 1]) {
     // q_e(C): degree-2 monomials C_a C_b (a <= b) in nested-loop order, and the
     // degree-4 monomials a <= b <= c <= d of the stabiliser part when Omega != 0.
@@ -157,7 +163,10 @@ __device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T 
                     for (int d1 = d0; d1 < N; ++d1) {
                         T p = pabc * c[d1];
 #pragma unroll
-                        for (int e = 0; e < N - 1; ++e) q[e] += __ldg(cf.q4 + e * M4 + j) * p;
+                        for (int e = 0; e < N - 1; ++e) {
+                            if constexpr (Q4 == Q4_PARAM && N <= kQ4InlineMaxN) q[e] += cf.q4c[e * M4 + j] * p;
+                            else q[e] += __ldg(cf.q4 + e * M4 + j) * p;
+                        }
                         ++j;
                     }
                 }
