@@ -70,8 +70,9 @@ def replica_throughput(sites_per_rank, steps, n_components, world_size, ms_total
 
 
 def _captured_traffic(variant):
-    """DRAM bytes per launch from the committed ncu capture of the fused D2Q9 kernel, or None
-    when the kernel sources changed since that capture or another tile shape is in use."""
+    """DRAM bytes per launch of the fused D2Q9 kernel with tile shape `variant`, from the
+    committed ncu capture (one value per tile shape), or None when the kernel sources changed
+    since that capture or that shape was not captured."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic_fused2d_spinodal512_N4.json")
     if not os.path.exists(path):
@@ -83,9 +84,9 @@ def _captured_traffic(variant):
     for f in ("nfe_fused2d.cuh", "nfe_kernels.cuh", "nfe_internal.h"):
         with open(os.path.join(src, f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != rec["source_sha256"] or variant != rec["variant"]:
+    if h.hexdigest() != rec["source_sha256"]:
         return None
-    return rec["dram_bytes_per_launch"]
+    return rec["dram_bytes_per_launch"].get(str(variant))
 
 
 def _dist():

@@ -85,6 +85,10 @@ __device__ __forceinline__ int wrap(int v, int n) {
 
 __device__ __forceinline__ int imod(int v, int n) { return ((v % n) + n) % n; }
 
+// Periodic index of a tile or ring coordinate v in [-2, n + tile + 2): a compare and an add,
+// unless the domain is narrower than a tile plus ring (then a full modulo).
+__device__ __forceinline__ int pwrap(int v, int n, bool tiny) { return tiny ? imod(v, n) : wrap(v, n); }
+
 // Stencil of one site from record A at local index ia (row pitch AX).  `wall`
 // holds bit k set when x + e_k lies beyond a wall (then that term is dropped).
 template <int N, typename T, int AX, bool CHECK>
@@ -221,8 +225,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     const int tx = tid % TX, ty = tid / TX;
     const int gx0 = x0 + tx, gy0 = y0 + ty;
     const bool own = gx0 < nx && gy0 < ny;             // ragged far edge: duplicates only
-    const int sx = edge ? imod(gx0, nx) : gx0;         // wrapped (periodic duplicates)
-    const int sy = edge ? imod(gy0, ny) : gy0;
+    const int sx = edge ? pwrap(gx0, nx, tiny) : gx0;  // wrapped (periodic duplicates)
+    const int sy = edge ? pwrap(gy0, ny, tiny) : gy0;
     const int s0 = sx + nx * sy;
     T f[9];
     f[0] = T(0);
@@ -240,7 +244,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     int hs = hx + nx * hy;
     if (edge && has_ring) {
         if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) ring_ok = false;
-        hs = imod(hx, nx) + nx * imod(hy, ny);
+        hs = pwrap(hx, nx, tiny) + nx * pwrap(hy, ny, tiny);
     }
     if (wallt && has_ring) {
         sfor<1, 9, 1>([&](auto kc_) {
@@ -269,8 +273,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             if (edge) {
                 // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
                 // such entries are never used by a real site's stencil
-                gx = g.wx ? min(max(gx, 0), nx - 1) : (tiny ? imod(gx, nx) : wrap(gx, nx));
-                gy = g.wy ? min(max(gy, 0), ny - 1) : (tiny ? imod(gy, ny) : wrap(gy, ny));
+                gx = g.wx ? min(max(gx, 0), nx - 1) : pwrap(gx, nx, tiny);
+                gy = g.wy ? min(max(gy, 0), ny - 1) : pwrap(gy, ny, tiny);
             }
             const int s = gx + nx * gy;
 #pragma unroll
@@ -346,6 +350,14 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
         const T vv = vx * vx + vy * vy, vF = vx * Fx + vy * Fy;
         const T base = T(3) * P - T(1.5) * vv;
+        // TRT with forcing (Eqs. 23-30) regrouped so that per-site factors are formed once:
+        // for a pair (k, kbar), with s = f_k + f_kbar and d = f_k - f_kbar,
+        //   sym  = w_k [X + e.v (Y e.v + Z e.F)] - (op / 2) s
+        //   anti = w_k (U e.v + V e.F) - (om / 2) d
+        // where X = op (3P - 1.5 v.v) - 3 ap v.F, Y = 4.5 op, Z = 9 ap, U = 3 om, V = 3 am;
+        // w_k X ... w_k V are shared by all pairs of one weight class.
+        const T hop = T(0.5) * op, hom = T(0.5) * om;
+        const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
         // no wrap and no wall for any target: the site is inside the domain by one site
         const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1;
         sfor<1, 9, 2>([&](auto kc_) {
@@ -354,14 +366,9 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             const T wk = T(LD2Q9::w(k));
             const T eu = T(LD2Q9::ex(k)) * vx + T(LD2Q9::ey(k)) * vy;
             const T eF = T(LD2Q9::ex(k)) * Fx + T(LD2Q9::ey(k)) * Fy;
-            const T eqp = wk * (base + T(4.5) * eu * eu);
-            const T eqm = wk * (T(3) * eu);
-            const T Fp = wk * (T(9) * eu * eF - T(3) * vF);
-            const T Fm = wk * (T(3) * eF);
-            const T fp = T(0.5) * (f[k] + f[kb]);
-            const T fm = T(0.5) * (f[k] - f[kb]);
-            const T sym = -op * (fp - eqp) + ap * Fp;
-            const T anti = -om * (fm - eqm) + am * Fm;
+            const T sp = f[k] + f[kb], dm = f[k] - f[kb];
+            const T sym = (wk * X + eu * ((wk * Y) * eu + (wk * Z) * eF)) - hop * sp;
+            const T anti = ((wk * U) * eu + (wk * V) * eF) - hom * dm;
             // post-collision values replace f in place (each pair is read once)
             f[k] = f[k] + sym + anti;
             f[kb] = f[kb] + sym - anti;

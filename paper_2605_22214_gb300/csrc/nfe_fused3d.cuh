@@ -24,7 +24,7 @@ struct Fused3DShape {
     static constexpr int AX = TX + 4, AY = TY + 4, APLANE = AX * AY;
     static constexpr int BX = TX + 2, BY = TY + 2, BPLANE = BX * BY;
     using RA = SRec<T, N>;               // evolved C (N-1), E_B
-    using RB = SRec<T, 2 * N + 1>;       // evolved C (N-1), vx, vy, vz, S (N-1)
+    using RB = SRec<T, 2 * N + 2>;       // evolved C (N-1), vx, vy, vz, S (N-1), |v|^2
     static constexpr int A_SLOT = RA::NVP * APLANE;
     static constexpr int B_SLOT = RB::NVP * BPLANE;
     static constexpr size_t BYTES = sizeof(T) * size_t(5 * A_SLOT + 3 * B_SLOT);
@@ -182,8 +182,8 @@ struct Fused3DTile {
         gx0 = x0 + tx;
         gy0 = y0 + ty;
         own_xy = gx0 < nx && gy0 < ny;
-        sx = edge ? imod(gx0, nx) : gx0;
-        sy = edge ? imod(gy0, ny) : gy0;
+        sx = edge ? pwrap(gx0, nx, tiny) : gx0;
+        sy = edge ? pwrap(gy0, ny, tiny) : gy0;
         sxy = sx + nx * sy;
         bx = 0;
         by = 0;
@@ -194,8 +194,11 @@ struct Fused3DTile {
         hx = x0 + bx - 1;
         hy = y0 + by - 1;
         ring_xy_ok = has_ring && !(edge && ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))));
-        hxy = edge ? imod(hx, nx) + nx * imod(hy, ny) : hx + nx * hy;
+        hxy = edge ? pwrap(hx, nx, tiny) + nx * pwrap(hy, ny, tiny) : hx + nx * hy;
     }
+
+    // Periodic plane index of z in [z_lo - 2, z_hi + 2) without a division.
+    __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
 
     // Loads are issued one plane ahead (load_A / load_F) and consumed by fill_A /
     // fill_B in the next iteration, so HBM latency overlaps the previous plane's work.
@@ -205,7 +208,7 @@ struct Fused3DTile {
     // ch: Cahn-Hilliard update of plane zc from B-planes zc-1..zc+1.
     __device__ __forceinline__ void load_A(int za, T (&cl)[ITER][N - 1]) {
         if (g.wz && (za < 0 || za >= nz)) return;
-        const int zw = imod(za, nz);
+        const int zw = zwrap(za);
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
             const int i = tid + it * NT;
@@ -213,8 +216,8 @@ struct Fused3DTile {
                 const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
                 int gx = x0 + lx - 2, gy = y0 + ly - 2;
                 if (edge) {
-                    gx = g.wx ? min(max(gx, 0), nx - 1) : (tiny ? imod(gx, nx) : wrap(gx, nx));
-                    gy = g.wy ? min(max(gy, 0), ny - 1) : (tiny ? imod(gy, ny) : wrap(gy, ny));
+                    gx = g.wx ? min(max(gx, 0), nx - 1) : pwrap(gx, nx, tiny);
+                    gy = g.wy ? min(max(gy, 0), ny - 1) : pwrap(gy, ny, tiny);
                 }
                 const int s = gx + nx * gy + nxy * zw;
 #pragma unroll
@@ -247,7 +250,7 @@ struct Fused3DTile {
     __device__ __forceinline__ void load_F(int zb, T (&fo)[19], T (&fr)[19]) {
         fo[0] = fr[0] = T(0);
         if (g.wz && (zb < 0 || zb >= nz)) return;
-        const int zw = imod(zb, nz);
+        const int zw = zwrap(zb);
         const int s0 = sxy + nxy * zw;
         sfor<1, 19, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; fo[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD3Q19::w(k), cf.finv); });
         if (ring_xy_ok) {
@@ -259,7 +262,7 @@ struct Fused3DTile {
     // fo is consumed: the collision leaves post-collision values in it
     __device__ __forceinline__ void fill_B(int zb, bool collide, T (&fo)[19], const T (&fr)[19]) {
         if (g.wz && (zb < 0 || zb >= nz)) return;      // sources beyond a wall bounce back
-        const int zw = imod(zb, nz);
+        const int zw = zwrap(zb);
         const T *pm = sA + slotA(zb - 1) * Sh::A_SLOT;
         const T *p0 = sA + slotA(zb) * Sh::A_SLOT;
         const T *pp = sA + slotA(zb + 1) * Sh::A_SLOT;
@@ -281,9 +284,10 @@ struct Fused3DTile {
 #pragma unroll
             for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
             rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
+            rec[2 * N + 1] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];   // read 18 times by the gather
 #pragma unroll
-            for (int a = 2 * N + 1; a < RB::NVP; ++a) rec[a] = T(0);
-            srec_store<T, 2 * N + 1>(bbase, Sh::BPLANE, (ty + 1) * Sh::BX + (tx + 1), rec);
+            for (int a = 2 * N + 2; a < RB::NVP; ++a) rec[a] = T(0);
+            srec_store<T, 2 * N + 2>(bbase, Sh::BPLANE, (ty + 1) * Sh::BX + (tx + 1), rec);
             if (collide && own_xy) {
                 T op, om;
                 relaxation<N, T>(cf, c, op, om);
@@ -291,6 +295,14 @@ struct Fused3DTile {
                 const T vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
                 const T vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
                 const T base = T(3) * P - T(1.5) * vv;
+                // TRT with forcing (Eqs. 23-30) regrouped so that per-site factors are formed once:
+                // for a pair (k, kbar), with s = f_k + f_kbar and d = f_k - f_kbar,
+                //   sym  = w_k [X + e.v (Y e.v + Z e.F)] - (op / 2) s
+                //   anti = w_k (U e.v + V e.F) - (om / 2) d
+                // where X = op (3P - 1.5 v.v) - 3 ap v.F, Y = 4.5 op, Z = 9 ap, U = 3 om, V = 3 am;
+                // w_k X ... w_k V are shared by all pairs of one weight class.
+                const T hop = T(0.5) * op, hom = T(0.5) * om;
+                const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
                 // no wrap and no wall for any target: the site is inside the domain by one site
                 const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && zw > 0 && zw < nz - 1;
                 sfor<1, 19, 2>([&](auto kc_) {
@@ -299,14 +311,9 @@ struct Fused3DTile {
                     const T wk = T(LD3Q19::w(k));
                     const T eu = T(LD3Q19::ex(k)) * v[0] + T(LD3Q19::ey(k)) * v[1] + T(LD3Q19::ez(k)) * v[2];
                     const T eF = T(LD3Q19::ex(k)) * F[0] + T(LD3Q19::ey(k)) * F[1] + T(LD3Q19::ez(k)) * F[2];
-                    const T eqp = wk * (base + T(4.5) * eu * eu);
-                    const T eqm = wk * (T(3) * eu);
-                    const T Fp = wk * (T(9) * eu * eF - T(3) * vF);
-                    const T Fm = wk * (T(3) * eF);
-                    const T fp = T(0.5) * (f[k] + f[kb]);
-                    const T fm = T(0.5) * (f[k] - f[kb]);
-                    const T sym = -op * (fp - eqp) + ap * Fp;
-                    const T anti = -om * (fm - eqm) + am * Fm;
+                    const T sp = f[k] + f[kb], dm = f[k] - f[kb];
+                    const T sym = (wk * X + eu * ((wk * Y) * eu + (wk * Z) * eF)) - hop * sp;
+                    const T anti = ((wk * U) * eu + (wk * V) * eF) - hom * dm;
                     // post-collision values replace f in place (each pair is read once)
                     f[k] = f[k] + sym + anti;
                     f[kb] = f[kb] + sym - anti;
@@ -350,9 +357,10 @@ struct Fused3DTile {
 #pragma unroll
             for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
             rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
+            rec[2 * N + 1] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
 #pragma unroll
-            for (int a = 2 * N + 1; a < RB::NVP; ++a) rec[a] = T(0);
-            srec_store<T, 2 * N + 1>(bbase, Sh::BPLANE, by * Sh::BX + bx, rec);
+            for (int a = 2 * N + 2; a < RB::NVP; ++a) rec[a] = T(0);
+            srec_store<T, 2 * N + 2>(bbase, Sh::BPLANE, by * Sh::BX + bx, rec);
         }
     }
 
@@ -363,8 +371,8 @@ struct Fused3DTile {
         const T *bp = sB + slotB(zc + 1) * Sh::B_SLOT;
         const int ib = (ty + 1) * Sh::BX + (tx + 1);
         T r0[RB::NVP];
-        srec_load<T, 2 * N + 1>(b0, Sh::BPLANE, ib, r0);
-        const T vv0 = r0[N - 1] * r0[N - 1] + r0[N] * r0[N] + r0[N + 1] * r0[N + 1];
+        srec_load<T, 2 * N + 2>(b0, Sh::BPLANE, ib, r0);
+        const T vv0 = r0[2 * N + 1];
         const T w0 = T(1) / T(3);
         T acc[N - 1], lapS[N - 1];
 #pragma unroll
@@ -381,9 +389,9 @@ struct Fused3DTile {
             } else {
                 const T *pl = LD3Q19::ez(kb) > 0 ? bp : (LD3Q19::ez(kb) < 0 ? bm : b0);
                 T r[RB::NVP];
-                srec_load<T, 2 * N + 1>(pl, Sh::BPLANE, ib + LD3Q19::ex(kb) + Sh::BX * LD3Q19::ey(kb), r);
+                srec_load<T, 2 * N + 2>(pl, Sh::BPLANE, ib + LD3Q19::ex(kb) + Sh::BX * LD3Q19::ey(kb), r);
                 const T eu = T(LD3Q19::ex(k)) * r[N - 1] + T(LD3Q19::ey(k)) * r[N] + T(LD3Q19::ez(k)) * r[N + 1];
-                const T uu = r[N - 1] * r[N - 1] + r[N] * r[N] + r[N + 1] * r[N + 1];
+                const T uu = r[2 * N + 1];
                 const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
 #pragma unroll
                 for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
