@@ -45,7 +45,7 @@ __device__ __forceinline__ bool grid_barrier(BatchSync *sync, unsigned nblocks, 
     return ok != 0;
 }
 
-template <typename T, typename SF, int TX, int TY>
+template <typename T, typename SF, int TX, int TY, bool L2ONLY>
 __device__ __noinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, int y0, unsigned char *smem) {
     // the tile's simulation descriptor (geometry, coefficients, pointers) -> shared memory
     __shared__ __align__(16) BatchSim<T> d;
@@ -63,14 +63,15 @@ __device__ __noinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, 
     SF *fout = static_cast<SF *>(d.f[1 - cur]);
     const T *Cin = static_cast<const T *>(d.C[cur]);
     T *Cout = static_cast<T *>(d.C[1 - cur]);
-    // L2-only loads: inside one launch, other CTAs' writes of the previous step must not be
-    // read from a stale L1 line.  The degree-4 table is read from device memory: loop-invariant
-    // loads of it from the shared descriptor would be hoisted into registers.
+    // L2ONLY (persistent form): inside one launch, other CTAs' writes of the previous step must
+    // not be read from a stale L1 line.  The one-launch-per-step form uses ordinary loads.  The
+    // degree-4 table is read from device memory: loop-invariant loads of it from the shared
+    // descriptor would be hoisted into registers.
     switch (d.N) {
-        case 2: fused2d_tile<2, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        case 3: fused2d_tile<3, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        case 4: fused2d_tile<4, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        default: fused2d_tile<5, T, SF, TX, TY, true, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 2: fused2d_tile<2, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 3: fused2d_tile<3, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 4: fused2d_tile<4, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        default: fused2d_tile<5, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
     }
 }
 
@@ -98,7 +99,7 @@ k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict_
         long long idx = next;
         while (idx < end) {
             const int4 w = items[idx - (long long)t * nitems];
-            batch_tile<T, SF, TX, TY>(sims[w.x], cur, w.y, w.z, smem_raw);
+            batch_tile<T, SF, TX, TY, true>(sims[w.x], cur, w.y, w.z, smem_raw);
             __syncthreads();      // shared memory is reused by the next tile
             if (threadIdx.x == 0) next = (long long)atomicAdd(&sync->ticket, 1ull);
             __syncthreads();
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(TX * TY, (BatchOcc<T, TX * TY>::value))
 k_batch_step(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ items, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int4 w = items[blockIdx.x];
-    batch_tile<T, SF, TX, TY>(sims[w.x], parity, w.y, w.z, smem_raw);
+    batch_tile<T, SF, TX, TY, false>(sims[w.x], parity, w.y, w.z, smem_raw);
 }
 
 template <typename T, int TX, int TY>

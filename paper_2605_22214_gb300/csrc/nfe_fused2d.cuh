@@ -449,8 +449,11 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     }
 }
 
-// Minimum resident CTAs per SM requested from the register allocator.
-template <typename T, int NT> struct Fused2DOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 8 : NT <= 256 ? 4 : 2) : 1; };
+// Minimum resident CTAs per SM requested from the register allocator.  The FP32 tile shapes
+// get different budgets (32x4 and 32x16: 64 registers; 32x8: 85, three CTAs per SM) and the
+// autotuner times them all, so each workload runs the trade-off of spills against occupancy
+// that suits it.
+template <typename T, int NT> struct Fused2DOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 8 : NT <= 256 ? 3 : 2) : 1; };
 
 template <int N, typename T, typename SF, int TX, int TY, int Q4>
 __global__ void __launch_bounds__(TX * TY, (Fused2DOcc<T, TX * TY>::value))
@@ -486,10 +489,14 @@ template <int N, typename T, typename SF>
 struct Fused2DLaunch {
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        return cf.has_q4 ? launch<Q4_GLOBAL>(g, cf, b, cur, st, variant) : launch<Q4_ABSENT>(g, cf, b, cur, st, variant);
+    }
+    template <int Q4>
+    static cudaError_t launch(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st, int variant) {
         switch (variant) {
-            case 0: return launch_fused2d<N, T, SF, 32, 4, Q4_GLOBAL>(g, cf, b, cur, st);
-            case 1: return launch_fused2d<N, T, SF, 32, 8, Q4_GLOBAL>(g, cf, b, cur, st);
-            default: return launch_fused2d<N, T, SF, 32, 16, Q4_GLOBAL>(g, cf, b, cur, st);
+            case 0: return launch_fused2d<N, T, SF, 32, 4, Q4>(g, cf, b, cur, st);
+            case 1: return launch_fused2d<N, T, SF, 32, 8, Q4>(g, cf, b, cur, st);
+            default: return launch_fused2d<N, T, SF, 32, 16, Q4>(g, cf, b, cur, st);
         }
     }
     static const Ops *ops(int prec) {

@@ -618,7 +618,7 @@ nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double 
     std::string err;
     nfe_status st = build_tables(N, sigma, uidx, D, omega, true, tab, err);
     if (st != NFE_OK) return fail(st, "%s", err.c_str());
-    const int m2 = N * (N + 1) / 2, m4 = mono4_count(N);
+    const int m2 = N * (N + 1) / 2, m4 = mono4s_count(N);
     for (int p = 0; p < npts; ++p) {
         double c[NFE_MAX_N];
         for (int k = 0; k < N; ++k) c[k] = Cpts[size_t(p) * N + uidx[k]];
@@ -630,11 +630,20 @@ nfe_status nfe_bulk_potential_host(int N, const double *sigma, double D, double 
             for (int i = 0; i < N; ++i)
                 for (int j = i; j < N; ++j) q += tab.q2[e * m2 + idx++] * c[i] * c[j];
             if (!tab.q4.empty()) {
+                // structured quartic part, in the layout of the table (see nfe_internal.h)
+                const double *a4 = tab.q4.data() + e * m4;
                 int jdx = 0;
-                for (int i = 0; i < N; ++i)
-                    for (int j = i; j < N; ++j)
-                        for (int k = j; k < N; ++k)
-                            for (int l = k; l < N; ++l) q += tab.q4[e * m4 + jdx++] * c[i] * c[j] * c[k] * c[l];
+                double sa = 0.0, sb = 0.0;
+                for (int l = 0; l < N; ++l) {
+                    if (l == e) continue;
+                    double lin = 0.0;
+                    for (int m = 0; m < N; ++m) if (m != e && m != l) lin += a4[jdx++] * c[m];
+                    sa += c[l] * c[l] * lin;
+                }
+                for (int k = 0; k < N; ++k)
+                    for (int l = k + 1; l < N; ++l)
+                        if (k != e && l != e) sb += a4[jdx++] * c[k] * c[k] * c[l] * c[l];
+                q += c[e] * sa + sb;
             }
             out[uidx[e]] = c[e] * q;
         }

@@ -13,12 +13,14 @@ namespace nfe {
 constexpr int kMaxN = NFE_MAX_N;
 constexpr int kMaxMono2 = kMaxN * (kMaxN + 1) / 2;   // degree-2 monomials in 8 variables
 
-// Degree-4 monomials a <= b <= c <= d in N variables: C(N+3, 4).
-__host__ __device__ constexpr int mono4_count(int n) { return n * (n + 1) * (n + 2) * (n + 3) / 24; }
+// Coefficients of the quartic (stabiliser) part of q_i per evolved component i, structured as
+//   C_i sum_{l != i} C_l^2 sum_{m not in {i,l}} a_{ilm} C_m + sum_{k<l; i not in {k,l}} b_{ikl} C_k^2 C_l^2:
+// (N-1)(N-2) values a, then (N-1)(N-2)/2 values b.
+__host__ __device__ constexpr int mono4s_count(int n) { return 3 * (n - 1) * (n - 2) / 2; }
 
-// Up to N = 5 the degree-4 coefficients also travel with the kernel parameters (constant bank).
-constexpr int kQ4InlineMaxN = 5;
-constexpr int kQ4Inline = (kQ4InlineMaxN - 1) * mono4_count(kQ4InlineMaxN);   // 280
+// Up to N = 6 the quartic coefficients also travel with the kernel parameters (constant bank).
+constexpr int kQ4InlineMaxN = 6;
+constexpr int kQ4Inline = (kQ4InlineMaxN - 1) * mono4s_count(kQ4InlineMaxN);   // 150
 
 // Grid geometry as the kernels see it.
 struct Geom {
@@ -45,8 +47,8 @@ struct Coef {
     T finv;                       // 1 / fscale
     int has_q4;                   // Omega != 0: degree-4 part present
     int nonconservative;          // force of Eq. 31 instead of Eq. 34
-    const T *q4;                  // (N-1) x mono4_count(N), device memory, or nullptr (Omega = 0)
-    T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 5); last member
+    const T *q4;                  // (N-1) x mono4s_count(N), device memory, or nullptr (Omega = 0)
+    T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 6); last member
 };
 
 // One kernel kind for profiling.

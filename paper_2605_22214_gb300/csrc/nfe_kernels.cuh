@@ -126,16 +126,17 @@ __device__ __forceinline__ T bulk_energy(const T (&c)[N], const Coef<T> &cf) {
     return E;
 }
 
-// Where the coefficients of the degree-4 (stabiliser) part of q are read (the part is
-// skipped when cf.has_q4 is 0): device memory, or the kernel's parameter block when
-// N <= kQ4InlineMaxN (saves a load per term; the D3Q19 step gains, while in the D2Q9 step
-// the extra register pressure costs more than it saves).
-enum Q4Source { Q4_GLOBAL = 0, Q4_PARAM = 1 };
+// Where the coefficients of the quartic (stabiliser) part of q are read (the part is skipped
+// when cf.has_q4 is 0): device memory, or the kernel's parameter block when N <= kQ4InlineMaxN
+// (saves a load per term; the D3Q19 step gains, while in the D2Q9 step the extra register
+// pressure costs more than it saves).  Q4_ABSENT compiles no quartic code at all, for kernels
+// launched only when Omega = 0: even never-executed quartic code raises register pressure.
+enum Q4Source { Q4_GLOBAL = 0, Q4_PARAM = 1, Q4_ABSENT = 2 };
 
 template <int N, typename T, int Q4 = Q4_GLOBAL>
 __device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T (&q)[N - 1]) {
     // q_e(C): degree-2 monomials C_a C_b (a <= b) in nested-loop order, and the
-    // degree-4 monomials a <= b <= c <= d of the stabiliser part when Omega != 0.
+    // structured quartic stabiliser part when Omega != 0.
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) q[e] = T(0);
     int idx = 0;
@@ -148,29 +149,35 @@ __device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T 
             for (int e = 0; e < N - 1; ++e) q[e] += cf.q2[e][idx] * p;
             ++idx;
         }
-    if (cf.has_q4) {
-        constexpr int M4 = mono4_count(N);
-        int j = 0;
+    if (Q4 != Q4_ABSENT && cf.has_q4) {
+        // structured quartic part (layout in nfe_internal.h): a_{ilm} then b_{ikl} per i
+        constexpr int M4 = mono4s_count(N);
+        const auto coef = [&](int t) -> T {
+            if constexpr (Q4 == Q4_PARAM && N <= kQ4InlineMaxN) return cf.q4c[t];
+            else return __ldg(cf.q4 + t);
+        };
+        T sq[N];
 #pragma unroll
-        for (int a = 0; a < N; ++a)
+        for (int a = 0; a < N; ++a) sq[a] = c[a] * c[a];
 #pragma unroll
-            for (int b = a; b < N; ++b) {
-                T pab = c[a] * c[b];
+        for (int e = 0; e < N - 1; ++e) {
+            int j = e * M4;
+            T sa = T(0), sb = T(0);
 #pragma unroll
-                for (int d0 = b; d0 < N; ++d0) {
-                    T pabc = pab * c[d0];
+            for (int l = 0; l < N; ++l) {
+                if (l == e) continue;
+                T lin = T(0);
 #pragma unroll
-                    for (int d1 = d0; d1 < N; ++d1) {
-                        T p = pabc * c[d1];
-#pragma unroll
-                        for (int e = 0; e < N - 1; ++e) {
-                            if constexpr (Q4 == Q4_PARAM && N <= kQ4InlineMaxN) q[e] += cf.q4c[e * M4 + j] * p;
-                            else q[e] += __ldg(cf.q4 + e * M4 + j) * p;
-                        }
-                        ++j;
-                    }
-                }
+                for (int m = 0; m < N; ++m) if (m != e && m != l) lin += coef(j++) * c[m];
+                sa += sq[l] * lin;
             }
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+#pragma unroll
+                for (int l = k + 1; l < N; ++l)
+                    if (k != e && l != e) sb += coef(j++) * (sq[k] * sq[l]);
+            q[e] += c[e] * sa + sb;
+        }
     }
 }
 

@@ -1,8 +1,17 @@
 // Sec. II tables of arXiv 2605.22214, built once per simulation on the host in
 // FP64: alpha and gamma (Eqs. 8-9), Lambda (Eqs. 14-15), Theta (Eqs. 18-19)
-// and the monomial coefficients of the factored flux potential
-//   S_i = C_i q_i(C) + (3D/4) lap C_i   (equal to Eq. 12 on the simplex).
+// and the coefficients of the factored flux potential
+//   S_i = C_i q_i(C) + (3D/4) lap C_i   (equal to Eq. 12 on the simplex):
+// the quadratic part of q_i as monomial coefficients, and the quartic (stabiliser,
+// Eq. 17) part in the structured form
+//   q4_i = C_i sum_{l != i} C_l^2 sum_{m not in {i,l}} a_{ilm} C_m
+//        + sum_{k < l; i not in {k,l}} b_{ikl} C_k^2 C_l^2,
+// which follows from xi_j = (12 Omega / D) sum_{k<l} C_k^2 C_l^2 inner_j^{kl}(C) with
+// inner_j^{kl} linear: the pairs that contain i carry C_i^2, and for the others the
+// Theta conditions (Eqs. 18-19) leave only the C_i term of sum_j alpha_ij inner_j^{kl}.
 #include "nfe_tables.h"
+
+#include "nfe_internal.h"
 
 #include <algorithm>
 #include <cmath>
@@ -145,9 +154,29 @@ nfe_status build_tables(int N, const double *sigma_user, const int *uidx, double
                 }
             }
 
-    // xi_j (Eq. 17) with Theta_{kl; j; m} from sub-matrix * Theta = 2 alpha_{., m} (Eqs. 18-19).
-    std::vector<Poly> xi(N);
+    // Stabiliser part (Eq. 17) with Theta_{kl; j; m} from sub-matrix * Theta = 2 alpha_{., m}
+    // (Eqs. 18-19), directly in the structured form above (layout per evolved i: the a_{ilm}
+    // for l != i ascending and m ascending, then the b_{ikl} for k < l ascending).
+    const int m4 = mono4s_count(N);
+    out.q4.assign(omega != 0.0 ? (N - 1) * m4 : 0, 0.0);
+    std::vector<double> q4max(N, 0.0), q4drop(N, 0.0);
     if (omega != 0.0) {
+        const auto pos_a = [&](int i, int l, int m) {
+            const int li = l - (l > i ? 1 : 0);
+            const int mi = m - (m > i ? 1 : 0) - (m > l ? 1 : 0);
+            return li * (N - 2) + mi;
+        };
+        const auto pos_b = [&](int i, int k, int l) {
+            int r = (N - 1) * (N - 2);
+            for (int a = 0; a < N; ++a)
+                for (int b = a + 1; b < N; ++b) {
+                    if (a == i || b == i) continue;
+                    if (a == k && b == l) return r;
+                    ++r;
+                }
+            return -1;
+        };
+        const double scale = 12.0 / D * omega;
         for (int k = 0; k < N; ++k)
             for (int l = k + 1; l < N; ++l) {
                 // inner_j = 2 C_j - sum_m Theta_{kl;j;m} C_m for every j outside {k, l}
@@ -167,9 +196,22 @@ nfe_status build_tables(int N, const double *sigma_user, const int *uidx, double
                     if (!gauss_solve(M, r, rhs, 1)) { err = "alpha sub-matrix of a Theta system is singular"; return NFE_ESINGULAR; }
                     for (int b = 0; b < r; ++b) axpy(inner[R[b]], -rhs[b], var(m));
                 }
-                const Poly w = mul(mul(var(k), var(k)), mul(var(l), var(l)));
-                for (int j = 0; j < N; ++j)
-                    if (j != k && j != l) axpy(xi[j], 12.0 / D * omega, mul(w, inner[j]));
+                // G_i^{kl} = sum_j alpha_ij inner_j^{kl}, linear in C_m (m outside {k, l})
+                for (int i = 0; i < N - 1; ++i) {
+                    Poly G;
+                    for (int j = 0; j < N; ++j) if (j != k && j != l) axpy(G, A(i, j), inner[j]);
+                    const auto coef = [&](int m) { const auto it = G.find(var_mono(m)); return it == G.end() ? 0.0 : it->second; };
+                    for (int m = 0; m < N; ++m) q4max[i] = std::max(q4max[i], std::fabs(scale * coef(m)));
+                    if (i == k || i == l) {
+                        const int o = i == k ? l : k;
+                        for (int m = 0; m < N; ++m)
+                            if (m != k && m != l) out.q4[i * m4 + pos_a(i, o, m)] = scale * coef(m);
+                    } else {
+                        out.q4[i * m4 + pos_b(i, k, l)] = scale * coef(i);
+                        for (int m = 0; m < N; ++m)            // must vanish: divisibility by C_i
+                            if (m != i) q4drop[i] = std::max(q4drop[i], std::fabs(scale * coef(m)));
+                    }
+                }
             }
     }
 
@@ -191,16 +233,11 @@ nfe_status build_tables(int N, const double *sigma_user, const int *uidx, double
     const Poly ssum2 = mul(ssum, ssum);
 
     // enumeration orders used by the kernels
-    std::vector<Mono> mono2, mono4;
+    std::vector<Mono> mono2;
     for (int a = 0; a < N; ++a)
         for (int b = a; b < N; ++b) mono2.push_back(var_mono(a) + var_mono(b));
-    for (int a = 0; a < N; ++a)
-        for (int b = a; b < N; ++b)
-            for (int c = b; c < N; ++c)
-                for (int d = c; d < N; ++d) mono4.push_back(var_mono(a) + var_mono(b) + var_mono(c) + var_mono(d));
 
     out.q2.assign((N - 1) * mono2.size(), 0.0);
-    out.q4.assign(omega != 0.0 ? (N - 1) * mono4.size() : 0, 0.0);
     out.residual = 0.0;
     for (int i = 0; i < N - 1; ++i) {
         Poly cubic;
@@ -227,20 +264,9 @@ nfe_status build_tables(int N, const double *sigma_user, const int *uidx, double
             out.q2[i * mono2.size() + (it - mono2.begin())] += kv.second;
         }
         out.residual = std::max(out.residual, rest / scale);
-        if (omega != 0.0) {
-            Poly qx;
-            for (int j = 0; j < N; ++j) axpy(qx, A(i, j), xi[j]);
-            const double sx = std::max(max_abs(qx), 1e-300);
-            double rx = 0.0;
-            for (const auto &kv : qx) {
-                if (mono_exp(kv.first, i) == 0) { rx = std::max(rx, std::fabs(kv.second)); continue; }
-                const Mono q = kv.first - var_mono(i);
-                const auto it = std::find(mono4.begin(), mono4.end(), q);
-                out.q4[i * mono4.size() + (it - mono4.begin())] += kv.second;
-            }
-            out.residual = std::max(out.residual, rx / sx);
-        }
     }
+    for (int i = 0; i < N - 1; ++i)
+        if (q4max[i] > 0.0) out.residual = std::max(out.residual, q4drop[i] / q4max[i]);
     if (with_phi && out.residual > 1e-10) {
         err = "flux potential does not factor by C_i (Lambda/Theta solve inaccurate)";
         return NFE_ESINGULAR;

@@ -13,7 +13,7 @@ struct Tables {
     double omega = 0.0;
     std::vector<double> beta, kappa, alpha, gamma;   // N x N (internal order), gamma N
     std::vector<double> q2;                           // (N-1) x N(N+1)/2, monomials a <= b
-    std::vector<double> q4;                           // (N-1) x C(N+3,4), monomials a<=b<=c<=d (Omega != 0)
+    std::vector<double> q4;                           // (N-1) x mono4s_count(N), structured quartic part (Omega != 0)
     double residual = 0.0;                            // largest dropped coefficient, relative
     int lambda_count = 0;
 };

@@ -3,7 +3,9 @@
     python -m paper_2605_22214_gb300.run WORKLOAD [--precision fp32] [--steps 50] [--size N]
 
 WORKLOAD is one of: spinodal (D2Q9, N = 4, size^2), janus3d (D3Q19, N = 4, size^3),
-lens (D2Q9, N = 3, size^2, walls in y), poiseuille3d (D3Q19, N = 7, 32 x 32 x 192).
+lens (D2Q9, N = 3, size^2, walls in y), poiseuille3d (D3Q19, N = 7, 32 x 32 x 192),
+batch (--sims D2Q9 lens/Janus simulations of mixed size and N in one batch, FP32;
+--mode persistent | per_step | auto).
 The time is taken with CUDA events around the steps, after three warm-up steps.
 """
 from __future__ import annotations
@@ -38,12 +40,16 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--variant", type=int, default=-1, help="tile shape (-1: autotune)")
+    ap.add_argument("--sims", type=int, default=512, help="batch: number of simulations")
+    ap.add_argument("--mode", default="auto", choices=["persistent", "per_step", "auto"], help="batch: launch form")
     args = ap.parse_args()
     import torch
 
     import paper_2605_22214_gb300 as nfe
     from paper_2605_22214_gb300 import build
     build.build()
+    if args.workload == "batch":
+        return run_batch(nfe, torch, args)
     p = make(args.workload, args.size)
     stream = torch.cuda.Stream()
     with nfe.Sim(p, args.precision, stream=stream.cuda_stream, scale_exp=10) as s:
@@ -64,6 +70,32 @@ def main():
     print(json.dumps({"workload": p["name"], "precision": args.precision, "sites": n, "ms_per_step": round(ms, 5),
                       "mlups": round(n / ms / 1e3, 1), "variant": info["variant"],
                       "effective_gbs": round(info["min_bytes_per_site"] * n / ms / 1e6, 1)}))
+
+
+def run_batch(nfe, torch, args):
+    import nfe_workloads as W
+    sims = W.batch_sweep(args.sims, seed=1005)
+    sites = sum(p["nx"] * p["ny"] for p in sims)
+    mode = {"persistent": nfe.NFE_BATCH_PERSISTENT, "per_step": nfe.NFE_BATCH_PER_STEP, "auto": nfe.NFE_BATCH_AUTO}[args.mode]
+    stream = torch.cuda.Stream()
+    with nfe.Batch(sims, "fp32", stream=stream.cuda_stream) as bt:
+        for i, p in enumerate(sims):
+            bt.set_fields(i, p["C0"])
+        bt.set_mode(mode)
+        with torch.cuda.stream(stream):
+            bt.step(3)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bt.step(args.steps)
+            b.record(stream)
+        b.synchronize()
+        bt.sync()
+        ms = a.elapsed_time(b) / args.steps
+        info = bt.info()
+    print(json.dumps({"workload": f"batch of {args.sims} D2Q9 simulations", "mode": args.mode, "sites": sites,
+                      "ms_per_step": round(ms, 5), "mlups": round(sites / ms / 1e3, 1), "form": info["form"],
+                      "tile_y": info["tile_y"]}))
 
 
 if __name__ == "__main__":

@@ -82,6 +82,26 @@ def test_status_strings():
         assert nfe.nfe_status_string(s)
 
 
+@pytest.mark.parametrize("N,imp", [(3, 2), (4, 0), (5, 4), (6, 1), (7, 6), (8, 3)])
+def test_library_stabiliser_part_matches_oracle(N, imp):
+    # The quartic (Omega) part of the library's flux potential alone, S(Omega) - S(0), against
+    # the oracle's literal xi_j (Eqs. 17-19): the library stores it in a structured form
+    # (squared pair products times linear forms), so this checks that form term by term.
+    lib()
+    rng = np.random.default_rng(80 + N)
+    sig = W.random_sigma(rng, N)
+    pts = W.random_simplex_points(rng, N, 200)
+    om = 1.0 / 90.0
+    d_lib = (nfe.nfe_bulk_potential_host(sig, pts, omega_stab=om, implicit=imp)
+             - nfe.nfe_bulk_potential_host(sig, pts, omega_stab=0.0, implicit=imp))
+    d_or = (thermo.Tables(sig, omega=om).bulk_flux_potential(pts.T).T
+            - thermo.Tables(sig, omega=0.0).bulk_flux_potential(pts.T).T)
+    ev = [c for c in range(N) if c != imp]
+    scale = np.abs(d_or[:, ev]).max()
+    assert scale > 0.0
+    np.testing.assert_allclose(d_lib[:, ev], d_or[:, ev], rtol=0, atol=1e-10 * scale)
+
+
 @pytest.mark.parametrize("N,omega,imp", [(2, 0.0, 1), (3, 0.0, 0), (4, 0.0, 3), (4, 1 / 90, 1),
                                          (5, float("nan"), 2), (6, 0.0, 5), (7, 1 / 90, 0), (8, 0.0, 4)])
 def test_library_tables_match_oracle(N, omega, imp):
