@@ -45,33 +45,40 @@ __device__ __forceinline__ bool grid_barrier(BatchSync *sync, unsigned nblocks, 
     return ok != 0;
 }
 
-template <typename T, typename SF, int TX, int TY, bool L2ONLY>
+// The tile's simulation descriptor (geometry, coefficients, pointers) -> shared memory, up to
+// the inline quartic table, which these kernels do not read (they read its device-memory copy:
+// loop-invariant loads from the shared descriptor would be hoisted into registers and spill).
+template <typename T>
+__device__ __forceinline__ void load_desc(const BatchSim<T> &dg, BatchSim<T> &d) {
+    static_assert(sizeof(BatchSim<T>) % 16 == 0, "16-byte copies");
+    constexpr size_t used = offsetof(BatchSim<T>, coef) + offsetof(Coef<T>, q4c);
+    constexpr int n16 = int((used + 15) / 16);
+    static_assert(n16 * 16 <= sizeof(BatchSim<T>), "copy inside the descriptor");
+    const int4 *src = reinterpret_cast<const int4 *>(&dg);
+    int4 *dst = reinterpret_cast<int4 *>(&d);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+}
+
+template <typename T, typename SF, int TX, int TY, int NN, bool L2ONLY>
+__device__ __forceinline__ void batch_tile_n(const BatchSim<T> &d, int cur, int x0, int y0, unsigned char *smem) {
+    fused2d_tile<NN, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, static_cast<const SF *>(d.f[cur]),
+                                                      static_cast<SF *>(d.f[1 - cur]), static_cast<const T *>(d.C[cur]),
+                                                      static_cast<T *>(d.C[1 - cur]), d.flag, x0, y0, smem);
+}
+
+// Any N (2..5) in one non-inlined function: the persistent form, whose CTAs meet simulations of
+// every N.  L2-only loads: inside one launch, other CTAs' writes of the previous step must not
+// be read from a stale L1 line.
+template <typename T, typename SF, int TX, int TY>
 __device__ __noinline__ void batch_tile(const BatchSim<T> &dg, int cur, int x0, int y0, unsigned char *smem) {
-    // the tile's simulation descriptor (geometry, coefficients, pointers) -> shared memory
     __shared__ __align__(16) BatchSim<T> d;
-    {
-        static_assert(sizeof(BatchSim<T>) % 16 == 0, "16-byte copies");
-        constexpr size_t used = offsetof(BatchSim<T>, coef) + offsetof(Coef<T>, q4c);
-        constexpr int n16 = int((used + 15) / 16);
-        static_assert(n16 * 16 <= sizeof(BatchSim<T>), "copy inside the descriptor");
-        const int4 *src = reinterpret_cast<const int4 *>(&dg);
-        int4 *dst = reinterpret_cast<int4 *>(&d);
-        for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
-    }
+    load_desc(dg, d);
     __syncthreads();
-    const SF *fin = static_cast<const SF *>(d.f[cur]);
-    SF *fout = static_cast<SF *>(d.f[1 - cur]);
-    const T *Cin = static_cast<const T *>(d.C[cur]);
-    T *Cout = static_cast<T *>(d.C[1 - cur]);
-    // L2ONLY (persistent form): inside one launch, other CTAs' writes of the previous step must
-    // not be read from a stale L1 line.  The one-launch-per-step form uses ordinary loads.  The
-    // degree-4 table is read from device memory: loop-invariant loads of it from the shared
-    // descriptor would be hoisted into registers.
     switch (d.N) {
-        case 2: fused2d_tile<2, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        case 3: fused2d_tile<3, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        case 4: fused2d_tile<4, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
-        default: fused2d_tile<5, T, SF, TX, TY, L2ONLY, Q4_GLOBAL>(d.geom, d.coef, fin, fout, Cin, Cout, d.flag, x0, y0, smem); break;
+        case 2: batch_tile_n<T, SF, TX, TY, 2, true>(d, cur, x0, y0, smem); break;
+        case 3: batch_tile_n<T, SF, TX, TY, 3, true>(d, cur, x0, y0, smem); break;
+        case 4: batch_tile_n<T, SF, TX, TY, 4, true>(d, cur, x0, y0, smem); break;
+        default: batch_tile_n<T, SF, TX, TY, 5, true>(d, cur, x0, y0, smem); break;
     }
 }
 
@@ -99,7 +106,7 @@ k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict_
         long long idx = next;
         while (idx < end) {
             const int4 w = items[idx - (long long)t * nitems];
-            batch_tile<T, SF, TX, TY, true>(sims[w.x], cur, w.y, w.z, smem_raw);
+            batch_tile<T, SF, TX, TY>(sims[w.x], cur, w.y, w.z, smem_raw);
             __syncthreads();      // shared memory is reused by the next tile
             if (threadIdx.x == 0) next = (long long)atomicAdd(&sync->ticket, 1ull);
             __syncthreads();
@@ -109,13 +116,18 @@ k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict_
     }
 }
 
-// One launch per step, one CTA per work item (the non-persistent batched form).
-template <typename T, typename SF, int TX, int TY>
+// One launch per step and per component count, one CTA per work item (the non-persistent
+// batched form).  The work list is grouped by N, so each launch covers one contiguous range and
+// carries a single inlined tile body (smaller code, its own register allocation, no switch).
+template <typename T, typename SF, int TX, int TY, int NN>
 __global__ void __launch_bounds__(TX * TY, (BatchOcc<T, TX * TY>::value))
 k_batch_step(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ items, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) BatchSim<T> d;
     const int4 w = items[blockIdx.x];
-    batch_tile<T, SF, TX, TY, false>(sims[w.x], parity, w.y, w.z, smem_raw);
+    load_desc(sims[w.x], d);
+    __syncthreads();
+    batch_tile_n<T, SF, TX, TY, NN, false>(d, parity, w.y, w.z, smem_raw);
 }
 
 template <typename T, int TX, int TY>
@@ -123,13 +135,19 @@ constexpr size_t batch_smem() { return Fused2DShape<5, T, TX, TY>::BYTES; }
 
 template <typename T, typename SF, int TX, int TY>
 struct BatchKernels {
+    template <int NN>
+    static cudaError_t step_attr() {
+        return cudaFuncSetAttribute(k_batch_step<T, SF, TX, TY, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    int(Fused2DShape<NN, T, TX, TY>::BYTES));
+    }
     static cudaError_t setup(int *blocks_per_sm) {
         const size_t smem = batch_smem<T, TX, TY>();
         cudaError_t e = cudaFuncSetAttribute(k_batch_persistent<T, SF, TX, TY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_batch_step<T, SF, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
+        if ((e = step_attr<2>()) != cudaSuccess || (e = step_attr<3>()) != cudaSuccess ||
+            (e = step_attr<4>()) != cudaSuccess || (e = step_attr<5>()) != cudaSuccess)
+            return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_persistent<T, SF, TX, TY>,
                                                              TX * TY, smem);
     }
@@ -148,10 +166,20 @@ struct BatchKernels {
                                   static_cast<const BatchSim<T> *>(L.sims), L.items, L.nitems, L.nsteps,
                                   L.parity, L.sync, L.spin_limit, L.expected);
     }
+    template <int NN>
+    static void step_n(const BatchLaunch &L, int parity, cudaStream_t st) {
+        const int g = NN - 2;
+        if (L.ncount[g] <= 0) return;
+        k_batch_step<T, SF, TX, TY, NN><<<L.ncount[g], TX * TY, Fused2DShape<NN, T, TX, TY>::BYTES, st>>>(
+            static_cast<const BatchSim<T> *>(L.sims), L.items + L.nstart[g], parity);
+    }
     static cudaError_t per_step(const BatchLaunch &L, cudaStream_t st) {
         for (int t = 0; t < L.nsteps; ++t) {
-            k_batch_step<T, SF, TX, TY><<<L.nitems, TX * TY, batch_smem<T, TX, TY>(), st>>>(
-                static_cast<const BatchSim<T> *>(L.sims), L.items, (L.parity + t) & 1);
+            const int parity = (L.parity + t) & 1;
+            step_n<2>(L, parity, st);
+            step_n<3>(L, parity, st);
+            step_n<4>(L, parity, st);
+            step_n<5>(L, parity, st);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) return e;
         }

@@ -7,6 +7,8 @@
 
 namespace nfe {
 
+constexpr int kBatchMaxN = 5;   // component counts 2..5 in a batch
+
 // One simulation as the batched kernel sees it (device memory, read-only).
 // The coefficients come last: the kernel copies the descriptor into shared memory
 // up to (not including) Coef::q4c, since it reads the degree-4 table from device memory.
@@ -40,6 +42,8 @@ struct BatchLaunch {
     long long spin_limit;   // polls before a barrier wait gives up
     unsigned expected;      // CTAs a barrier waits for (normally the grid size)
     int grid;
+    int nstart[kBatchMaxN - 1];   // items of simulations with N = 2 + g: [nstart[g], nstart[g] + ncount[g])
+    int ncount[kBatchMaxN - 1];
 };
 
 using BatchSetup = cudaError_t (*)(int *blocks_per_sm);

@@ -672,6 +672,8 @@ struct nfe_batch {
     int variant = -1;
     int grid = 0;
     int nitems = 0;
+    int nstart[kBatchMaxN - 1] = {0};   // work-list range of the simulations with N = 2 + g
+    int ncount[kBatchMaxN - 1] = {0};
     int parity = 0;
     int mode = NFE_BATCH_AUTO;        // requested form
     int form = -1;                    // form in use (persistent or per-step) after tuning
@@ -717,10 +719,16 @@ nfe_status batch_items(nfe_batch *b, int v) {
     for (int i = 0; i < b->nsims; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->sims[a]->N < b->sims[c]->N; });
     std::vector<int4> items;
+    for (int g = 0; g < kBatchMaxN - 1; ++g) { b->nstart[g] = 0; b->ncount[g] = 0; }
     for (int i : order) {
         const Geom &g = b->sims[i]->geom;
+        const int grp = b->sims[i]->N - 2;
+        if (b->ncount[grp] == 0) b->nstart[grp] = int(items.size());
         for (int y0 = 0; y0 < g.ny; y0 += TY)
-            for (int x0 = 0; x0 < g.nx; x0 += TX) items.push_back(make_int4(i, x0, y0, 0));
+            for (int x0 = 0; x0 < g.nx; x0 += TX) {
+                items.push_back(make_int4(i, x0, y0, 0));
+                ++b->ncount[grp];
+            }
     }
     if (items.size() > b->items_cap) {
         if (b->d_items) cudaFree(b->d_items);
@@ -753,6 +761,7 @@ BatchLaunch batch_launch_args(const nfe_batch *b, int64_t nsteps, long long spin
     L.spin_limit = spins;
     L.expected = unsigned(b->grid) + extra;
     L.grid = b->grid;
+    for (int g = 0; g < kBatchMaxN - 1; ++g) { L.nstart[g] = b->nstart[g]; L.ncount[g] = b->ncount[g]; }
     return L;
 }
 
