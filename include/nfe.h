@@ -70,7 +70,10 @@ enum { NFE_WALL_X = 1, NFE_WALL_Y = 2, NFE_WALL_Z = 4 };
 /* Flags (nfe_params.flags). */
 enum {
     NFE_NONCONSERVATIVE_FORCE = 1,  /* F_s = sum_i mu_i grad C_i (Eq. 31) instead of Eq. 34 */
-    NFE_NO_PHI = 2                  /* drop phi_j from the flux potential (Eq. 12) */
+    NFE_NO_PHI = 2                  /* drop phi_j from the flux potential (Eq. 12): the ablation in
+                                       which an absent component nucleates at interfaces (Sec. IV).
+                                       D2Q9 single simulations only; nfe_create returns
+                                       NFE_EUNSUPPORTED for D3Q19, nfe_batch_create for batches */
 };
 
 #define NFE_MAX_N 8

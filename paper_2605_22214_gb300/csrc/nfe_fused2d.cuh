@@ -171,6 +171,7 @@ __device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N],
     flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
+    flux_rest<N, T, Q4>(c, cf, S);
     // moments (Eqs. 37-38), rho = 1
     const T jx = (f[1] - f[2]) + (f[5] - f[6]) + (f[7] - f[8]);
     const T jy = (f[3] - f[4]) + (f[5] - f[6]) - (f[7] - f[8]);
@@ -489,6 +490,7 @@ template <int N, typename T, typename SF>
 struct Fused2DLaunch {
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        if (cf.no_phi) return launch<Q4_NOPHI>(g, cf, b, cur, st, variant);
         return cf.has_q4 ? launch<Q4_GLOBAL>(g, cf, b, cur, st, variant) : launch<Q4_ABSENT>(g, cf, b, cur, st, variant);
     }
     template <int Q4>

@@ -91,6 +91,7 @@ struct nfe_sim {
     Coef<float> cfl{};
     const void *coef = nullptr;       // points at cd or cfl
     void *q4dev = nullptr;
+    void *r3dev = nullptr;            // no-phi remainder table
     Buffers buf{};
     int uidx[NFE_MAX_N] = {0};        // internal slot -> user component
     cudaStream_t stream = nullptr;
@@ -137,6 +138,8 @@ void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
     c.has_q4 = s.tab.omega != 0.0 ? 1 : 0;
     c.nonconservative = (p.flags & NFE_NONCONSERVATIVE_FORCE) ? 1 : 0;
     c.q4 = static_cast<const T *>(s.q4dev);
+    c.r3 = static_cast<const T *>(s.r3dev);
+    c.no_phi = (p.flags & NFE_NO_PHI) ? 1 : 0;
     if (N <= kQ4InlineMaxN)
         for (size_t j = 0; j < s.tab.q4.size(); ++j) c.q4c[j] = T(s.tab.q4[j]);
 }
@@ -148,10 +151,11 @@ nfe_status free_all(nfe_sim *s) {
     for (auto e : s->event_pool) cudaEventDestroy(e);
     s->event_pool.clear();
     void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
-                    s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev};
+                    s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
+    s->r3dev = nullptr;
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     s->stream = nullptr;
     return NFE_OK;
@@ -307,7 +311,8 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     if (p->implicit_component < 0 || p->implicit_component >= N) return fail(NFE_EINVAL, "implicit_component out of range");
     if (p->precision < NFE_FP64 || p->precision > NFE_FP32_BF16STORE) return fail(NFE_EINVAL, "unknown precision");
     if (p->flags & ~(NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI)) return fail(NFE_EINVAL, "unknown flags");
-    if (p->flags & NFE_NO_PHI) return fail(NFE_EUNSUPPORTED, "NFE_NO_PHI is not implemented on the GPU");
+    if ((p->flags & NFE_NO_PHI) && grid->lattice != NFE_D2Q9)
+        return fail(NFE_EUNSUPPORTED, "NFE_NO_PHI (the no-phi ablation) runs on D2Q9 only");
     if (p->precision == NFE_FP32_F16STORE && (p->scale_exp < -20 || p->scale_exp > 20))
         return fail(NFE_EINVAL, "scale_exp outside -20..20");
 
@@ -349,17 +354,20 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     ALLOC(s->buf.C[1], s->cplanes_bytes);
     ALLOC(s->buf.flag, sizeof(int));
     if (!s->tab.q4.empty()) ALLOC(s->q4dev, s->tab.q4.size() * ce);
+    if (!s->tab.r3.empty()) ALLOC(s->r3dev, s->tab.r3.size() * ce);
 #undef ALLOC
-    // upload q4 in the arithmetic type
-    if (s->q4dev) {
+    // upload the quartic and no-phi tables in the arithmetic type
+    const std::pair<void *, const std::vector<double> *> uploads[] = {{s->q4dev, &s->tab.q4}, {s->r3dev, &s->tab.r3}};
+    for (const auto &u : uploads) {
+        if (!u.first) continue;
         cudaError_t e;
         if (s->prec == NFE_FP64) {
-            e = cudaMemcpy(s->q4dev, s->tab.q4.data(), s->tab.q4.size() * sizeof(double), cudaMemcpyHostToDevice);
+            e = cudaMemcpy(u.first, u.second->data(), u.second->size() * sizeof(double), cudaMemcpyHostToDevice);
         } else {
-            std::vector<float> tmp(s->tab.q4.begin(), s->tab.q4.end());
-            e = cudaMemcpy(s->q4dev, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice);
+            std::vector<float> tmp(u.second->begin(), u.second->end());
+            e = cudaMemcpy(u.first, tmp.data(), tmp.size() * sizeof(float), cudaMemcpyHostToDevice);
         }
-        if (e != cudaSuccess) { free_all(s); delete s; return cuda_fail(e, "upload q4"); }
+        if (e != cudaSuccess) { free_all(s); delete s; return cuda_fail(e, "upload coefficient tables"); }
     }
     if (s->prec == NFE_FP64) { fill_coef<double>(*s, *p, s->cd); s->coef = &s->cd; }
     else { fill_coef<float>(*s, *p, s->cfl); s->coef = &s->cfl; }
@@ -843,6 +851,8 @@ nfe_status nfe_batch_create(int nsims, const nfe_grid *grids, const int *N, cons
         if (grids[i].lattice != NFE_D2Q9) return fail(NFE_EUNSUPPORTED, "batched sweeps are D2Q9 (simulation %d)", i);
         if (N[i] < 2 || N[i] > 5) return fail(NFE_EUNSUPPORTED, "batched sweeps take N = 2..5 (simulation %d)", i);
         if (params[i].precision != prec) return fail(NFE_EINVAL, "all simulations of a batch share one precision");
+        if (params[i].flags & NFE_NO_PHI)
+            return fail(NFE_EUNSUPPORTED, "the no-phi ablation (NFE_NO_PHI) is not available in batched sweeps (simulation %d)", i);
     }
     nfe_batch *b = new (std::nothrow) nfe_batch();
     if (!b) return fail(NFE_ENOMEM, "host allocation failed");

@@ -18,6 +18,10 @@ constexpr int kMaxMono2 = kMaxN * (kMaxN + 1) / 2;   // degree-2 monomials in 8 
 // (N-1)(N-2) values a, then (N-1)(N-2)/2 values b.
 __host__ __device__ constexpr int mono4s_count(int n) { return 3 * (n - 1) * (n - 2) / 2; }
 
+// Degree-3 monomials a <= b <= c over the N - 1 components other than i: the part of the bulk
+// flux potential that is not divisible by C_i once phi_j is dropped (the no-phi ablation).
+__host__ __device__ constexpr int mono3r_count(int n) { return (n - 1) * n * (n + 1) / 6; }
+
 // Up to N = 6 the quartic coefficients also travel with the kernel parameters (constant bank).
 constexpr int kQ4InlineMaxN = 6;
 constexpr int kQ4Inline = (kQ4InlineMaxN - 1) * mono4s_count(kQ4InlineMaxN);   // 150
@@ -48,6 +52,8 @@ struct Coef {
     int has_q4;                   // Omega != 0: degree-4 part present
     int nonconservative;          // force of Eq. 31 instead of Eq. 34
     const T *q4;                  // (N-1) x mono4s_count(N), device memory, or nullptr (Omega = 0)
+    const T *r3;                  // (N-1) x mono3r_count(N), device memory: no-phi remainder, or nullptr
+    int no_phi;                   // the no-phi ablation (flux potential without phi_j)
     T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 6); last member
 };
 

@@ -131,7 +131,8 @@ __device__ __forceinline__ T bulk_energy(const T (&c)[N], const Coef<T> &cf) {
 // (saves a load per term; the D3Q19 step gains, while in the D2Q9 step the extra register
 // pressure costs more than it saves).  Q4_ABSENT compiles no quartic code at all, for kernels
 // launched only when Omega = 0: even never-executed quartic code raises register pressure.
-enum Q4Source { Q4_GLOBAL = 0, Q4_PARAM = 1, Q4_ABSENT = 2 };
+// Q4_NOPHI reads the quartic part from device memory and adds the no-phi remainder (below).
+enum Q4Source { Q4_GLOBAL = 0, Q4_PARAM = 1, Q4_ABSENT = 2, Q4_NOPHI = 3 };
 
 template <int N, typename T, int Q4 = Q4_GLOBAL>
 __device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T (&q)[N - 1]) {
@@ -177,6 +178,28 @@ __device__ __forceinline__ void flux_poly(const T (&c)[N], const Coef<T> &cf, T 
                 for (int l = k + 1; l < N; ++l)
                     if (k != e && l != e) sb += coef(j++) * (sq[k] * sq[l]);
             q[e] += c[e] * sa + sb;
+        }
+    }
+}
+
+// The no-phi ablation: S_e += r_e(C), the cubic part of sum_j alpha_ej dE_B/dC_j (Eq. 12 without
+// phi_j) that has no factor C_e, monomials a <= b <= d over the components other than e.
+template <int N, typename T, int Q4>
+__device__ __forceinline__ void flux_rest(const T (&c)[N], const Coef<T> &cf, T (&S)[N - 1]) {
+    if constexpr (Q4 == Q4_NOPHI) {
+        constexpr int M3 = mono3r_count(N);
+#pragma unroll
+        for (int e = 0; e < N - 1; ++e) {
+            int j = e * M3;
+            T r = T(0);
+#pragma unroll
+            for (int a = 0; a < N; ++a)
+#pragma unroll
+                for (int b = a; b < N; ++b)
+#pragma unroll
+                    for (int d = b; d < N; ++d)
+                        if (a != e && b != e && d != e) r += __ldg(cf.r3 + j++) * (c[a] * c[b] * c[d]);
+            S[e] += r;
         }
     }
 }

@@ -238,6 +238,10 @@ nfe_status build_tables(int N, const double *sigma_user, const int *uidx, double
         for (int b = a; b < N; ++b) mono2.push_back(var_mono(a) + var_mono(b));
 
     out.q2.assign((N - 1) * mono2.size(), 0.0);
+    // without phi_j the cubic keeps monomials free of C_i: kept as a remainder r_i(C), in the
+    // order a <= b <= c over the components other than i
+    const int m3 = mono3r_count(N);
+    if (!with_phi) out.r3.assign((N - 1) * m3, 0.0);
     out.residual = 0.0;
     for (int i = 0; i < N - 1; ++i) {
         Poly cubic;
@@ -257,8 +261,20 @@ nfe_status build_tables(int N, const double *sigma_user, const int *uidx, double
         }
         const double scale = std::max(max_abs(h), 1e-300);
         double rest = 0.0;
+        std::vector<Mono> mono3r;
+        for (int a = 0; a < N; ++a)
+            for (int b = a; b < N; ++b)
+                for (int c = b; c < N; ++c)
+                    if (a != i && b != i && c != i) mono3r.push_back(var_mono(a) + var_mono(b) + var_mono(c));
         for (const auto &kv : h) {
-            if (mono_exp(kv.first, i) == 0) { rest = std::max(rest, std::fabs(kv.second)); continue; }
+            if (mono_exp(kv.first, i) == 0) {
+                rest = std::max(rest, std::fabs(kv.second));
+                if (!with_phi) {
+                    const auto it = std::find(mono3r.begin(), mono3r.end(), kv.first);
+                    out.r3[i * m3 + (it - mono3r.begin())] += kv.second;
+                }
+                continue;
+            }
             const Mono q = kv.first - var_mono(i);
             const auto it = std::find(mono2.begin(), mono2.end(), q);
             out.q2[i * mono2.size() + (it - mono2.begin())] += kv.second;

@@ -14,6 +14,7 @@ struct Tables {
     std::vector<double> beta, kappa, alpha, gamma;   // N x N (internal order), gamma N
     std::vector<double> q2;                           // (N-1) x N(N+1)/2, monomials a <= b
     std::vector<double> q4;                           // (N-1) x mono4s_count(N), structured quartic part (Omega != 0)
+    std::vector<double> r3;                           // (N-1) x mono3r_count(N), cubic remainder without C_i (no phi)
     double residual = 0.0;                            // largest dropped coefficient, relative
     int lambda_count = 0;
 };

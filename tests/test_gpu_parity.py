@@ -132,6 +132,24 @@ def test_absent_component_stays_exactly_zero(precision):
         assert (C[6] == 0.0).all()
 
 
+@pytest.mark.parametrize("precision,tol_c,tol_v", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)])
+def test_no_phi_ablation_matches_oracle_and_nucleates(precision, tol_c, tol_v):
+    # The no-phi ablation (Eq. 12 without phi_j, the paper's negative control): the GPU follows
+    # the oracle's literal flux potential without phi_j, and the absent fourth component appears
+    # at the interfaces (with phi_j it stays exactly zero: test_absent_component_stays_exactly_zero).
+    p = _absent_lens()
+    steps = 60
+    prm = lbm.Params(p)
+    st = lbm.run(prm, lbm.init_state(prm, p["C0"]), steps, with_phi=False)
+    Co, vo, Po, _ = lbm.fields(prm, st)
+    g = gpu_run(p, steps, precision, flags=nfe.NFE_NO_PHI)
+    assert rel(g["C"], Co) < tol_c
+    assert rel(g["v"], vo) < tol_v
+    assert np.abs(Co[3]).max() > 1e-6 and np.abs(g["C"][3]).max() > 1e-6
+    if precision == "fp64":
+        assert rel(g["C"][3], Co[3]) < 1e-9
+
+
 def test_mass_and_momentum_conservation_fp64():
     p = W.janus_2d(nx=64, ny=64, radius=12, offset=15)
     with nfe.Sim(p, "fp64") as s:
