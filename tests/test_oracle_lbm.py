@@ -266,3 +266,39 @@ def test_nonconservative_force_drifts_conservative_does_not():
     mn = np.abs(lbm.diagnostics(prm, ncon, force_form="nonconservative")["momentum"]).max() / n
     assert mc < 1e-15
     assert mn > 1e3 * max(mc, 1e-18)
+
+
+def _mode_decay_rate(tau_g, nx, steps, C0=0.1, amp=1e-4, m=0.05):
+    # Decay rate of a small single-mode perturbation of a stable binary mixture (C0 outside the
+    # spinodal), measured from the projection of C_0 onto cos(2 pi x / nx) at two times.
+    sig = np.array([[0.0, 0.005], [0.005, 0.0]])
+    p = W.base_params(9, nx, 2, 1, 2, sig, 1.0, m=m, omega_stab=0.0)
+    p["tau_g"] = tau_g
+    x = np.arange(nx)
+    mode = np.cos(2 * np.pi * x / nx)
+    C = np.zeros((2, 1, 2, nx))
+    C[0] = (C0 + amp * mode)[None, None, :]
+    C[1] = 1.0 - C[0]
+    prm = lbm.Params(p)
+    st = lbm.init_state(prm, C)
+    amps, t = [], 0
+    for target in steps:
+        st = lbm.run(prm, st, target - t)
+        t = target
+        c = lbm.components(prm, st.g)[0, 0].mean(axis=0)
+        amps.append(2.0 * np.mean((c - c.mean()) * mode))
+    return math.log(amps[0] / amps[1]) / (steps[1] - steps[0])
+
+
+@pytest.mark.slow
+def test_tau_g_sets_the_mobility():
+    # Eq. 43: the Cahn-Hilliard mobility is M = c_s^2 m (tau_g - 1/2).  In the linear regime a
+    # mode decays at a rate proportional to M times a factor fixed by the free energy and k, so
+    # the rates of tau_g = 1.4 and 0.8 are in the ratio (1.4 - 0.5) / (0.8 - 0.5) = 3, up to a
+    # lattice correction of order k^2: it must shrink about fourfold when the wavelength
+    # doubles, and the Richardson extrapolation of the two ratios must give 3.
+    r32 = _mode_decay_rate(1.4, 32, (100, 1100)) / _mode_decay_rate(0.8, 32, (100, 1100))
+    r64 = _mode_decay_rate(1.4, 64, (400, 4400)) / _mode_decay_rate(0.8, 64, (400, 4400))
+    assert abs(r32 - 3.0) < 0.12
+    assert abs(r64 - 3.0) < 0.3 * abs(r32 - 3.0)
+    assert abs((4.0 * r64 - r32) / 3.0 - 3.0) < 0.01
