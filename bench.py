@@ -286,6 +286,8 @@ def run_nfe(args):
                  ("spinodal 4096x4096 N=4", W.spinodal_2d(nx=4096, ny=4096, seed=1012), "fp32", 60, False),
                  ("spinodal 4096x4096 N=4", W.spinodal_2d(nx=4096, ny=4096, seed=1012), "f16", 60, False),
                  ("spinodal 4096x4096 N=4", W.spinodal_2d(nx=4096, ny=4096, seed=1012), "fp64", 10, False),
+                 ("spinodal 4096x4096 N=4, tau_g = 1.3 (stored g)", dict(W.spinodal_2d(nx=4096, ny=4096, seed=1012), tau_g=1.3),
+                  "fp32", 30, False),
                  ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "fp32", 20, False),
                  ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "bf16", 20, False)]
         for name, q, prec, K, fl in cases:

@@ -94,7 +94,7 @@ typedef struct {
     const double *tau;        /* N relaxation times tau_i > 1/2; omega+ = 1/tau of
                                  the component with the largest C (Eq. 42) (host) */
     double lambda_trt;        /* magic parameter of Eq. 26; < 0 selects BGK (omega- = omega+) */
-    double m;                 /* coefficient m of g^eq (Eq. 40); mobility M = m / 6 (Eq. 43, tau_g = 1) */
+    double m;                 /* coefficient m of g^eq (Eq. 40); mobility M = m (tau_g - 1/2) / 3 (Eq. 43) */
     double D;                 /* interface width (Sec. II; the paper uses 4) */
     double omega_stab;        /* Omega of Eq. 17; NaN selects 0 when every spreading
                                  parameter (Eq. 16) is negative and 1/90 otherwise */
@@ -104,6 +104,12 @@ typedef struct {
     int flags;                /* NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI (ablations) */
     int scale_exp;            /* FP16 storage scale 2^scale_exp; ignored otherwise */
     void *cuda_stream;        /* cudaStream_t to queue work on (borrowed); NULL = default */
+    double tau_g;             /* relaxation time of the component populations g (Sec. III B); 0 or 1
+                                 selects tau_g = 1, where g* = g^eq and g needs no storage.  Other
+                                 values (> 1/2) store the N-1 evolved components' g populations
+                                 ((N-1) x Q planes, two buffers, compute type) and run D2Q9 single
+                                 simulations only: NFE_EUNSUPPORTED for D3Q19, for batches and
+                                 together with NFE_NO_PHI */
 } nfe_params;
 
 /* Global quantities of the current state, reduced on the GPU in FP64. */

@@ -202,11 +202,13 @@ __device__ __forceinline__ T fload(const SF *p, double w, T finv) {
     }
 }
 
-template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4>
+// TAUG: the stored-g path (tau_g != 1), with the component populations in gin / gout.
+template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4, bool TAUG = false>
 __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, const SF *__restrict__ fin,
                                              SF *__restrict__ fout, const T *__restrict__ Cin,
                                              T *__restrict__ Cout, int *__restrict__ flag,
-                                             int x0, int y0, unsigned char *smem) {
+                                             int x0, int y0, unsigned char *smem,
+                                             const T *__restrict__ gin = nullptr, T *__restrict__ gout = nullptr) {
     using Sh = Fused2DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     using RB = typename Sh::RB;
@@ -396,6 +398,78 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     }
     __syncthreads();
 
+    // ---- phase 4 with stored g (tau_g != 1): pull, relax and bounce back -----
+    // g_k(x, t+1) = g*_k(x - e_k), g* = g + (g^eq - g) / tau_g, with g^eq_k(x - e_k) from the
+    // shared (C, v, S) records; a source beyond a wall gives g*_kbar(x) (Eqs. 44-45); then
+    // C_i(x, t+1) = sum_k g_{i,k}(x, t+1) (Eq. 41).
+    if constexpr (TAUG) {
+        if (own) {
+            const T m = cf.m, omg = cf.gomega;
+            const int ib = (ty + 1) * Sh::BX + (tx + 1);
+            T r0[RB::NVP];
+            srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib, r0);
+            const T vv0 = r0[N - 1] * r0[N - 1] + r0[N] * r0[N];
+            const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1;
+            constexpr int offB[9] = {0, 1, -1, TX + 2, -(TX + 2), TX + 3, -(TX + 3), -(TX + 2) + 1, (TX + 2) - 1};
+            constexpr int Q = 9;
+            T csum[N - 1];
+#pragma unroll
+            for (int e = 0; e < N - 1; ++e) csum[e] = T(0);
+            sfor<0, 9, 1>([&](auto kc_) {
+                constexpr int k = decltype(kc_)::value;
+                const T wk = T(LD2Q9::w(k));
+                if constexpr (k == 0) {
+                    const T s0k = wk * (-T(1.5) * vv0);
+#pragma unroll
+                    for (int e = 0; e < N - 1; ++e) {
+                        const T geq = r0[e] * (T(1) + s0k) + (T(1) - wk) * m * r0[N + 1 + e];
+                        const T gg = gin[size_t(e * Q) * n + s0];
+                        const T post = gg + omg * (geq - gg);
+                        gout[size_t(e * Q) * n + s0] = post;
+                        csum[e] += post;
+                    }
+                } else {
+                    constexpr int kb = opp(k);
+                    if (wall0 && ((wall0 >> kb) & 1u)) {
+                        const T eu = T(LD2Q9::ex(kb)) * r0[N - 1] + T(LD2Q9::ey(kb)) * r0[N];
+                        const T skb = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
+#pragma unroll
+                        for (int e = 0; e < N - 1; ++e) {
+                            const T geq = r0[e] * skb - wk * m * r0[N + 1 + e];
+                            const T gg = gin[size_t(e * Q + kb) * n + s0];
+                            const T post = gg + omg * (geq - gg);
+                            gout[size_t(e * Q + k) * n + s0] = post;
+                            csum[e] += post;
+                        }
+                    } else {
+                        T r[RB::NVP];
+                        srec_load<T, 2 * N>(sB, Sh::BCOUNT, ib + offB[kb], r);
+                        const T eu = T(LD2Q9::ex(k)) * r[N - 1] + T(LD2Q9::ey(k)) * r[N];
+                        const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * (r[N - 1] * r[N - 1] + r[N] * r[N]));
+                        const int src = fast ? s0 - (LD2Q9::ex(k) + nx * LD2Q9::ey(k))
+                                             : wrap(sx - LD2Q9::ex(k), nx) + nx * wrap(sy - LD2Q9::ey(k), ny);
+#pragma unroll
+                        for (int e = 0; e < N - 1; ++e) {
+                            const T geq = r[e] * sk - wk * m * r[N + 1 + e];
+                            const T gg = gin[size_t(e * Q + k) * n + src];
+                            const T post = gg + omg * (geq - gg);
+                            gout[size_t(e * Q + k) * n + s0] = post;
+                            csum[e] += post;
+                        }
+                    }
+                }
+            });
+            bool bad = false;
+#pragma unroll
+            for (int e = 0; e < N - 1; ++e) {
+                Cout[e * n + s0] = csum[e];
+                bad |= !isfinite(csum[e]);
+            }
+            if (bad) atomicOr(flag, 1);
+        }
+        return;
+    }
+
     // ---- phase 4: Cahn-Hilliard update of the own site ----------------------
     if (own) {
         const T m = cf.m;
@@ -456,28 +530,31 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
 // that suits it.
 template <typename T, int NT> struct Fused2DOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 8 : NT <= 256 ? 3 : 2) : 1; };
 
-template <int N, typename T, typename SF, int TX, int TY, int Q4>
+template <int N, typename T, typename SF, int TX, int TY, int Q4, bool TAUG>
 __global__ void __launch_bounds__(TX * TY, (Fused2DOcc<T, TX * TY>::value))
 k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag) {
+          const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag,
+          const T *__restrict__ gin, T *__restrict__ gout) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused2d_tile<N, T, SF, TX, TY, false, Q4>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX, blockIdx.y * TY, smem_raw);
+    fused2d_tile<N, T, SF, TX, TY, false, Q4, TAUG>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX,
+                                                    blockIdx.y * TY, smem_raw, gin, gout);
 }
 
-template <int N, typename T, typename SF, int TX, int TY, int Q4>
+template <int N, typename T, typename SF, int TX, int TY, int Q4, bool TAUG = false>
 cudaError_t launch_fused2d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Fused2DShape<N, T, TX, TY>;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY, Q4>,
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY, Q4, TAUG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused2d<N, T, SF, TX, TY, Q4><<<grid, TX * TY, Sh::BYTES, st>>>(
+    k_fused2d<N, T, SF, TX, TY, Q4, TAUG><<<grid, TX * TY, Sh::BYTES, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
-        static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]), b.flag);
+        static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]), b.flag,
+        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]));
     return cudaGetLastError();
 }
 
@@ -490,6 +567,8 @@ template <int N, typename T, typename SF>
 struct Fused2DLaunch {
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        // stored g (tau_g != 1): one tile shape
+        if (b.g[0]) return launch_fused2d<N, T, SF, 32, 8, Q4_GLOBAL, true>(g, cf, b, cur, st);
         if (cf.no_phi) return launch<Q4_NOPHI>(g, cf, b, cur, st, variant);
         return cf.has_q4 ? launch<Q4_GLOBAL>(g, cf, b, cur, st, variant) : launch<Q4_ABSENT>(g, cf, b, cur, st, variant);
     }
@@ -505,7 +584,7 @@ struct Fused2DLaunch {
         using B = Launch<LD2Q9, N, T, SF>;
         static const Ops o = {9, 2, N, prec, 1, {K_FUSED, K_FUSED}, {&step, nullptr}, 3,
                               {"fused 32x4", "fused 32x8", "fused 32x16", nullptr},
-                              &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C,
+                              &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
                               int(sizeof(SF)), int(sizeof(T))};
         return &o;
     }

@@ -506,7 +506,7 @@ struct Fused3DLaunch {
         using B = Launch<LD3Q19, N, T, SF>;
         static const Ops o = {19, 3, N, prec, 1, {K_FUSED, K_FUSED}, {&step, nullptr}, 2,
                               {"fused3d 32x4", "fused3d 32x8", nullptr, nullptr},
-                              &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C,
+                              &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
                               int(sizeof(SF)), int(sizeof(T))};
         return &o;
     }

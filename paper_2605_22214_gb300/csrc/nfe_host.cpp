@@ -97,7 +97,8 @@ struct nfe_sim {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int64_t step = 0;
-    size_t fplanes_bytes = 0, cplanes_bytes = 0;
+    size_t fplanes_bytes = 0, cplanes_bytes = 0, gplanes_bytes = 0;   // gplanes: stored g (tau_g != 1)
+    double tau_g = 1.0;
     size_t fields_planes = 0;
     size_t device_bytes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -140,6 +141,7 @@ void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
     c.q4 = static_cast<const T *>(s.q4dev);
     c.r3 = static_cast<const T *>(s.r3dev);
     c.no_phi = (p.flags & NFE_NO_PHI) ? 1 : 0;
+    c.gomega = T(1.0 / s.tau_g);
     if (N <= kQ4InlineMaxN)
         for (size_t j = 0; j < s.tab.q4.size(); ++j) c.q4c[j] = T(s.tab.q4[j]);
 }
@@ -151,7 +153,8 @@ nfe_status free_all(nfe_sim *s) {
     for (auto e : s->event_pool) cudaEventDestroy(e);
     s->event_pool.clear();
     void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
-                    s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev};
+                    s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev,
+                    s->buf.g[0], s->buf.g[1]};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
@@ -313,6 +316,11 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     if (p->flags & ~(NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI)) return fail(NFE_EINVAL, "unknown flags");
     if ((p->flags & NFE_NO_PHI) && grid->lattice != NFE_D2Q9)
         return fail(NFE_EUNSUPPORTED, "NFE_NO_PHI (the no-phi ablation) runs on D2Q9 only");
+    const double tau_g = p->tau_g == 0.0 ? 1.0 : p->tau_g;
+    if (!(tau_g > 0.5) || !std::isfinite(tau_g)) return fail(NFE_EINVAL, "tau_g must be > 1/2 (0 selects 1)");
+    const bool stored_g = tau_g != 1.0;
+    if (stored_g && grid->lattice != NFE_D2Q9) return fail(NFE_EUNSUPPORTED, "tau_g != 1 runs on D2Q9 only");
+    if (stored_g && (p->flags & NFE_NO_PHI)) return fail(NFE_EUNSUPPORTED, "tau_g != 1 together with NFE_NO_PHI");
     if (p->precision == NFE_FP32_F16STORE && (p->scale_exp < -20 || p->scale_exp > 20))
         return fail(NFE_EINVAL, "scale_exp outside -20..20");
 
@@ -344,6 +352,8 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     const int Q = s->ops->Q;
     s->fplanes_bytes = size_t(Q - 1) * n * s->ops->f_elem_bytes;
     s->cplanes_bytes = size_t(N - 1) * n * s->ops->c_elem_bytes;
+    s->gplanes_bytes = stored_g ? size_t(N - 1) * Q * n * s->ops->c_elem_bytes : 0;
+    s->tau_g = tau_g;
     s->fields_planes = size_t(std::max(N + 7, Q - 1));
     const size_t ce = s->ops->c_elem_bytes;
 #define ALLOC(ptr, bytes) do { st = dev_alloc(s, reinterpret_cast<void **>(&(ptr)), (bytes)); \
@@ -353,6 +363,10 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     ALLOC(s->buf.C[0], s->cplanes_bytes);
     ALLOC(s->buf.C[1], s->cplanes_bytes);
     ALLOC(s->buf.flag, sizeof(int));
+    if (stored_g) {
+        ALLOC(s->buf.g[0], s->gplanes_bytes);
+        ALLOC(s->buf.g[1], s->gplanes_bytes);
+    }
     if (!s->tab.q4.empty()) ALLOC(s->q4dev, s->tab.q4.size() * ce);
     if (!s->tab.r3.empty()) ALLOC(s->r3dev, s->tab.r3.size() * ce);
 #undef ALLOC
@@ -374,6 +388,7 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
 
     cudaError_t e = cudaMemsetAsync(s->buf.f[0], 0, s->fplanes_bytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->buf.C[0], 0, s->cplanes_bytes, s->stream);
+    if (e == cudaSuccess && s->buf.g[0]) e = cudaMemsetAsync(s->buf.g[0], 0, s->gplanes_bytes, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) { free_all(s); delete s; return cuda_fail(e, "initialise state"); }
@@ -407,6 +422,8 @@ nfe_status nfe_set_fields(nfe_sim *s, const double *C, const double *v) {
     } else {
         CK(cudaMemsetAsync(s->buf.f[0], 0, s->fplanes_bytes, s->stream));
     }
+    // stored g (tau_g != 1): g = g^eq(C, v, S(C)) at the start
+    if (s->buf.g[0]) CK(s->ops->init_g(s->geom, s->coef, s->buf, 0, v ? s->buf.fields + (N - 1) * n : nullptr, s->stream));
     CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->buf.cur = 0;
@@ -522,7 +539,8 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
     out->variant = s->variant;
     out->nvariants = s->ops->nvariants;
     out->min_bytes_per_site = 2.0 * ((s->ops->Q - 1) * s->ops->f_elem_bytes + (s->N - 1) * s->ops->c_elem_bytes);
-    out->state_bytes = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
+    if (s->buf.g[0]) out->min_bytes_per_site += 2.0 * (s->N - 1) * s->ops->Q * s->ops->c_elem_bytes;
+    out->state_bytes = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes;
     out->device_bytes = s->device_bytes;
     return NFE_OK;
 }
@@ -530,7 +548,7 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
 nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
     nfe_status st = check_sim(s);
     if (st != NFE_OK) return st;
-    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
+    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes;
     if (!host || bytes != need) return fail(NFE_EINVAL, "state buffer must be %zu bytes", need);
     char *h = static_cast<char *>(host);
     CK(cudaStreamSynchronize(s->stream));
@@ -538,6 +556,9 @@ nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
     CK(cudaMemcpyAsync(h + sizeof(int64_t), s->buf.f[s->buf.cur], s->fplanes_bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaMemcpyAsync(h + sizeof(int64_t) + s->fplanes_bytes, s->buf.C[s->buf.cur], s->cplanes_bytes,
                        cudaMemcpyDeviceToHost, s->stream));
+    if (s->buf.g[0])
+        CK(cudaMemcpyAsync(h + sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes, s->buf.g[s->buf.cur],
+                           s->gplanes_bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return NFE_OK;
 }
@@ -545,7 +566,7 @@ nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
 nfe_status nfe_set_state(nfe_sim *s, const void *host, size_t bytes) {
     nfe_status st = check_sim(s);
     if (st != NFE_OK) return st;
-    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes;
+    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes;
     if (!host || bytes != need) return fail(NFE_EINVAL, "state buffer must be %zu bytes", need);
     const char *h = static_cast<const char *>(host);
     CK(cudaStreamSynchronize(s->stream));
@@ -553,6 +574,9 @@ nfe_status nfe_set_state(nfe_sim *s, const void *host, size_t bytes) {
     CK(cudaMemcpyAsync(s->buf.f[s->buf.cur], h + sizeof(int64_t), s->fplanes_bytes, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemcpyAsync(s->buf.C[s->buf.cur], h + sizeof(int64_t) + s->fplanes_bytes, s->cplanes_bytes,
                        cudaMemcpyHostToDevice, s->stream));
+    if (s->buf.g[0])
+        CK(cudaMemcpyAsync(s->buf.g[s->buf.cur], h + sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes,
+                           s->gplanes_bytes, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return NFE_OK;
@@ -853,6 +877,8 @@ nfe_status nfe_batch_create(int nsims, const nfe_grid *grids, const int *N, cons
         if (params[i].precision != prec) return fail(NFE_EINVAL, "all simulations of a batch share one precision");
         if (params[i].flags & NFE_NO_PHI)
             return fail(NFE_EUNSUPPORTED, "the no-phi ablation (NFE_NO_PHI) is not available in batched sweeps (simulation %d)", i);
+        if (params[i].tau_g != 0.0 && params[i].tau_g != 1.0)
+            return fail(NFE_EUNSUPPORTED, "batched sweeps run tau_g = 1 (simulation %d)", i);
     }
     nfe_batch *b = new (std::nothrow) nfe_batch();
     if (!b) return fail(NFE_ENOMEM, "host allocation failed");

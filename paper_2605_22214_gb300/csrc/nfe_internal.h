@@ -54,6 +54,7 @@ struct Coef {
     const T *q4;                  // (N-1) x mono4s_count(N), device memory, or nullptr (Omega = 0)
     const T *r3;                  // (N-1) x mono3r_count(N), device memory: no-phi remainder, or nullptr
     int no_phi;                   // the no-phi ablation (flux potential without phi_j)
+    T gomega;                     // 1 / tau_g (stored-g path, tau_g != 1)
     T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 6); last member
 };
 
@@ -65,6 +66,7 @@ extern const char *kKernelNames[K_NKINDS];
 struct Buffers {
     void *f[2];           // populations k = 1..Q-1, planar, storage type
     void *C[2];           // evolved volume fractions, planar, compute type
+    void *g[2];           // component populations ((N-1) x Q planes, compute type) when tau_g != 1, else null
     double *fields;       // moments output: C (N), v (3), P, Fs (3) planes, FP64
     double *partials;     // reduction partials
     double *diag;         // reduction result
@@ -96,6 +98,8 @@ struct Ops {
     cudaError_t (*unpack_f)(const Geom &, const void *coef, const Buffers &, int cur, double *out, cudaStream_t);
     // evolved C from FP64 device array ((N-1) x n) into buffer cur
     cudaError_t (*pack_C)(const Geom &, const Buffers &, int cur, const double *in, cudaStream_t);
+    // g = g^eq(C, v, S(C)) in buffer cur from C of buffer cur and an FP64 velocity (3 x n, or null)
+    cudaError_t (*init_g)(const Geom &, const void *coef, const Buffers &, int cur, const double *v, cudaStream_t);
     int f_elem_bytes;     // bytes per stored population
     int c_elem_bytes;     // bytes per stored volume fraction (and per scratch value)
 };

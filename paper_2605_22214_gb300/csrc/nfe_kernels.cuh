@@ -379,6 +379,39 @@ __global__ void k_init_f(Geom g, Coef<T> cf, const double *__restrict__ v, SF *_
     }
 }
 
+// Stored-g path (tau_g != 1): g = g^eq(C, v, S(C)) at the start (Eq. 40 as read: the C_i part
+// of the zeroth moment in the rest population, g^eq_k = C_i (delta_k0 + s_k(v)) + (1 - w_0) m S_i
+// for k = 0 and - w_k m S_i otherwise), from the C of the state and an FP64 velocity (null: 0).
+// Layout of g: plane (e Q + k) for evolved slot e and direction k.
+template <class L, int N, typename T>
+__global__ void k_init_g(Geom g, Coef<T> cf, const T *__restrict__ C, const double *__restrict__ v,
+                         T *__restrict__ gout) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const int x = s % g.nx;
+    const int r = s / g.nx;
+    const int y = r % g.ny;
+    const int z = r / g.ny;
+    const size_t n = size_t(g.n);
+    Stencil<L, N, T> st;
+    stencil<L, N, T>(g, cf, C, s, x, y, z, st);
+    T Fs[3], S[N - 1];
+    force_and_potential<L, N, T>(cf, st, Fs, S);
+    const T a0 = v ? T(v[s]) : T(0), a1 = v ? T(v[n + s]) : T(0), a2 = v ? T(v[2 * n + s]) : T(0);
+    const T uu = a0 * a0 + a1 * a1 + a2 * a2;
+#pragma unroll
+    for (int k = 0; k < L::Q; ++k) {
+        const T wk = T(L::w(k));
+        const T eu = T(L::ex(k)) * a0 + T(L::ey(k)) * a1 + T(L::ez(k)) * a2;
+        const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
+#pragma unroll
+        for (int e = 0; e < N - 1; ++e) {
+            const T geq = k == 0 ? st.c[e] * (T(1) + sk) + (T(1) - wk) * cf.m * S[e] : st.c[e] * sk - wk * cf.m * S[e];
+            gout[(size_t(e) * L::Q + k) * n + s] = geq;
+        }
+    }
+}
+
 template <class L, typename T, typename SF>
 __global__ void k_unpack_f(Geom g, Coef<T> cf, const SF *__restrict__ f, double *__restrict__ out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -435,6 +468,12 @@ struct Launch {
     static cudaError_t pack_C(const Geom &g, const Buffers &b, int cur, const double *in, cudaStream_t st) {
         const long long total = g.n * (N - 1);
         k_pack_C<T><<<blocks_for(total, 256), 256, 0, st>>>(total, in, static_cast<T *>(b.C[cur]));
+        return cudaGetLastError();
+    }
+    static cudaError_t init_g(const Geom &g, const void *coef, const Buffers &b, int cur, const double *v, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_init_g<L, N, T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, cf, static_cast<const T *>(b.C[cur]), v,
+                                                                  static_cast<T *>(b.g[cur]));
         return cudaGetLastError();
     }
 };

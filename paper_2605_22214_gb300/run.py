@@ -40,6 +40,7 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--variant", type=int, default=-1, help="tile shape (-1: autotune)")
+    ap.add_argument("--tau-g", type=float, default=1.0, help="relaxation time of the component populations")
     ap.add_argument("--sims", type=int, default=512, help="batch: number of simulations")
     ap.add_argument("--mode", default="auto", choices=["persistent", "per_step", "auto"], help="batch: launch form")
     args = ap.parse_args()
@@ -51,6 +52,7 @@ def main():
     if args.workload == "batch":
         return run_batch(nfe, torch, args)
     p = make(args.workload, args.size)
+    p["tau_g"] = args.tau_g
     stream = torch.cuda.Stream()
     with nfe.Sim(p, args.precision, stream=stream.cuda_stream, scale_exp=10) as s:
         s.set_fields(p["C0"])

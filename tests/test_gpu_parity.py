@@ -150,6 +150,41 @@ def test_no_phi_ablation_matches_oracle_and_nucleates(precision, tol_c, tol_v):
         assert rel(g["C"][3], Co[3]) < 1e-9
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case,tau_g", [("lens_walls_N3", 0.8), ("spinodal_N4", 1.3)])
+def test_stored_g_tau_g_parity_with_oracle(precision, case, tau_g):
+    # tau_g != 1 (Sec. III B): the component populations are stored, relaxed with 1/tau_g,
+    # pulled and bounced back; the GPU follows the oracle's literal g populations.
+    p = CASES[case]()
+    p["tau_g"] = tau_g
+    compare(p, 100, precision)
+
+
+def test_stored_g_conservation_checkpoint_and_absent_component():
+    # tau_g = 1.3, FP64: per-component mass to round-off, a checkpoint (which carries g)
+    # restores the run bitwise, and an absent component stays exactly zero.
+    p = W.spinodal_2d(nx=48, ny=40, seed=7)
+    p["tau_g"] = 1.3
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        m0 = s.diagnostics()["mass"]
+        s.step(50)
+        snap = s.get_state()
+        s.step(50)
+        a = s.get_state()
+        np.testing.assert_allclose(s.diagnostics()["mass"], m0, rtol=1e-12)
+        s.set_state(snap)
+        s.step(50)
+        assert np.array_equal(s.get_state(), a)
+    q = _absent_lens()
+    q["tau_g"] = 1.3
+    with nfe.Sim(q, "fp64") as s:
+        s.set_fields(q["C0"])
+        s.step(200)
+        C, _, _ = s.fields()
+        assert (C[3] == 0.0).all()
+
+
 def test_mass_and_momentum_conservation_fp64():
     p = W.janus_2d(nx=64, ny=64, radius=12, offset=15)
     with nfe.Sim(p, "fp64") as s:
