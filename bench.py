@@ -319,9 +319,11 @@ def run_nfe(args):
 
     batched = None
     precision = None
+    coarsening = None
     if not args.no_extras:
         batched = batch_sweep_measure(nfe, torch, stream, args.batch_steps)
         precision = precision_study(nfe, stream)
+        coarsening = coarsening_measure(nfe, stream)
 
     s32 = path_summary(r32)
     s64 = path_summary(results["fp64"])
@@ -355,6 +357,7 @@ def run_nfe(args):
         "extras": extras,
         "batched": batched,
         "precision_study": precision,
+        "coarsening": coarsening,
         "clocks": r32["clocks"].summary() if r32["clocks"] is not None else None,
     }
     for r in results.values():
@@ -367,11 +370,33 @@ def run_nfe(args):
         dist.destroy_process_group()
 
 
+def coarsening_measure(nfe, stream, n=1600, t_end=40000):
+    """Domain growth of the paper's binary phase-separation run (Sec. IV): n^2, C_i ~ U(0, 1)
+    renormalised, sigma = 0.005, eta = 1/6, FP32.  L (mean over the two components, the
+    equation for L_i of Sec. IV, via nfe_domain_size) at geometric times; the late-time exponent
+    is the least-squares slope of log L on log t over the last half of the samples."""
+    p = W.phase_separation_2d(nx=n, ny=n, N=2, seed=1013)
+    times = [int(round(500 * (t_end / 500) ** (i / 10))) for i in range(11)]
+    Ls = []
+    with nfe.Sim(p, "fp32", stream=stream.cuda_stream) as s:
+        s.set_fields(p["C0"])
+        t = 0
+        for target in times:
+            s.step(target - t)
+            t = target
+            Ls.append(s.domain_size()[1])
+    half = len(times) // 2
+    a = float(np.polyfit(np.log(times[half:]), np.log(Ls[half:]), 1)[0])
+    return {"workload": f"binary phase separation {n}x{n} (C_i ~ U(0, 1) renormalised, sigma = 0.005, tau = 1, m = 0.1, "
+                        "seed 1013), FP32", "t": times, "L": [round(x, 3) for x in Ls], "late_exponent": round(a, 3),
+            "expected": "2/3 (inertial hydrodynamic coarsening, Sec. IV)"}
+
+
 def precision_study(nfe, stream, n=128, steps=300):
     """Four Janus drops (the 256^3 layout scaled to n^3), FP32 compute with FP32 / FP16 / BF16
     storage of f against the FP64 path: volume-fraction error, Laplace-pressure error of each
     drop (mean P inside minus mean P in the matrix) and momentum drift per site."""
-    p = W.janus_3d(n=n, radius=32.0 * n / 256.0, seed=1004)
+    p = W.janus_3d(n=n, radius=8.0, seed=1004)
     R = p["radius"]
     z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
     dists = [np.sqrt((x - cx) ** 2 + (y - cy) ** 2 + (z - cz) ** 2) for cx, cy, cz in p["centres"]]

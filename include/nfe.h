@@ -179,6 +179,21 @@ nfe_status nfe_populations(nfe_sim *sim, double *f);
 /* FP64 reductions of the current state on the GPU.  Synchronises. */
 nfe_status nfe_diagnostics(nfe_sim *sim, nfe_diag *out);
 
+/* Domain size of the phase-separation study (Sec. IV, the equation for L_i):
+ * lambda_i = H(C_i - 1/2) (H(0) = 1), its discrete Fourier transform over the grid
+ * taken as periodic (cuFFT), and L_i = 2 pi sum_{k != 0} |lambda_i(k)|^2 /
+ * sum_{k != 0} |k| |lambda_i(k)|^2 with k = 2 pi (m_x / n_x, m_y / n_y, m_z / n_z),
+ * the folded integer m in (-n/2, n/2].
+ * L: host, N + 1 doubles: L_i in the user's component order, then their mean over
+ *    the finite ones (a component without interface, lambda uniform, gives NaN).
+ * nbins > 0: also the circularly averaged S_c(k) = <|lambda_c(k)|^2> of user
+ *    component `component` in shells |k| ~ b dk, b = 1 .. nbins, dk = 2 pi / min(n_x,
+ *    n_y[, n_z]) (host, nbins doubles; 0 for an empty shell).  nbins = 0: Sk unused.
+ * The cuFFT plan and scratch are allocated on the first call and kept with the
+ * simulation.  NFE_EINVAL for NULL L, nbins outside 0..2^20 or, with nbins > 0,
+ * NULL Sk or a component outside 0..N-1.  Synchronises. */
+nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, double *Sk);
+
 /* Raw state (checkpoint / resume, host buffer of info.state_bytes bytes):
  * populations and evolved volume fractions in device format, plus the step
  * counter.  get then set restores the simulation bit for bit. */

@@ -28,7 +28,7 @@ D3Q19 = 19
 __all__ = [
     "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
     "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
-    "batch_sweep", "random_sigma", "random_simplex_points", "CONFIGS",
+    "batch_sweep", "random_sigma", "random_simplex_points", "phase_separation_2d", "CONFIGS",
 ]
 
 
@@ -129,6 +129,19 @@ def spinodal_2d(nx=512, ny=512, N=4, seed=1002, amp=0.02, sigma=0.005, tau=0.8, 
     return p
 
 
+def phase_separation_2d(nx=400, ny=400, N=4, seed=1013, sigma=0.005, tau=1.0, m=0.1):
+    """Phase-separation start of Sec. IV: C_i ~ U(0, 2/N) on every site, renormalised to sum 1;
+    all sigma_ij equal, eta_i = 1/6 (tau = 1)."""
+    rng = np.random.default_rng(seed)
+    C = rng.uniform(0.0, 2.0 / N, size=(N, 1, ny, nx))
+    C /= C.sum(axis=0, keepdims=True)
+    sig = np.full((N, N), float(sigma))
+    np.fill_diagonal(sig, 0.0)
+    p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, name=f"phase_separation_{nx}x{ny}_N{N}")
+    p["C0"] = C
+    return p
+
+
 def layered_poiseuille(nx=32, ny=32, nz=192, taus=(0.6, 0.7, 0.8, 0.9, 1.0, 1.2),
                        force=1e-6, lattice=D3Q19, absent=True, sigma=0.005, m=1.0 / 50.0):
     """Equal fluid layers stacked along the wall-normal axis with a body force along x.
@@ -181,8 +194,13 @@ def _janus_fields(x, y, z, centres, pairs, radius, N, split_axis=0):
     return C
 
 
-def janus_3d(n=256, radius=32.0, seed=1004, N=4, tau=1.0, m=1.0 / 50.0):
-    """Four Janus droplets (two components each, split by the plane x = x_c) in matrix C1."""
+def janus_3d(n=256, radius=None, seed=1004, N=4, tau=1.0, m=1.0 / 50.0):
+    """Four Janus droplets (two components each, split by the plane x = x_c) in matrix C1.
+
+    radius in lattice units; the default n / 8 is the 256^3 layout's radius 32 at any size.
+    """
+    if radius is None:
+        radius = n / 8.0
     rng = np.random.default_rng(seed)
     sig = random_sigma(rng, N)
     x, y, z = _coords(n, n, n)
@@ -190,11 +208,11 @@ def janus_3d(n=256, radius=32.0, seed=1004, N=4, tau=1.0, m=1.0 / 50.0):
     centres = [(q - 0.5, q - 0.5, q - 0.5), (3 * q - 0.5, 3 * q - 0.5, q - 0.5),
                (q - 0.5, 3 * q - 0.5, 3 * q - 0.5), (3 * q - 0.5, q - 0.5, 3 * q - 0.5)]
     pairs = [(1, 2), (2, 3), (1, 3), (1, 2)]
-    C = _janus_fields(x, y, z, centres, pairs, radius * n / 256.0 if n != 256 else radius, N)
+    C = _janus_fields(x, y, z, centres, pairs, radius, N)
     p = base_params(D3Q19, n, n, n, N, sig, tau, m=m, name=f"janus3d_{n}^3_N{N}")
     p["C0"] = C
     p["centres"] = centres
-    p["radius"] = radius * n / 256.0 if n != 256 else radius
+    p["radius"] = radius
     return p
 
 

@@ -1,4 +1,4 @@
-"""Sec. IV observables: Neumann angles, layered Poiseuille flow, Laplace pressure.
+"""Sec. IV observables: Neumann angles, layered Poiseuille flow, Laplace pressure, domain size.
 
 Oracle code (test infrastructure only).  Plain numpy in float64.
 """
@@ -132,3 +132,27 @@ def lens_angle(C_lens, keep=0.6):
     n2 = np.array([px - c2[0], py - c2[1]]) / c2[2]
     psi = math.acos(max(-1.0, min(1.0, float(n1 @ n2))))
     return math.degrees(math.pi - psi)
+
+
+def domain_size(C):
+    """Domain size of every component (Sec. IV, the equation for L_i), with the mean over them.
+
+    lambda_i = H(C_i - 1/2) (H(0) = 1); S_i(k) = |lambda_i(k)|^2 from the discrete Fourier
+    transform over the grid taken as periodic; L_i = 2 pi sum_{k != 0} S_i(k) /
+    sum_{k != 0} |k| S_i(k), the k-plane integrals of the circularly averaged S_i written
+    as sums over the grid's modes, k = 2 pi m / n per axis.  C has shape (N, nz, ny, nx);
+    returns (L array of N values, mean of the finite ones).
+    """
+    C = np.asarray(C, dtype=np.float64)
+    shape = C.shape[1:]
+    ks = np.meshgrid(*[2.0 * np.pi * np.fft.fftfreq(n) for n in shape], indexing="ij")
+    kabs = np.sqrt(sum(k * k for k in ks))
+    L = np.empty(C.shape[0])
+    for i in range(C.shape[0]):
+        lam = (C[i] >= 0.5).astype(np.float64)
+        S = np.abs(np.fft.fftn(lam)) ** 2
+        S.flat[0] = 0.0                                  # k = 0 is excluded
+        den = np.sum(kabs * S)
+        L[i] = 2.0 * np.pi * S.sum() / den if den > 0.0 else np.nan
+    fin = L[np.isfinite(L)]
+    return L, (fin.mean() if fin.size else np.nan)

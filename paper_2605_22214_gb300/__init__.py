@@ -31,7 +31,7 @@ STATUS = {0: "NFE_OK", 1: "NFE_EINVAL", 2: "NFE_ENOMEM", 3: "NFE_ECUDA", 4: "NFE
 
 # every symbol include/nfe.h declares
 EXPORTS = ["nfe_create", "nfe_set_fields", "nfe_step", "nfe_sync", "nfe_fields", "nfe_populations",
-           "nfe_diagnostics", "nfe_get_state", "nfe_set_state", "nfe_get_info", "nfe_profile_enable",
+           "nfe_diagnostics", "nfe_domain_size", "nfe_get_state", "nfe_set_state", "nfe_get_info", "nfe_profile_enable",
            "nfe_profile_read", "nfe_destroy", "nfe_status_string", "nfe_last_error",
            "nfe_bulk_potential_host", "nfe_set_variant", "nfe_field_stats_static",
            "nfe_batch_create", "nfe_batch_set_fields", "nfe_batch_step", "nfe_batch_set_mode",
@@ -101,6 +101,7 @@ def load():
         "nfe_fields": ([P, dp, dp, dp], C.c_int),
         "nfe_populations": ([P, dp], C.c_int),
         "nfe_diagnostics": ([P, C.POINTER(nfe_diag)], C.c_int),
+        "nfe_domain_size": ([P, dp, C.c_int, C.c_int, dp], C.c_int),
         "nfe_get_state": ([P, P, C.c_size_t], C.c_int),
         "nfe_set_state": ([P, P, C.c_size_t], C.c_int),
         "nfe_get_info": ([P, C.POINTER(nfe_info)], C.c_int),
@@ -217,6 +218,14 @@ def nfe_diagnostics(h):
                 max_speed=d.max_speed, nonfinite=d.nonfinite)
 
 
+def nfe_domain_size(h, N, component=0, nbins=0):
+    """(L of every component (user order), their mean, shell-averaged S(k) of `component` or None)."""
+    L = np.zeros(N + 1)
+    Sk = np.zeros(max(nbins, 1))
+    _check(load().nfe_domain_size(h, _dptr(L), int(component), int(nbins), _dptr(Sk) if nbins > 0 else None))
+    return L[:N], L[N], (Sk[:nbins] if nbins > 0 else None)
+
+
 def nfe_get_info(h):
     i = nfe_info()
     _check(load().nfe_get_info(h, C.byref(i)))
@@ -324,6 +333,9 @@ class Sim:
 
     def diagnostics(self):
         return nfe_diagnostics(self.h)
+
+    def domain_size(self, component=0, nbins=0):
+        return nfe_domain_size(self.h, self.N, component, nbins)
 
     def info(self):
         return nfe_get_info(self.h)

@@ -76,7 +76,7 @@ def build(verbose=False, force=False):
     with cf.ThreadPoolExecutor(workers) as ex:
         objs = list(ex.map(run, jobs))
     tmp = LIB + ".tmp"
-    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
+    link = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lcufft"]
     r = subprocess.run(link, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + r.stdout + r.stderr)

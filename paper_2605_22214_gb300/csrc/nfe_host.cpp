@@ -17,6 +17,7 @@
 
 #include "nfe_batch.h"
 #include "nfe_internal.h"
+#include "nfe_spectrum.h"
 #include "nfe_tables.h"
 
 using namespace nfe;
@@ -92,6 +93,7 @@ struct nfe_sim {
     const void *coef = nullptr;       // points at cd or cfl
     void *q4dev = nullptr;
     void *r3dev = nullptr;            // no-phi remainder table
+    Spectrum *spectrum = nullptr;     // domain-size diagnostic (cuFFT plan + scratch), on first use
     Buffers buf{};
     int uidx[NFE_MAX_N] = {0};        // internal slot -> user component
     cudaStream_t stream = nullptr;
@@ -159,6 +161,8 @@ nfe_status free_all(nfe_sim *s) {
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
     s->r3dev = nullptr;
+    spectrum_destroy(s->spectrum);
+    s->spectrum = nullptr;
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
     s->stream = nullptr;
     return NFE_OK;
@@ -491,6 +495,22 @@ nfe_status nfe_populations(nfe_sim *s, double *f) {
     CK(cudaMemcpyAsync(f, s->buf.fields, size_t(s->ops->Q - 1) * s->geom.n * sizeof(double),
                        cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_domain_size(nfe_sim *s, double *L, int component, int nbins, double *Sk) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    if (!L) return fail(NFE_EINVAL, "L is NULL");
+    if (nbins < 0 || nbins > (1 << 20)) return fail(NFE_EINVAL, "nbins must be 0..2^20");
+    if (nbins > 0 && (!Sk || component < 0 || component >= s->N))
+        return fail(NFE_EINVAL, "S(k) wanted: Sk must be non-NULL and component in 0..N-1");
+    if ((st = ensure_fields(s)) != NFE_OK) return st;
+    CK(s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream));      // C of all components, FP64
+    std::string err;
+    if (!s->spectrum && (st = spectrum_create(s->geom, s->N, &s->spectrum, err)) != NFE_OK) return fail(st, "%s", err.c_str());
+    if ((st = domain_size(s->spectrum, s->N, s->buf.fields, component, nbins, L, Sk, s->stream, err)) != NFE_OK)
+        return fail(st, "%s", err.c_str());
     return NFE_OK;
 }
 

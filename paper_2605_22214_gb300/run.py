@@ -25,7 +25,7 @@ def make(name, size):
     if name == "spinodal":
         return W.spinodal_2d(nx=size, ny=size)
     if name == "janus3d":
-        return W.janus_3d(n=size, radius=32.0 * size / 256.0)
+        return W.janus_3d(n=size)
     if name == "lens":
         return W.lens_2d(nx=size, ny=size, radius=12.0 * size / 64.0)
     if name == "poiseuille3d":

@@ -156,3 +156,64 @@ def test_janus_c4_precision_study_small(precision):
     n = C.shape[1] * C.shape[2] * C.shape[3]
     drift = np.abs(d["momentum"]).max() / n
     assert drift < {"fp32": 1e-9, "f16": 1e-6, "bf16": 1e-5}[precision], drift
+
+
+def _shell_average(C_comp, nbins):
+    # circularly averaged |lambda(k)|^2 in shells |k| ~ b dk, dk = 2 pi / min(n): the same
+    # binning as the library's nfe_domain_size, written out in numpy
+    lam = (C_comp >= 0.5).astype(np.float64)
+    shape = lam.shape
+    ks = np.meshgrid(*[2.0 * np.pi * np.fft.fftfreq(n) for n in shape], indexing="ij")
+    kabs = np.sqrt(sum(k * k for k in ks))
+    S = np.abs(np.fft.fftn(lam)) ** 2
+    nmin = min(n for n in shape if n > 1)
+    b = np.floor(kabs / (2 * np.pi / nmin) + 0.5).astype(int)
+    out = np.zeros(nbins)
+    for i in range(1, nbins + 1):
+        sel = b == i
+        out[i - 1] = S[sel].mean() if sel.any() else 0.0
+    return out
+
+
+@pytest.mark.parametrize("case", ["binary2d", "janus3d"])
+def test_domain_size_matches_oracle(case):
+    # L_i of every component, their mean and the shell-averaged S(k) from the GPU (cuFFT)
+    # against the oracle's numpy FFT, on the GPU's own FP64 fields
+    if case == "binary2d":
+        p = W.phase_separation_2d(nx=96, ny=80, N=2, seed=11)
+        steps = 300
+    else:
+        p = W.janus_3d(n=32, radius=5.0)
+        steps = 30
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        s.step(steps)
+        C, _, _ = s.fields()
+        L, mean, Sk = s.domain_size(component=1, nbins=12)
+    Lo, mo = observables.domain_size(C)
+    assert np.all(np.isfinite(Lo))
+    np.testing.assert_allclose(L, Lo, rtol=1e-10)
+    assert abs(mean - mo) <= 1e-10 * mo
+    np.testing.assert_allclose(Sk, _shell_average(C[1], 12), rtol=1e-9, atol=1e-9 * np.abs(Sk).max())
+
+
+def test_binary_phase_separation_coarsens():
+    # Sec. IV: a symmetric binary mixture (the paper's start, C_i ~ U(0, 2/N) renormalised,
+    # sigma = 0.005, eta = 1/6) separates and its domains coarsen; with hydrodynamics the paper
+    # expects L ~ t^(2/3) at late times.  The fitted late-time exponent is printed and bounded
+    # loosely (a 256^2 box over 16000 steps is far from the paper's 1600^2 runs).
+    p = W.phase_separation_2d(nx=256, ny=256, N=2, seed=1013)
+    ts, Ls = [], []
+    with nfe.Sim(p, "fp32") as s:
+        s.set_fields(p["C0"])
+        t = 0
+        for target in (1000, 2000, 4000, 8000, 12000, 16000):
+            s.step(target - t)
+            t = target
+            ts.append(t)
+            Ls.append(s.domain_size()[1])
+    ts, Ls = np.array(ts, dtype=float), np.array(Ls)
+    a = np.polyfit(np.log(ts[2:]), np.log(Ls[2:]), 1)[0]
+    print(f"binary phase separation 256^2: L = {np.round(Ls, 2)}, late exponent {a:.3f}")
+    assert np.all(np.diff(Ls) > 0)
+    assert 0.25 < a < 1.0
