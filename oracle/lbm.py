@@ -118,10 +118,18 @@ def _outside_plus(prm, k):
 
 
 def neighbour(prm, psi, k):
-    """psi(x + e_k); periodic wrap, and psi(x) where x + e_k is inside a wall (Sec. III C)."""
+    """psi(x + e_k); periodic wrap, and psi(x) where x + e_k is inside a wall (Sec. III C).
+
+    A run with solid nodes (`prm.solid`, boolean field, or absent) applies the same rule
+    where x + e_k is a solid node."""
     e = prm.lat.e[k]
-    shifted = np.roll(psi, shift=(-int(e[2]), -int(e[1]), -int(e[0])), axis=(-3, -2, -1))
-    return np.where(_outside_plus(prm, k), psi, shifted)
+    shift = (-int(e[2]), -int(e[1]), -int(e[0]))
+    shifted = np.roll(psi, shift=shift, axis=(-3, -2, -1))
+    blocked = _outside_plus(prm, k)
+    solid = getattr(prm, "solid", None)
+    if solid is not None:
+        blocked = blocked | np.roll(solid, shift=shift, axis=(-3, -2, -1))
+    return np.where(blocked, psi, shifted)
 
 
 def grad(prm, psi):
