@@ -289,11 +289,16 @@ def run_nfe(args):
                  ("spinodal 4096x4096 N=4, tau_g = 1.3 (stored g)", dict(W.spinodal_2d(nx=4096, ny=4096, seed=1012), tau_g=1.3),
                   "fp32", 30, False),
                  ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "fp32", 20, False),
-                 ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "bf16", 20, False)]
+                 ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "bf16", 20, False),
+                 ("emulsion generator 600x140 D2Q9 N=4 (solid walls, 6 inlets, convective outflow)",
+                  W.emulsion_2d(), "fp32", args.steps // 4, True)]
         for name, q, prec, K, fl in cases:
             nq = q["nx"] * q["ny"] * q["nz"]
             with nfe.Sim(q, prec, stream=stream.cuda_stream, scale_exp=10) as sx:
                 sx.set_fields(q["C0"])
+                if "geometry" in q:
+                    geo = q["geometry"]
+                    sx.set_geometry(geo["node"], geo["inlets"], geo["outflow"])
                 if fl:
                     ms_total, _ = timed_steps(sx, K, 5)
                     ms = ms_total / K

@@ -16,7 +16,9 @@
  *     Cahn-Hilliard lattice Boltzmann update of the N-1 evolved volume
  *     fractions (Sec. III B, Eqs. 39-43) with tau_g = 1,
  *   - halfway bounce-back and the wall-gradient rule on walls, periodic
- *     wrap on every other edge (Sec. III C, Eqs. 44-45).
+ *     wrap on every other edge (Sec. III C, Eqs. 44-45);
+ *   - on D2Q9, solid nodes anywhere in the grid, velocity and volume-fraction
+ *     inlets and the convective outflow (Sec. III C; nfe_set_geometry).
  *
  * Conventions shared by every call:
  *   - Site index s = x + nx * (y + ny * z), x fastest.  Field arrays are
@@ -136,7 +138,7 @@ typedef struct {
     int kernels_per_step;            /* kernel launches of one nfe_step(1) */
     int variant;                     /* tile shape in use (-1: not tuned yet) */
     int nvariants;                   /* tile shapes available for this lattice/N/precision */
-    double min_bytes_per_site;       /* f (Q-1) and C (N-1) read once and written once */
+    double min_bytes_per_site;       /* f (Q-1) and C (N-1) read once and written once (+ stored g, + the node class byte of a geometry) */
     size_t state_bytes;              /* size of the raw state (nfe_get_state) */
     size_t device_bytes;             /* device memory held by the simulation */
 } nfe_info;
@@ -194,9 +196,38 @@ nfe_status nfe_diagnostics(nfe_sim *sim, nfe_diag *out);
  * NULL Sk or a component outside 0..N-1.  Synchronises. */
 nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, double *Sk);
 
+/* Open and complex boundaries of the D2Q9 step (Sec. III C, the conditions that the
+ * emulsion and patterned-surface applications of Sec. V use).
+ * node: host, n bytes, one class per site (x fastest): 0 fluid, 1 solid, 2 + j inlet j;
+ *   NULL removes the geometry (ninlets, inlets and outflow are then ignored).
+ * inlets: host, ninlets x (2 + N) doubles, row j = v_b (x, y) then C_b of all N
+ *   components in the user's order (finite, >= 0, summing to 1 within 1e-9);
+ *   0 <= ninlets <= 64, NULL when ninlets = 0.
+ * outflow: nonzero = convective outflow on the x = nx - 1 edge; then column 0 must
+ *   hold no fluid node, column nx - 1 no inlet node, nx >= 3 and the x axis no wall.
+ * Rules: a solid node takes halfway bounce-back for f and for the component
+ *   populations, and a neighbour inside it takes the value at x in every directional
+ *   difference; links from inlet j carry f_k(x, t+1) = f*_kbar(x) + 2 w_k (e_k . v_b) /
+ *   c_s^2 (e_k the entering direction, rho_b = 1) and the component equilibrium
+ *   g^eq_k(C_b, v_b, S_b) of the prescribed state (S_b: Eq. 12 at the uniform C_b), and
+ *   directional differences see C_b there; the outflow replaces every population and
+ *   volume fraction of a fluid node in column nx - 1 by (old + U new(x - 1)) / (1 + U),
+ *   U the mean x-momentum of the fluid nodes of column nx - 2 after streaming, and keeps a
+ *   ghost column of volume fractions (convected the same way, started from column nx - 1)
+ *   for the directional differences of column nx - 1.  Non-fluid nodes keep their
+ *   populations and volume fractions; C := C_b on the inlet nodes now and at every
+ *   nfe_set_fields.  nfe_fields reports v = P = 0 on solid nodes and v = v_b, P = 0 on
+ *   inlet nodes.  With outflow the raw state (nfe_get_state) also holds the ghost column,
+ *   so set the geometry before restoring a state.
+ * Errors: NFE_EUNSUPPORTED for D3Q19, tau_g != 1 or NFE_NO_PHI; NFE_EINVAL for a class
+ *   outside 0 .. 1 + ninlets, a bad inlet row or a violated outflow condition; NFE_ENOMEM.
+ * Synchronises the stream. */
+nfe_status nfe_set_geometry(nfe_sim *sim, const uint8_t *node, int ninlets, const double *inlets, int outflow);
+
 /* Raw state (checkpoint / resume, host buffer of info.state_bytes bytes):
  * populations and evolved volume fractions in device format, plus the step
- * counter.  get then set restores the simulation bit for bit. */
+ * counter (and, with an outflow, the ghost column).  get then set restores the
+ * simulation bit for bit. */
 nfe_status nfe_get_state(nfe_sim *sim, void *host_buf, size_t bytes);
 nfe_status nfe_set_state(nfe_sim *sim, const void *host_buf, size_t bytes);
 

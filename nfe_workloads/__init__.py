@@ -29,7 +29,11 @@ __all__ = [
     "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
     "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
     "batch_sweep", "random_sigma", "random_simplex_points", "phase_separation_2d", "CONFIGS",
+    "open_channel_2d", "emulsion_2d", "FLUID", "SOLID", "INLET0",
 ]
+
+# node classes of a geometry (one byte per site)
+FLUID, SOLID, INLET0 = 0, 1, 2
 
 
 def tanh_step(d):
@@ -263,6 +267,90 @@ def planar_2d(nx=4, ny=64, sigma=0.005, tau=1.0, m=1.0 / 50.0, offset=0.0, width
     sig = np.array([[0.0, sigma], [sigma, 0.0]])
     p = base_params(D2Q9, nx, ny, 1, 2, sig, tau, m=m, name=f"planar_{nx}x{ny}")
     p["C0"] = C
+    return p
+
+
+def open_channel_2d(nx=70, ny=36, N=3, seed=1021, tau=0.8, m=1.0 / 50.0, outflow=True):
+    """Small open channel with every boundary kind: solid rows at y = 0 and y = ny - 1, a solid
+    post in the middle, two inlets on the left edge (column 0, the rest of it solid) with
+    different compositions and velocities, one inlet in the top wall, and (optionally) the
+    convective outflow on the right edge.  The interior starts as a seeded smooth mixture."""
+    rng = np.random.default_rng(seed)
+    sig = random_sigma(rng, N)
+    node = np.zeros((1, ny, nx), dtype=np.uint8)
+    node[:, 0, :] = SOLID
+    node[:, -1, :] = SOLID
+    node[:, :, 0] = SOLID
+    if not outflow:
+        node[:, :, -1] = SOLID
+    h = (ny - 2) // 2
+    node[:, 1:1 + h, 0] = INLET0                 # inlet 0: lower half of the left edge
+    node[:, 1 + h:ny - 1, 0] = INLET0 + 1        # inlet 1: upper half
+    a0 = nx // 3
+    node[:, -1, a0:a0 + 6] = INLET0 + 2          # inlet 2: in the top wall, flowing down
+    px, py = nx // 2, ny // 2
+    node[:, py - 3:py + 2, px - 2:px + 1] = SOLID
+    pts = random_simplex_points(rng, N, 3)
+    inlets = np.zeros((3, 2 + N))
+    inlets[0, :2], inlets[1, :2], inlets[2, :2] = (0.01, 0.0), (0.006, 0.002), (0.0, -0.008)
+    inlets[:, 2:] = pts
+    x, y, z = _coords(nx, ny, 1)
+    C = np.empty((N, 1, ny, nx))
+    for i in range(N):
+        kx, ky, ph = rng.uniform(1, 3), rng.uniform(1, 3), rng.uniform(0, 2 * np.pi)
+        C[i] = 1.0 + 0.6 * np.sin(2 * np.pi * kx * x / nx + ph) * np.cos(2 * np.pi * ky * y / ny)
+    C /= C.sum(axis=0, keepdims=True)
+    p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, omega_stab=1.0 / 90.0, name=f"open_channel_{nx}x{ny}_N{N}")
+    p["C0"] = C
+    p["geometry"] = dict(node=node, inlets=inlets, outflow=bool(outflow))
+    return p
+
+
+def emulsion_2d(nx=600, ny=140, m=1.0 / 50.0):
+    """The emulsion generator of Sec. V (Fig. of the microfluidic design), N = 4, built from the
+    dimensions the paper lists; the figure itself is not reproduced, so the placement below is a
+    reading of it.  Fluids 1..4 are components 0..3.
+      - inlets of fluids 3 and 4 on the left edge: channels of width 10 and length 30 whose
+        inner edges lie 55 sites from the bottom and top edges, velocity 0.003;
+      - a channel of height 80 (centred) and length 30 after them, with inlets of fluid 2 of
+        width 8 in its bottom and top walls right at its start, velocity 0.0045;
+      - inlets of fluid 1 of width 51 in the bottom and top walls of the channel of height 110
+        (centred) that follows, velocity 0.0098; it runs to the convective outflow at x = nx - 1.
+    sigma_13 = sigma_14 = 0.012, the others 0.005, Omega = 1/18, eta_i = 1/12 (tau = 0.75).
+    The fluid region starts as fluid 1, the two left channels as fluids 3 and 4."""
+    N = 4
+    sig = np.full((N, N), 0.005)
+    np.fill_diagonal(sig, 0.0)
+    sig[0, 2] = sig[2, 0] = sig[0, 3] = sig[3, 0] = 0.012
+    node = np.full((1, ny, nx), SOLID, dtype=np.uint8)
+    L1, w1, H2, H3, L2, w2, w3, H4 = 30, 10, 55, 80, 30, 8, 51, 110
+    lo3 = (H2, H2 + w1)                           # fluid-3 channel rows
+    lo4 = (ny - H2 - w1, ny - H2)                 # fluid-4 channel rows
+    node[:, lo3[0]:lo3[1], 1:L1] = FLUID
+    node[:, lo4[0]:lo4[1], 1:L1] = FLUID
+    node[:, lo3[0]:lo3[1], 0] = INLET0            # inlet 0: fluid 3
+    node[:, lo4[0]:lo4[1], 0] = INLET0 + 1        # inlet 1: fluid 4
+    y3 = ((ny - H3) // 2, (ny + H3) // 2)
+    node[:, y3[0]:y3[1], L1:L1 + L2] = FLUID
+    node[:, y3[0] - 1, L1:L1 + w2] = INLET0 + 2   # inlet 2: fluid 2 from below
+    node[:, y3[1], L1:L1 + w2] = INLET0 + 3       # inlet 3: fluid 2 from above
+    y4 = ((ny - H4) // 2, (ny + H4) // 2)
+    x4 = L1 + L2
+    node[:, y4[0]:y4[1], x4:] = FLUID
+    node[:, y4[0] - 1, x4:x4 + w3] = INLET0 + 4   # inlet 4: fluid 1 from below
+    node[:, y4[1], x4:x4 + w3] = INLET0 + 5       # inlet 5: fluid 1 from above
+    pure = np.eye(N)
+    inlets = np.array([[0.003, 0.0, *pure[2]], [0.003, 0.0, *pure[3]],
+                       [0.0, 0.0045, *pure[1]], [0.0, -0.0045, *pure[1]],
+                       [0.0, 0.0098, *pure[0]], [0.0, -0.0098, *pure[0]]])
+    C = np.zeros((N, 1, ny, nx))
+    C[0] = 1.0
+    for rows, comp in ((lo3, 2), (lo4, 3)):
+        C[:, :, rows[0]:rows[1], :L1] = 0.0
+        C[comp, :, rows[0]:rows[1], :L1] = 1.0
+    p = base_params(D2Q9, nx, ny, 1, N, sig, 0.75, m=m, omega_stab=1.0 / 18.0, name=f"emulsion_{nx}x{ny}")
+    p["C0"] = C
+    p["geometry"] = dict(node=node, inlets=inlets, outflow=True)
     return p
 
 

@@ -90,26 +90,26 @@ def _with_inlet_values(prm, geo, C):
     return C
 
 
-def init_state(prm, geo, C0, v0=None):
+def init_state(prm, geo, C0, v0=None, flux_form="literal"):
     """f = f^eq(P = 0, v0), g = g^eq(C0, v0, S(C0)) (lbm.init_state) with C0 := C_b on the
     inlet nodes; the ghost column starts as column nx - 1."""
     C0 = np.asarray(C0, dtype=np.float64).reshape((prm.N,) + prm.shape)
     C0 = _with_inlet_values(prm, geo, C0)
     sp = copy.copy(prm)
     sp.solid = geo.node == SOLID
-    st = lbm.init_state(sp, C0, v0)
+    st = lbm.init_state(sp, C0, v0, flux_form=flux_form)
     ghost = C0[prm.evolved][..., -1].copy() if geo.outflow else None
     return OpenState(st.f, st.g, 0, ghost)
 
 
-def _macroscopic(prm, geo, C, f):
+def _macroscopic(prm, geo, C, f, flux_form):
     """lbm.macroscopic with the solid rule."""
     ext = copy.copy(prm)
     ext.solid = geo.node == SOLID
-    return lbm.macroscopic(ext, C, f)
+    return lbm.macroscopic(ext, C, f, flux_form)
 
 
-def _macroscopic_out(prm, geo, C, f, ghost):
+def _macroscopic_out(prm, geo, C, f, ghost, flux_form):
     """lbm.macroscopic with the solid rule on the grid extended by the ghost column."""
     N = prm.N
     gh = np.empty((N,) + prm.shape[:-1] + (1,))
@@ -125,13 +125,14 @@ def _macroscopic_out(prm, geo, C, f, ghost):
     ext.nx = prm.nx + 1
     ext.shape = prm.shape[:-1] + (prm.nx + 1,)
     ext.solid = np.concatenate([solid, solid[..., -1:]], axis=-1)
-    mac = lbm.macroscopic(ext, Cx, fx)
+    mac = lbm.macroscopic(ext, Cx, fx, flux_form)
     return {k: (v[..., :prm.nx] if isinstance(v, np.ndarray) else v) for k, v in mac.items()}
 
 
-def macroscopic(prm, geo, C, f, ghost=None):
+def macroscopic(prm, geo, C, f, ghost=None, flux_form="literal"):
     """Fields of every fluid node, with the inlet nodes' v and S set to (v_b, S_b)."""
-    mac = _macroscopic_out(prm, geo, C, f, ghost) if geo.outflow else _macroscopic(prm, geo, C, f)
+    mac = (_macroscopic_out(prm, geo, C, f, ghost, flux_form) if geo.outflow
+           else _macroscopic(prm, geo, C, f, flux_form))
     for j, (vb, _, Sb) in enumerate(geo.inlets):
         sel = geo.node == INLET0 + j
         mac["v"][:, sel] = vb[:, None]
@@ -163,11 +164,11 @@ def _stream(prm, geo, post, old, velocity_rule):
     return np.where(geo.fluid, new, old)
 
 
-def step(prm, geo, st):
+def step(prm, geo, st, flux_form="literal"):
     """One time step (lbm.step with the boundaries above).  Returns the new OpenState."""
     lat = prm.lat
     C = _with_inlet_values(prm, geo, lbm.components(prm, st.g))
-    mac = macroscopic(prm, geo, C, st.f, st.ghost)
+    mac = macroscopic(prm, geo, C, st.f, st.ghost, flux_form)
     fpost = lbm.collide_f(lat, st.f, mac["P"], mac["v"], mac["F"], mac["omega_p"], mac["omega_m"])
     gpost = np.empty_like(st.g)
     for a, c in enumerate(prm.evolved):
@@ -193,17 +194,17 @@ def step(prm, geo, st):
     return OpenState(f_new, g_new, st.t + 1, ghost)
 
 
-def run(prm, geo, st, nsteps):
+def run(prm, geo, st, nsteps, flux_form="literal"):
     for _ in range(nsteps):
-        st = step(prm, geo, st)
+        st = step(prm, geo, st, flux_form)
     return st
 
 
-def fields(prm, geo, st):
+def fields(prm, geo, st, flux_form="literal"):
     """(C, v, P, F_s): fluid nodes as lbm.fields; solid nodes v = P = F_s = 0; inlet nodes
     C = C_b, v = v_b, P = F_s = 0."""
     C = _with_inlet_values(prm, geo, lbm.components(prm, st.g))
-    mac = macroscopic(prm, geo, C, st.f, st.ghost)
+    mac = macroscopic(prm, geo, C, st.f, st.ghost, flux_form)
     v, P, Fs = mac["v"].copy(), mac["P"].copy(), mac["Fs"].copy()
     nonfluid = ~geo.fluid
     v[:, nonfluid] = 0.0

@@ -33,7 +33,7 @@ STATUS = {0: "NFE_OK", 1: "NFE_EINVAL", 2: "NFE_ENOMEM", 3: "NFE_ECUDA", 4: "NFE
 EXPORTS = ["nfe_create", "nfe_set_fields", "nfe_step", "nfe_sync", "nfe_fields", "nfe_populations",
            "nfe_diagnostics", "nfe_domain_size", "nfe_get_state", "nfe_set_state", "nfe_get_info", "nfe_profile_enable",
            "nfe_profile_read", "nfe_destroy", "nfe_status_string", "nfe_last_error",
-           "nfe_bulk_potential_host", "nfe_set_variant", "nfe_field_stats_static",
+           "nfe_bulk_potential_host", "nfe_set_variant", "nfe_field_stats_static", "nfe_set_geometry",
            "nfe_batch_create", "nfe_batch_set_fields", "nfe_batch_step", "nfe_batch_set_mode",
            "nfe_batch_sync", "nfe_batch_fields", "nfe_batch_diagnostics", "nfe_batch_get_info",
            "nfe_batch_set_barrier_test", "nfe_batch_destroy"]
@@ -107,6 +107,7 @@ def load():
         "nfe_get_info": ([P, C.POINTER(nfe_info)], C.c_int),
         "nfe_profile_enable": ([P, C.c_int], C.c_int),
         "nfe_set_variant": ([P, C.c_int], C.c_int),
+        "nfe_set_geometry": ([P, C.c_void_p, C.c_int, dp, C.c_int], C.c_int),
         "nfe_field_stats_static": ([C.c_int, C.c_int64, P, P, P], C.c_int),
         "nfe_batch_create": ([C.c_int, C.POINTER(nfe_grid), C.POINTER(C.c_int), C.POINTER(nfe_params),
                               C.POINTER(P)], C.c_int),
@@ -224,6 +225,19 @@ def nfe_domain_size(h, N, component=0, nbins=0):
     Sk = np.zeros(max(nbins, 1))
     _check(load().nfe_domain_size(h, _dptr(L), int(component), int(nbins), _dptr(Sk) if nbins > 0 else None))
     return L[:N], L[N], (Sk[:nbins] if nbins > 0 else None)
+
+
+def nfe_set_geometry(h, node, inlets=None, outflow=False):
+    """Node classes (uint8 per site, x fastest; None removes the geometry), inlet rows
+    (vx, vy, C_1..C_N) and the convective outflow on the x = nx - 1 edge."""
+    if node is None:
+        _check(load().nfe_set_geometry(h, None, 0, None, 0))
+        return
+    node = np.ascontiguousarray(node, dtype=np.uint8).ravel()
+    tab = np.ascontiguousarray(np.zeros((0, 1)) if inlets is None else inlets, dtype=np.float64)
+    k = tab.shape[0] if tab.size else 0
+    _check(load().nfe_set_geometry(h, node.ctypes.data_as(C.c_void_p), k, _dptr(tab.ravel()) if k else None,
+                                   1 if outflow else 0))
 
 
 def nfe_get_info(h):
@@ -348,6 +362,9 @@ class Sim:
 
     def set_variant(self, variant):
         nfe_set_variant(self.h, variant)
+
+    def set_geometry(self, node, inlets=None, outflow=False):
+        nfe_set_geometry(self.h, node, inlets, outflow)
 
     def profile_enable(self, on=True):
         nfe_profile_enable(self.h, on)

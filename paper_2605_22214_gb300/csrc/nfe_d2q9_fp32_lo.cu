@@ -1,0 +1,9 @@
+// D2Q9 time-step kernels, N = 2 .. 4, fp32 storage/arithmetic variant (the fused
+// single-kernel step: three tile shapes, the stored-g and geometry forms), and the dispatch
+// over N.
+#include "nfe_fused2d.cuh"
+
+namespace nfe {
+const Ops *ops_d2q9_fp32_hi(int N);
+const Ops *ops_d2q9_fp32(int N) { return N <= 4 ? ops_fused2d_lo<float, float>(N, NFE_FP32) : ops_d2q9_fp32_hi(N); }
+}  // namespace nfe

@@ -75,7 +75,17 @@ struct Fused2DShape {
     static constexpr int A_VALUES = RA::NVP * ACOUNT;
     static constexpr int B_VALUES = RB::NVP * BCOUNT;
     static constexpr size_t BYTES = sizeof(T) * size_t(A_VALUES + B_VALUES);
+    static constexpr size_t GEO_BYTES = BYTES + ((ACOUNT + 15) / 16) * 16;   // + node class of tile + 2-ring
     static constexpr int NHALO = BCOUNT - TX * TY;
+};
+
+// What the geometry form of the step reads besides the state (all null / 0 without one).
+template <typename T>
+struct GeoView {
+    const unsigned char *node;    // node class per site
+    const T *inl;                 // inlet table, 2N values per inlet: vx, vy, C_b (N-1), S_b (N-1)
+    const T *ghost;               // outflow ghost column of buffer cur, (N-1) x ny
+    int outflow;
 };
 
 __device__ __forceinline__ int wrap(int v, int n) {
@@ -203,18 +213,22 @@ __device__ __forceinline__ T fload(const SF *p, double w, T finv) {
 }
 
 // TAUG: the stored-g path (tau_g != 1), with the component populations in gin / gout.
-template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4, bool TAUG = false>
+// GEO: node classes (solid nodes, inlets, outflow ghost column) from `geo`; see the boundary
+// rules at the phases below.
+template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4, bool TAUG = false, bool GEO = false>
 __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, const SF *__restrict__ fin,
                                              SF *__restrict__ fout, const T *__restrict__ Cin,
                                              T *__restrict__ Cout, int *__restrict__ flag,
                                              int x0, int y0, unsigned char *smem,
-                                             const T *__restrict__ gin = nullptr, T *__restrict__ gout = nullptr) {
+                                             const T *__restrict__ gin = nullptr, T *__restrict__ gout = nullptr,
+                                             GeoView<T> geo = {}) {
     using Sh = Fused2DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     using RB = typename Sh::RB;
     static_assert(Sh::NHALO <= TX * TY, "one ring site per thread at most");
     T *sA = reinterpret_cast<T *>(smem);
     T *sB = sA + Sh::A_VALUES;
+    unsigned char *sN = reinterpret_cast<unsigned char *>(sB + Sh::B_VALUES);   // GEO only
     const int nx = g.nx, ny = g.ny;
     const int n = int(g.n);
     const int tid = threadIdx.x;
@@ -249,7 +263,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         if ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))) ring_ok = false;
         hs = pwrap(hx, nx, tiny) + nx * pwrap(hy, ny, tiny);
     }
-    if (wallt && has_ring) {
+    if (!GEO && wallt && has_ring) {
         sfor<1, 9, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int xx = hx + LD2Q9::ex(k), yy = hy + LD2Q9::ey(k);
@@ -272,7 +286,8 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const int i = tid + it * NT;
         if (i < Sh::ACOUNT) {
             const int ly = i / Sh::AX, lx = i - ly * Sh::AX;
-            int gx = x0 + lx - 2, gy = y0 + ly - 2;
+            const int gxu = x0 + lx - 2, gyu = y0 + ly - 2;
+            int gx = gxu, gy = gyu;
             if (edge) {
                 // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
                 // such entries are never used by a real site's stencil
@@ -280,8 +295,26 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
                 gy = g.wy ? min(max(gy, 0), ny - 1) : pwrap(gy, ny, tiny);
             }
             const int s = gx + nx * gy;
+            if constexpr (GEO) {
+                // beyond the outflow edge: the ghost column (its class that of column nx - 1,
+                // ghost where that is not solid); beyond an edge wall: solid
+                const bool gcol = geo.outflow && gxu >= nx;
+                if (gcol) {
 #pragma unroll
-            for (int a = 0; a < N - 1; ++a) cl[it][a] = ldin<L2ONLY>(Cin + a * n + s);
+                    for (int a = 0; a < N - 1; ++a) cl[it][a] = geo.ghost[a * ny + gy];
+                } else {
+#pragma unroll
+                    for (int a = 0; a < N - 1; ++a) cl[it][a] = ldin<L2ONLY>(Cin + a * n + s);
+                }
+                unsigned char cls;
+                if ((g.wx && (gxu < 0 || gxu >= nx)) || (g.wy && (gyu < 0 || gyu >= ny))) cls = kNodeSolid;
+                else if (gcol) cls = geo.node[(nx - 1) + nx * gy] == kNodeSolid ? kNodeSolid : kNodeGhost;
+                else cls = geo.node[s];
+                sN[i] = cls;
+            } else {
+#pragma unroll
+                for (int a = 0; a < N - 1; ++a) cl[it][a] = ldin<L2ONLY>(Cin + a * n + s);
+            }
         }
     }
 #pragma unroll
@@ -304,8 +337,20 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
 
     // ---- phase 2a: own site ---------------------------------------------------
     // wall mask of the own site: bit k set when x + e_k is beyond a wall
-    unsigned wall0 = 0;
-    if (wallt) {
+    // GEO: wall0 = solid neighbours (mirror rule, bounce-back), open0 = every non-fluid
+    // neighbour (inlet, solid, ghost: no plain push there), cls0 = the site's own class
+    unsigned wall0 = 0, open0 = 0;
+    unsigned char cls0 = kNodeFluid;
+    if constexpr (GEO) {
+        const int ia = (ty + 2) * Sh::AX + (tx + 2);
+        cls0 = sN[ia];
+        sfor<1, 9, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
+            const unsigned char cl = sN[ia + LD2Q9::ex(k) + Sh::AX * LD2Q9::ey(k)];
+            if (cl == kNodeSolid) wall0 |= 1u << k;
+            if (cl != kNodeFluid) open0 |= 1u << k;
+        });
+    } else if (wallt) {
         sfor<1, 9, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int xx = gx0 + LD2Q9::ex(k), yy = gy0 + LD2Q9::ey(k);
@@ -316,9 +361,18 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     T S[N - 1], Fx, Fy, vx, vy, P, sumf;
     {
         const int ia = (ty + 2) * Sh::AX + (tx + 2);
-        if (wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
-        else       stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
+        if (GEO ? wall0 != 0u : wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
+        else                           stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
         site_physics<N, T, Q4>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
+        if constexpr (GEO) {
+            // an inlet node's record is its prescribed state (C_b is its stored C)
+            if (cls0 >= kNodeInlet0 && cls0 != kNodeGhost) {
+                const T *row = geo.inl + (cls0 - kNodeInlet0) * (2 * N);
+                vx = row[0]; vy = row[1];
+#pragma unroll
+                for (int a = 0; a < N - 1; ++a) S[a] = row[N + 1 + a];
+            }
+        }
         T rec[RB::NVP];
 #pragma unroll
         for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 1 + a] = S[a]; }
@@ -333,10 +387,26 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     if (ring_ok) {
         T hc[N], hl[N], hgx[N], hgy[N], hEx, hEy;
         const int ia = (by + 1) * Sh::AX + (bx + 1);
-        if (wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
-        else       stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
+        unsigned char hcls = kNodeFluid;
+        if constexpr (GEO) {
+            hcls = sN[ia];
+            sfor<1, 9, 1>([&](auto kc_) {
+                constexpr int k = decltype(kc_)::value;
+                if (sN[ia + LD2Q9::ex(k) + Sh::AX * LD2Q9::ey(k)] == kNodeSolid) hwall |= 1u << k;
+            });
+        }
+        if (GEO ? hwall != 0u : wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
+        else                           stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
         T hS[N - 1], hFx, hFy, hvx, hvy, hP, hsum;
         site_physics<N, T, Q4>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
+        if constexpr (GEO) {
+            if (hcls >= kNodeInlet0 && hcls != kNodeGhost) {
+                const T *row = geo.inl + (hcls - kNodeInlet0) * (2 * N);
+                hvx = row[0]; hvy = row[1];
+#pragma unroll
+                for (int a = 0; a < N - 1; ++a) hS[a] = row[N + 1 + a];
+            }
+        }
         T rec[RB::NVP];
 #pragma unroll
         for (int a = 0; a < N - 1; ++a) { rec[a] = hc[a]; rec[N + 1 + a] = hS[a]; }
@@ -347,7 +417,12 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     }
 
     // ---- phase 3: collide and push-stream the own site ----------------------
-    if (own) {
+    // GEO: a non-fluid node keeps its populations (copied bit for bit to the new buffer)
+    if (GEO && own && cls0 != kNodeFluid) {
+#pragma unroll
+        for (int k = 1; k < 9; ++k) fout[(k - 1) * n + s0] = fin[(k - 1) * n + s0];
+    }
+    if (own && (!GEO || cls0 == kNodeFluid)) {
         T op, om;
         relaxation<N, T>(cf, c, op, om);
         const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
@@ -362,7 +437,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T hop = T(0.5) * op, hom = T(0.5) * om;
         const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
         // no wrap and no wall for any target: the site is inside the domain by one site
-        const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1;
+        const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && (!GEO || open0 == 0u);
         sfor<1, 9, 2>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int kb = k + 1;
@@ -384,6 +459,26 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
                 constexpr int dk0 = LD2Q9::ex(k);
                 const int dk = dk0 + nx * LD2Q9::ey(k);
                 FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), f[k], LD2Q9::w(k), cf.fscale);
+            });
+        } else if constexpr (GEO) {
+            const int ia = (ty + 2) * Sh::AX + (tx + 2);
+            sfor<1, 9, 1>([&](auto kc_) {
+                constexpr int k = decltype(kc_)::value;
+                constexpr int kb = opp(k);
+                const unsigned char cl = sN[ia + LD2Q9::ex(k) + Sh::AX * LD2Q9::ey(k)];
+                if (cl == kNodeFluid) {
+                    FStore<SF, T>::store(fout + (k - 1) * n + (wrap(sx + LD2Q9::ex(k), nx) + nx * wrap(sy + LD2Q9::ey(k), ny)),
+                                         f[k], LD2Q9::w(k), cf.fscale);
+                } else if (cl == kNodeSolid) {
+                    FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k], LD2Q9::w(kb), cf.fscale);
+                } else if (cl != kNodeGhost) {
+                    // inlet j (moving-wall bounce-back, rho_b = 1):
+                    // f_kbar(x, t+1) = post_k(x) - 2 w_k (e_k . v_b) / c_s^2
+                    const T *row = geo.inl + (cl - kNodeInlet0) * (2 * N);
+                    const T ev = T(LD2Q9::ex(k)) * row[0] + T(LD2Q9::ey(k)) * row[1];
+                    FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k] - T(6.0 * LD2Q9::w(k)) * ev, LD2Q9::w(kb), cf.fscale);
+                }
+                // into the ghost column: the population leaves the domain
             });
         } else {
             sfor<1, 9, 1>([&](auto kc_) {
@@ -471,7 +566,13 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     }
 
     // ---- phase 4: Cahn-Hilliard update of the own site ----------------------
-    if (own) {
+    // GEO: a non-fluid node keeps its volume fractions; links from an inlet node carry the
+    // equilibrium of its prescribed record, links from a solid node bounce back (wall0)
+    if (GEO && own && cls0 != kNodeFluid) {
+#pragma unroll
+        for (int e = 0; e < N - 1; ++e) Cout[e * n + s0] = Cin[e * n + s0];
+    }
+    if (own && (!GEO || cls0 == kNodeFluid)) {
         const T m = cf.m;
         const T w0 = T(4) / T(9);
         const int ib = (ty + 1) * Sh::BX + (tx + 1);
@@ -530,35 +631,40 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
 // that suits it.
 template <typename T, int NT> struct Fused2DOcc { static constexpr int value = sizeof(T) == 4 ? (NT <= 128 ? 8 : NT <= 256 ? 3 : 2) : 1; };
 
-template <int N, typename T, typename SF, int TX, int TY, int Q4, bool TAUG>
+template <int N, typename T, typename SF, int TX, int TY, int Q4, bool TAUG, bool GEO = false>
 __global__ void __launch_bounds__(TX * TY, (Fused2DOcc<T, TX * TY>::value))
 k_fused2d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
           const T *__restrict__ Cin, T *__restrict__ Cout, int *__restrict__ flag,
-          const T *__restrict__ gin, T *__restrict__ gout) {
+          const T *__restrict__ gin, T *__restrict__ gout, GeoView<T> geo) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    fused2d_tile<N, T, SF, TX, TY, false, Q4, TAUG>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX,
-                                                    blockIdx.y * TY, smem_raw, gin, gout);
+    fused2d_tile<N, T, SF, TX, TY, false, Q4, TAUG, GEO>(g, cf, fin, fout, Cin, Cout, flag, blockIdx.x * TX,
+                                                         blockIdx.y * TY, smem_raw, gin, gout, geo);
 }
 
-template <int N, typename T, typename SF, int TX, int TY, int Q4, bool TAUG = false>
+template <int N, typename T, typename SF, int TX, int TY, int Q4, bool TAUG = false, bool GEO = false>
 cudaError_t launch_fused2d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Fused2DShape<N, T, TX, TY>;
+    constexpr size_t bytes = GEO ? Sh::GEO_BYTES : Sh::BYTES;
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY, Q4, TAUG>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
+        cudaError_t e = cudaFuncSetAttribute(k_fused2d<N, T, SF, TX, TY, Q4, TAUG, GEO>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
         if (e != cudaSuccess) return e;
         attr_done = true;
     }
     const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY);
-    k_fused2d<N, T, SF, TX, TY, Q4, TAUG><<<grid, TX * TY, Sh::BYTES, st>>>(
+    GeoView<T> geo{};
+    if constexpr (GEO) geo = {b.node, static_cast<const T *>(b.inl), static_cast<const T *>(b.ghost[cur]), b.outflow};
+    k_fused2d<N, T, SF, TX, TY, Q4, TAUG, GEO><<<grid, TX * TY, bytes, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
         static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]), b.flag,
-        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]));
+        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]), geo);
     return cudaGetLastError();
 }
 
 }  // namespace nfe
+
+#include "nfe_geo2d.cuh"
 
 namespace nfe {
 
@@ -569,6 +675,12 @@ struct Fused2DLaunch {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         // stored g (tau_g != 1): one tile shape
         if (b.g[0]) return launch_fused2d<N, T, SF, 32, 8, Q4_GLOBAL, true>(g, cf, b, cur, st);
+        // open and complex boundaries: one tile shape, then the convective outflow
+        if (b.node) {
+            cudaError_t e = launch_fused2d<N, T, SF, 32, 8, Q4_GLOBAL, false, true>(g, cf, b, cur, st);
+            if (e == cudaSuccess && b.outflow) e = launch_outflow2d<N, T, SF>(g, cf, b, cur, st);
+            return e;
+        }
         if (cf.no_phi) return launch<Q4_NOPHI>(g, cf, b, cur, st, variant);
         return cf.has_q4 ? launch<Q4_GLOBAL>(g, cf, b, cur, st, variant) : launch<Q4_ABSENT>(g, cf, b, cur, st, variant);
     }
@@ -585,17 +697,26 @@ struct Fused2DLaunch {
         static const Ops o = {9, 2, N, prec, 1, {K_FUSED, K_FUSED}, {&step, nullptr}, 3,
                               {"fused 32x4", "fused 32x8", "fused 32x16", nullptr},
                               &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
-                              int(sizeof(SF)), int(sizeof(T))};
+                              int(sizeof(SF)), int(sizeof(T)),
+                              &GeoOps<N, T, SF>::inlet_table, &GeoOps<N, T, SF>::prepare, &GeoOps<N, T, SF>::moments};
         return &o;
     }
 };
 
+// N = 2 .. 4 and N = 5 .. 8 are instantiated in separate translation units (compiled in parallel).
 template <typename T, typename SF>
-const Ops *ops_fused2d(int N, int prec) {
+const Ops *ops_fused2d_lo(int N, int prec) {
     switch (N) {
         case 2: return Fused2DLaunch<2, T, SF>::ops(prec);
         case 3: return Fused2DLaunch<3, T, SF>::ops(prec);
         case 4: return Fused2DLaunch<4, T, SF>::ops(prec);
+        default: return nullptr;
+    }
+}
+
+template <typename T, typename SF>
+const Ops *ops_fused2d_hi(int N, int prec) {
+    switch (N) {
         case 5: return Fused2DLaunch<5, T, SF>::ops(prec);
         case 6: return Fused2DLaunch<6, T, SF>::ops(prec);
         case 7: return Fused2DLaunch<7, T, SF>::ops(prec);

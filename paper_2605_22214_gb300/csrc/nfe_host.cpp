@@ -101,6 +101,13 @@ struct nfe_sim {
     int64_t step = 0;
     size_t fplanes_bytes = 0, cplanes_bytes = 0, gplanes_bytes = 0;   // gplanes: stored g (tau_g != 1)
     double tau_g = 1.0;
+    bool no_phi = false;
+    // D2Q9 geometry (nfe_set_geometry): device node classes, inlet table and ghost column
+    unsigned char *node_dev = nullptr;
+    void *inl_dev = nullptr;
+    int ninlets = 0;
+    size_t ghost_bytes = 0;           // one ghost buffer ((N-1) x ny), 0 without an outflow
+    size_t geo_bytes = 0;             // device bytes held by the geometry
     size_t fields_planes = 0;
     size_t device_bytes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -156,11 +163,13 @@ nfe_status free_all(nfe_sim *s) {
     s->event_pool.clear();
     void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
                     s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev,
-                    s->buf.g[0], s->buf.g[1]};
+                    s->buf.g[0], s->buf.g[1], s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1]};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
     s->r3dev = nullptr;
+    s->node_dev = nullptr;
+    s->inl_dev = nullptr;
     spectrum_destroy(s->spectrum);
     s->spectrum = nullptr;
     if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
@@ -208,7 +217,8 @@ nfe_status launch_step(nfe_sim *s, int cur, bool timed, int variant) {
 // step reads buffer cur and writes buffer 1 - cur, so the state is untouched.
 nfe_status autotune(nfe_sim *s) {
     if (s->variant >= 0) return NFE_OK;
-    if (s->ops->nvariants <= 1) { s->variant = 0; return NFE_OK; }
+    // the geometry form has one tile shape whatever the variant
+    if (s->ops->nvariants <= 1 || s->buf.node) { s->variant = 0; return NFE_OK; }
     cudaEvent_t a = get_event(s), b = get_event(s);
     double best = 1e300;
     int best_v = 0;
@@ -257,6 +267,32 @@ nfe_status ensure_fields(nfe_sim *s) {
                    size_t(kReduceBlocks) * diag_count(s->N) * sizeof(double));
     if (st != NFE_OK) return st;
     return dev_alloc(s, reinterpret_cast<void **>(&s->buf.diag), diag_count(s->N) * sizeof(double));
+}
+
+// fields of the current state (FP64 planes in bufs.fields), with the node classes when the
+// grid has a geometry
+cudaError_t run_moments(nfe_sim *s) {
+    if (s->buf.node) return s->ops->moments_geo(s->geom, s->coef, s->buf, s->buf.cur, s->stream);
+    return s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream);
+}
+
+size_t state_size(const nfe_sim *s) {
+    return sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes + s->ghost_bytes;
+}
+
+void geo_free(nfe_sim *s) {
+    void *ptrs[] = {s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1]};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    s->device_bytes -= s->geo_bytes;
+    s->geo_bytes = 0;
+    s->node_dev = nullptr;
+    s->inl_dev = nullptr;
+    s->buf.node = nullptr;
+    s->buf.inl = nullptr;
+    s->buf.ghost[0] = s->buf.ghost[1] = nullptr;
+    s->buf.outflow = 0;
+    s->ninlets = 0;
+    s->ghost_bytes = 0;
 }
 
 nfe_status check_sim(const nfe_sim *s) {
@@ -358,6 +394,7 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     s->cplanes_bytes = size_t(N - 1) * n * s->ops->c_elem_bytes;
     s->gplanes_bytes = stored_g ? size_t(N - 1) * Q * n * s->ops->c_elem_bytes : 0;
     s->tau_g = tau_g;
+    s->no_phi = (p->flags & NFE_NO_PHI) != 0;
     s->fields_planes = size_t(std::max(N + 7, Q - 1));
     const size_t ce = s->ops->c_elem_bytes;
 #define ALLOC(ptr, bytes) do { st = dev_alloc(s, reinterpret_cast<void **>(&(ptr)), (bytes)); \
@@ -428,6 +465,8 @@ nfe_status nfe_set_fields(nfe_sim *s, const double *C, const double *v) {
     }
     // stored g (tau_g != 1): g = g^eq(C, v, S(C)) at the start
     if (s->buf.g[0]) CK(s->ops->init_g(s->geom, s->coef, s->buf, 0, v ? s->buf.fields + (N - 1) * n : nullptr, s->stream));
+    // geometry: C := C_b on the inlet nodes, ghost column := column nx - 1
+    if (s->buf.node) CK(s->ops->geo_prepare(s->geom, s->buf, 0, s->ninlets, s->stream));
     CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
     CK(cudaStreamSynchronize(s->stream));
     s->buf.cur = 0;
@@ -476,7 +515,7 @@ nfe_status nfe_fields(nfe_sim *s, double *C, double *v, double *P) {
     nfe_status st = check_sim(s);
     if (st != NFE_OK) return st;
     if ((st = ensure_fields(s)) != NFE_OK) return st;
-    CK(s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream));
+    CK(run_moments(s));
     const size_t n = size_t(s->geom.n);
     const int N = s->N;
     if (C) CK(cudaMemcpyAsync(C, s->buf.fields, N * n * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -506,7 +545,7 @@ nfe_status nfe_domain_size(nfe_sim *s, double *L, int component, int nbins, doub
     if (nbins > 0 && (!Sk || component < 0 || component >= s->N))
         return fail(NFE_EINVAL, "S(k) wanted: Sk must be non-NULL and component in 0..N-1");
     if ((st = ensure_fields(s)) != NFE_OK) return st;
-    CK(s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream));      // C of all components, FP64
+    CK(run_moments(s));      // C of all components, FP64
     std::string err;
     if (!s->spectrum && (st = spectrum_create(s->geom, s->N, &s->spectrum, err)) != NFE_OK) return fail(st, "%s", err.c_str());
     if ((st = domain_size(s->spectrum, s->N, s->buf.fields, component, nbins, L, Sk, s->stream, err)) != NFE_OK)
@@ -520,7 +559,7 @@ nfe_status nfe_diagnostics(nfe_sim *s, nfe_diag *out) {
     if (!out) return fail(NFE_EINVAL, "out is NULL");
     if ((st = ensure_fields(s)) != NFE_OK) return st;
     const int N = s->N;
-    CK(s->ops->moments(s->geom, s->coef, s->buf, s->buf.cur, s->stream));
+    CK(run_moments(s));
     CK(s->ops->reduce(s->geom, s->buf, s->buf.cur, kReduceBlocks, s->stream));
     std::vector<double> d(diag_count(N));
     CK(cudaMemcpyAsync(d.data(), s->buf.diag, d.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
@@ -555,12 +594,13 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
     out->sites = s->geom.n;
     out->omega_stab = s->tab.omega;
     out->factor_residual = s->tab.residual;
-    out->kernels_per_step = s->ops->nk;
+    out->kernels_per_step = s->ops->nk + (s->buf.outflow ? 1 : 0);   // + the convective outflow
     out->variant = s->variant;
     out->nvariants = s->ops->nvariants;
     out->min_bytes_per_site = 2.0 * ((s->ops->Q - 1) * s->ops->f_elem_bytes + (s->N - 1) * s->ops->c_elem_bytes);
     if (s->buf.g[0]) out->min_bytes_per_site += 2.0 * (s->N - 1) * s->ops->Q * s->ops->c_elem_bytes;
-    out->state_bytes = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes;
+    if (s->buf.node) out->min_bytes_per_site += 1.0;   // the node class
+    out->state_bytes = state_size(s);
     out->device_bytes = s->device_bytes;
     return NFE_OK;
 }
@@ -568,7 +608,7 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
 nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
     nfe_status st = check_sim(s);
     if (st != NFE_OK) return st;
-    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes;
+    const size_t need = state_size(s);
     if (!host || bytes != need) return fail(NFE_EINVAL, "state buffer must be %zu bytes", need);
     char *h = static_cast<char *>(host);
     CK(cudaStreamSynchronize(s->stream));
@@ -579,6 +619,9 @@ nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
     if (s->buf.g[0])
         CK(cudaMemcpyAsync(h + sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes, s->buf.g[s->buf.cur],
                            s->gplanes_bytes, cudaMemcpyDeviceToHost, s->stream));
+    if (s->ghost_bytes)
+        CK(cudaMemcpyAsync(h + sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes,
+                           s->buf.ghost[s->buf.cur], s->ghost_bytes, cudaMemcpyDeviceToHost, s->stream));
     CK(cudaStreamSynchronize(s->stream));
     return NFE_OK;
 }
@@ -586,7 +629,7 @@ nfe_status nfe_get_state(nfe_sim *s, void *host, size_t bytes) {
 nfe_status nfe_set_state(nfe_sim *s, const void *host, size_t bytes) {
     nfe_status st = check_sim(s);
     if (st != NFE_OK) return st;
-    const size_t need = sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes;
+    const size_t need = state_size(s);
     if (!host || bytes != need) return fail(NFE_EINVAL, "state buffer must be %zu bytes", need);
     const char *h = static_cast<const char *>(host);
     CK(cudaStreamSynchronize(s->stream));
@@ -597,8 +640,83 @@ nfe_status nfe_set_state(nfe_sim *s, const void *host, size_t bytes) {
     if (s->buf.g[0])
         CK(cudaMemcpyAsync(s->buf.g[s->buf.cur], h + sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes,
                            s->gplanes_bytes, cudaMemcpyHostToDevice, s->stream));
+    if (s->ghost_bytes)
+        CK(cudaMemcpyAsync(s->buf.ghost[s->buf.cur], h + sizeof(int64_t) + s->fplanes_bytes + s->cplanes_bytes + s->gplanes_bytes,
+                           s->ghost_bytes, cudaMemcpyHostToDevice, s->stream));
     CK(cudaMemsetAsync(s->buf.flag, 0, sizeof(int), s->stream));
     CK(cudaStreamSynchronize(s->stream));
+    return NFE_OK;
+}
+
+nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const double *inlets, int outflow) {
+    nfe_status st = check_sim(s);
+    if (st != NFE_OK) return st;
+    CK(cudaStreamSynchronize(s->stream));
+    for (auto &g : s->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    if (!node) {
+        geo_free(s);
+        return NFE_OK;
+    }
+    if (s->grid.lattice != NFE_D2Q9 || !s->ops->geo_prepare)
+        return fail(NFE_EUNSUPPORTED, "open and complex boundaries run on D2Q9 only");
+    if (s->buf.g[0]) return fail(NFE_EUNSUPPORTED, "open and complex boundaries need tau_g = 1");
+    if (s->no_phi) return fail(NFE_EUNSUPPORTED, "open and complex boundaries together with NFE_NO_PHI");
+    if (ninlets < 0 || ninlets > kMaxInlets) return fail(NFE_EINVAL, "ninlets must be 0..%d", kMaxInlets);
+    if (ninlets > 0 && !inlets) return fail(NFE_EINVAL, "inlets is NULL");
+    const int N = s->N, nx = s->geom.nx, ny = s->geom.ny;
+    const size_t n = size_t(s->geom.n);
+    for (size_t i = 0; i < n; ++i)
+        if (node[i] >= kNodeInlet0 + ninlets) return fail(NFE_EINVAL, "node class %d at site %zu (ninlets = %d)", int(node[i]), i, ninlets);
+    // inlet rows in internal component order
+    std::vector<double> rows(size_t(std::max(ninlets, 1)) * (2 + N), 0.0);
+    for (int j = 0; j < ninlets; ++j) {
+        const double *r = inlets + size_t(j) * (2 + N);
+        double sum = 0.0;
+        for (int a = 0; a < 2 + N; ++a)
+            if (!std::isfinite(r[a])) return fail(NFE_EINVAL, "inlet %d: non-finite value", j);
+        for (int a = 0; a < N; ++a) {
+            if (r[2 + a] < 0.0) return fail(NFE_EINVAL, "inlet %d: C_b[%d] < 0", j, a);
+            sum += r[2 + a];
+        }
+        if (std::fabs(sum - 1.0) > 1e-9) return fail(NFE_EINVAL, "inlet %d: C_b sums to %.17g, not 1", j, sum);
+        double *o = rows.data() + size_t(j) * (2 + N);
+        o[0] = r[0];
+        o[1] = r[1];
+        for (int a = 0; a < N; ++a) o[2 + a] = r[2 + s->uidx[a]];
+    }
+    if (outflow) {
+        if (s->geom.wx) return fail(NFE_EINVAL, "outflow needs a periodic x axis (no x walls)");
+        if (nx < 3) return fail(NFE_EINVAL, "outflow needs nx >= 3");
+        for (int y = 0; y < ny; ++y) {
+            if (node[size_t(nx) * y] == kNodeFluid) return fail(NFE_EINVAL, "outflow: fluid node at (0, %d)", y);
+            if (node[size_t(nx) * y + nx - 1] >= kNodeInlet0) return fail(NFE_EINVAL, "outflow: inlet node at (%d, %d)", nx - 1, y);
+        }
+    }
+    geo_free(s);
+    const size_t ce = s->ops->c_elem_bytes;
+    if ((st = ensure_fields(s)) != NFE_OK) return st;
+    if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->node_dev), n)) != NFE_OK) return st;
+    if ((st = dev_alloc(s, &s->inl_dev, size_t(std::max(ninlets, 1)) * 2 * N * ce)) != NFE_OK) { geo_free(s); return st; }
+    if (outflow) {
+        s->ghost_bytes = size_t(N - 1) * ny * ce;
+        for (int b = 0; b < 2; ++b)
+            if ((st = dev_alloc(s, &s->buf.ghost[b], s->ghost_bytes)) != NFE_OK) { geo_free(s); return st; }
+    }
+    s->geo_bytes = n + size_t(std::max(ninlets, 1)) * 2 * N * ce + 2 * s->ghost_bytes;
+    s->buf.node = s->node_dev;
+    s->buf.inl = s->inl_dev;
+    s->buf.outflow = outflow ? 1 : 0;
+    s->ninlets = ninlets;
+    cudaError_t e = cudaMemcpyAsync(s->node_dev, node, n, cudaMemcpyHostToDevice, s->stream);
+    // the FP64 rows go through the fields scratch (n >= 1 doubles per plane, at least N + 7 planes)
+    if (e == cudaSuccess && ninlets > 0) {
+        if (rows.size() > s->fields_planes * n) { geo_free(s); return fail(NFE_EINVAL, "inlet table larger than the grid scratch"); }
+        e = cudaMemcpyAsync(s->buf.fields, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = s->ops->inlet_table(s->coef, s->buf.fields, ninlets, s->inl_dev, s->stream);
+    }
+    if (e == cudaSuccess) e = s->ops->geo_prepare(s->geom, s->buf, s->buf.cur, ninlets, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) { geo_free(s); return cuda_fail(e, "nfe_set_geometry"); }
     return NFE_OK;
 }
 

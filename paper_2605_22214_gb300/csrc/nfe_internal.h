@@ -58,6 +58,11 @@ struct Coef {
     T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 6); last member
 };
 
+// Node classes of the D2Q9 geometry (open and complex boundaries, Sec. III C): one byte per
+// site.  Inside the kernels, kNodeGhost marks the outflow ghost column beyond x = nx - 1.
+constexpr unsigned char kNodeFluid = 0, kNodeSolid = 1, kNodeInlet0 = 2, kNodeGhost = 255;
+constexpr int kMaxInlets = 64;
+
 // One kernel kind for profiling.
 enum KernelKind { K_FUSED = 0, K_MOMENTS = 1, K_REDUCE = 2, K_NKINDS = 3 };
 extern const char *kKernelNames[K_NKINDS];
@@ -72,6 +77,11 @@ struct Buffers {
     double *diag;         // reduction result
     int *flag;            // non-finite flag
     int cur;              // index of the buffer holding the current state
+    // D2Q9 geometry (null when the grid has none)
+    const unsigned char *node;   // node class per site
+    const void *inl;             // inlet table, compute type: per inlet vx, vy, C_b (N-1), S_b (N-1)
+    void *ghost[2];              // outflow ghost column, (N-1) x ny, compute type, or null
+    int outflow;                 // convective outflow on the x = nx - 1 edge
 };
 
 // Launchers exported by the lattice translation units.  Each returns
@@ -102,6 +112,12 @@ struct Ops {
     cudaError_t (*init_g)(const Geom &, const void *coef, const Buffers &, int cur, const double *v, cudaStream_t);
     int f_elem_bytes;     // bytes per stored population
     int c_elem_bytes;     // bytes per stored volume fraction (and per scratch value)
+    // D2Q9 geometry (null for D3Q19): the inlet table from FP64 rows (vx, vy, C_b of all N
+    // components in internal order) on the device; C := C_b on the inlet nodes and ghost :=
+    // column nx - 1 in buffer cur; the fields of the state in buffer cur with the node classes
+    cudaError_t (*inlet_table)(const void *coef, const double *rows, int ninl, void *out, cudaStream_t);
+    cudaError_t (*geo_prepare)(const Geom &, const Buffers &, int cur, int ninl, cudaStream_t);
+    cudaError_t (*moments_geo)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
 };
 
 // One translation unit per lattice and precision (compiled in parallel).
