@@ -99,11 +99,76 @@ __device__ __forceinline__ int imod(int v, int n) { return ((v % n) + n) % n; }
 // unless the domain is narrower than a tile plus ring (then a full modulo).
 __device__ __forceinline__ int pwrap(int v, int n, bool tiny) { return tiny ? imod(v, n) : wrap(v, n); }
 
+// Packed FP32 arithmetic (two values per instruction, sm_100 and later).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// The stencil sums of stencil2d below for FP32, two record values at a time: values 2p and
+// 2p + 1 of record A (the evolved C, then E_B) share every instruction.
+template <int N, int AX, bool CHECK>
+__device__ __forceinline__ void stencil2d_packed(const float *sA, int acount, int ia, unsigned wall,
+                                                 float (&c)[N], float (&lap)[N], float (&gx)[N], float (&gy)[N],
+                                                 float &gEx, float &gEy) {
+    using RA = SRec<float, N>;
+    constexpr int NPU = (N + 1) / 2;     // pairs holding the N used values
+    float r0[RA::NVP];
+    srec_load<float, N>(sA, acount, ia, r0);
+    float2 d[9][NPU];
+    constexpr int off[9] = {0, 1, -1, AX, -AX, AX + 1, -AX - 1, -AX + 1, AX - 1};
+    sfor<1, 9, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
+        if (CHECK && ((wall >> k) & 1u)) {
+#pragma unroll
+            for (int p = 0; p < NPU; ++p) d[k][p] = make_float2(0.0f, 0.0f);
+        } else {
+            float r[RA::NVP];
+            srec_load<float, N>(sA, acount, ia + off[k], r);
+#pragma unroll
+            for (int p = 0; p < NPU; ++p)
+                d[k][p] = sub2(make_float2(r[2 * p], r[2 * p + 1]), make_float2(r0[2 * p], r0[2 * p + 1]));
+        }
+    });
+    const float2 third = dup2(1.0f / 3.0f), twelfth = dup2(1.0f / 12.0f), two3 = dup2(2.0f / 3.0f), sixth = dup2(1.0f / 6.0f);
+    float L[2 * NPU], X[2 * NPU], Y[2 * NPU];
+#pragma unroll
+    for (int p = 0; p < NPU; ++p) {
+        const float2 ax = add2(add2(d[1][p], d[2][p]), add2(d[3][p], d[4][p]));
+        const float2 dg = add2(add2(d[5][p], d[6][p]), add2(d[7][p], d[8][p]));
+        const float2 d56 = sub2(d[5][p], d[6][p]), d78 = sub2(d[7][p], d[8][p]);
+        const float2 l = fma2(two3, ax, mul2(sixth, dg));                           // (2/c_s^2) sum w_k d_k
+        const float2 x = fma2(third, sub2(d[1][p], d[2][p]), mul2(twelfth, add2(d56, d78)));
+        const float2 y = fma2(third, sub2(d[3][p], d[4][p]), mul2(twelfth, sub2(d56, d78)));
+        L[2 * p] = l.x; L[2 * p + 1] = l.y;
+        X[2 * p] = x.x; X[2 * p + 1] = x.y;
+        Y[2 * p] = y.x; Y[2 * p + 1] = y.y;
+    }
+    float sl = 0.0f, sgx = 0.0f, sgy = 0.0f, rest = 0.0f;
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) {
+        c[a] = r0[a];
+        lap[a] = L[a]; gx[a] = X[a]; gy[a] = Y[a];
+        sl += L[a]; sgx += X[a]; sgy += Y[a];
+        rest += r0[a];
+    }
+    // implicit component: C_N = 1 - sum, its stencils are minus the sum of the others
+    c[N - 1] = 1.0f - rest;
+    lap[N - 1] = -sl; gx[N - 1] = -sgx; gy[N - 1] = -sgy;
+    gEx = X[N - 1];
+    gEy = Y[N - 1];
+}
+
 // Stencil of one site from record A at local index ia (row pitch AX).  `wall`
 // holds bit k set when x + e_k lies beyond a wall (then that term is dropped).
 template <int N, typename T, int AX, bool CHECK>
 __device__ __forceinline__ void stencil2d(const T *sA, int acount, int ia, unsigned wall,
                                           T (&c)[N], T (&lap)[N], T (&gx)[N], T (&gy)[N], T &gEx, T &gEy) {
+    if constexpr (sizeof(T) == 4) {
+        stencil2d_packed<N, AX, CHECK>(sA, acount, ia, wall, c, lap, gx, gy, gEx, gEy);
+        return;
+    }
     using RA = SRec<T, N>;
     T r0[RA::NVP];
     srec_load<T, N>(sA, acount, ia, r0);
@@ -438,6 +503,21 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
         // no wrap and no wall for any target: the site is inside the domain by one site
         const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && (!GEO || open0 == 0u);
+        if constexpr (sizeof(T) == 4) {
+            // FP32: the two pairs of one weight class share every instruction, pair (1, 2) or
+            // (5, 6) in the first lane and (3, 4) or (7, 8) in the second
+            const float2 mhop = dup2(-hop), mhom = dup2(-hom);
+            auto cls = [&](float wk, float2 eu, float2 eF, float &fa, float &fab, float &fc, float &fcb) {
+                const float2 fk = make_float2(fa, fc), fkb = make_float2(fab, fcb);
+                const float2 sp = add2(fk, fkb), dm = sub2(fk, fkb);
+                const float2 sym = fma2(mhop, sp, fma2(eu, fma2(dup2(wk * Y), eu, mul2(dup2(wk * Z), eF)), dup2(wk * X)));
+                const float2 anti = fma2(mhom, dm, fma2(dup2(wk * U), eu, mul2(dup2(wk * V), eF)));
+                const float2 pk = add2(fk, add2(sym, anti)), pkb = add2(fkb, sub2(sym, anti));
+                fa = pk.x; fc = pk.y; fab = pkb.x; fcb = pkb.y;
+            };
+            cls(float(LD2Q9::w(1)), make_float2(vx, vy), make_float2(Fx, Fy), f[1], f[2], f[3], f[4]);
+            cls(float(LD2Q9::w(5)), make_float2(vx + vy, vx - vy), make_float2(Fx + Fy, Fx - Fy), f[5], f[6], f[7], f[8]);
+        } else {
         sfor<1, 9, 2>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             const int kb = k + 1;
@@ -451,6 +531,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             f[k] = f[k] + sym + anti;
             f[kb] = f[kb] + sym - anti;
         });
+        }
         // one branch around the whole store block: inside the unrolled loop the compiler
         // would predicate both forms for every site
         if (fast) {
