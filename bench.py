@@ -291,7 +291,9 @@ def run_nfe(args):
                  ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "fp32", 20, False),
                  ("janus 256^3 D3Q19 N=4", W.janus_3d(seed=1004), "bf16", 20, False),
                  ("emulsion generator 600x140 D2Q9 N=4 (solid walls, 6 inlets, convective outflow)",
-                  W.emulsion_2d(), "fp32", args.steps // 4, True)]
+                  W.emulsion_2d(), "fp32", args.steps // 4, True),
+                 ("porous channel 4096x1024 D2Q9 N=4 (4x4 posts every 16 sites, inlet, outflow)",
+                  W.porous_channel_2d(), "fp32", 60, False)]
         for name, q, prec, K, fl in cases:
             nq = q["nx"] * q["ny"] * q["nz"]
             with nfe.Sim(q, prec, stream=stream.cuda_stream, scale_exp=10) as sx:

@@ -29,7 +29,7 @@ __all__ = [
     "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
     "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
     "batch_sweep", "random_sigma", "random_simplex_points", "phase_separation_2d", "CONFIGS",
-    "open_channel_2d", "emulsion_2d", "FLUID", "SOLID", "INLET0",
+    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "FLUID", "SOLID", "INLET0",
 ]
 
 # node classes of a geometry (one byte per site)
@@ -303,6 +303,34 @@ def open_channel_2d(nx=70, ny=36, N=3, seed=1021, tau=0.8, m=1.0 / 50.0, outflow
     p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, omega_stab=1.0 / 90.0, name=f"open_channel_{nx}x{ny}_N{N}")
     p["C0"] = C
     p["geometry"] = dict(node=node, inlets=inlets, outflow=bool(outflow))
+    return p
+
+
+def porous_channel_2d(nx=4096, ny=1024, N=4, seed=1031, pitch=16, post=4, u=0.01, tau=0.8, m=0.1):
+    """A large channel through a square lattice of solid posts (post x post sites every pitch
+    sites), solid rows at y = 0 and ny - 1, an inlet column at x = 0 feeding component 0 at
+    (u, 0), and the convective outflow at x = nx - 1; the interior starts as the seeded
+    spinodal mixture (C_i = 1/N + U(-0.02, 0.02), renormalised).  A throughput case for the
+    geometry form of the step at a size far beyond L2."""
+    rng = np.random.default_rng(seed)
+    node = np.zeros((1, ny, nx), dtype=np.uint8)
+    y, x = np.mgrid[0:ny, 0:nx]
+    node[0][((x % pitch) >= pitch // 2) & ((x % pitch) < pitch // 2 + post)
+            & ((y % pitch) >= pitch // 2) & ((y % pitch) < pitch // 2 + post)] = SOLID
+    node[:, 0, :] = SOLID
+    node[:, -1, :] = SOLID
+    node[:, :, 0] = SOLID
+    node[:, 1:-1, 0] = INLET0
+    inlets = np.zeros((1, 2 + N))
+    inlets[0, 0] = u
+    inlets[0, 2] = 1.0
+    C = 1.0 / N + rng.uniform(-0.02, 0.02, size=(N, 1, ny, nx))
+    C /= C.sum(axis=0, keepdims=True)
+    sig = np.full((N, N), 0.005)
+    np.fill_diagonal(sig, 0.0)
+    p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, name=f"porous_{nx}x{ny}_N{N}")
+    p["C0"] = C
+    p["geometry"] = dict(node=node, inlets=inlets, outflow=True)
     return p
 
 

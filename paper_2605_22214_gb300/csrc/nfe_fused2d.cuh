@@ -426,8 +426,12 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
     T S[N - 1], Fx, Fy, vx, vy, P, sumf;
     {
         const int ia = (ty + 2) * Sh::AX + (tx + 2);
-        if (GEO ? wall0 != 0u : wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
-        else                           stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
+        // GEO: one choice per warp (the checked form gives the same values where no neighbour is
+        // solid, and a per-site choice would run both forms in every warp that meets a post)
+        if (GEO ? __any_sync(0xffffffffu, wall0 != 0u) : wallt)
+            stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, wall0, c, lap, gxv, gyv, gEx, gEy);
+        else
+            stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, c, lap, gxv, gyv, gEx, gEy);
         site_physics<N, T, Q4>(cf, c, lap, gxv, gyv, gEx, gEy, f, S, Fx, Fy, vx, vy, P, sumf);
         if constexpr (GEO) {
             // an inlet node's record is its prescribed state (C_b is its stored C)
@@ -460,8 +464,10 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
                 if (sN[ia + LD2Q9::ex(k) + Sh::AX * LD2Q9::ey(k)] == kNodeSolid) hwall |= 1u << k;
             });
         }
-        if (GEO ? hwall != 0u : wallt) stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
-        else                           stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
+        if (GEO ? __any_sync(__activemask(), hwall != 0u) : wallt)
+            stencil2d<N, T, Sh::AX, true>(sA, Sh::ACOUNT, ia, hwall, hc, hl, hgx, hgy, hEx, hEy);
+        else
+            stencil2d<N, T, Sh::AX, false>(sA, Sh::ACOUNT, ia, 0u, hc, hl, hgx, hgy, hEx, hEy);
         T hS[N - 1], hFx, hFy, hvx, hvy, hP, hsum;
         site_physics<N, T, Q4>(cf, hc, hl, hgx, hgy, hEx, hEy, hf, hS, hFx, hFy, hvx, hvy, hP, hsum);
         if constexpr (GEO) {
@@ -502,7 +508,9 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         const T hop = T(0.5) * op, hom = T(0.5) * om;
         const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
         // no wrap and no wall for any target: the site is inside the domain by one site
-        const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && (!GEO || open0 == 0u);
+        bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && (!GEO || open0 == 0u);
+        // GEO: the general store block gives the same stores for a fast site; one choice per warp
+        if constexpr (GEO) fast = __all_sync(__activemask(), fast);
         if constexpr (sizeof(T) == 4) {
             // FP32: the two pairs of one weight class share every instruction, pair (1, 2) or
             // (5, 6) in the first lane and (3, 4) or (7, 8) in the second
@@ -690,8 +698,10 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
                 }
             });
         };
-        // decided per site (not per tile), so a site runs the same code under every tile shape
-        if (wall0) gather(std::true_type{});
+        // decided per site (not per tile), so a site runs the same code under every tile shape;
+        // the geometry form (one tile shape) decides per warp, the checked form giving the same
+        // values where no neighbour is solid
+        if (GEO ? __any_sync(__activemask(), wall0 != 0u) : wall0 != 0u) gather(std::true_type{});
         else gather(std::false_type{});
         bool bad = false;
 #pragma unroll

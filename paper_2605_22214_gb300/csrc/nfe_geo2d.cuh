@@ -1,12 +1,14 @@
 // Open and complex boundaries of the D2Q9 step (Sec. III C; the conditions of the microfluidic
 // and patterned-surface applications): the kernels besides the fused tile's geometry form.
 //
-//   k_outflow2d     the convective outflow on the x = nx - 1 edge, after the fused step:
+//   k_outflow_sum / k_outflow_apply
+//                   the convective outflow on the x = nx - 1 edge, after the fused step:
 //                   U = mean over the fluid nodes of column nx - 2 of sum_k e_kx f_k(t+1);
 //                   every population and volume fraction of a fluid node in column nx - 1
 //                   becomes (old + U new(upstream)) / (1 + U); the ghost column follows
 //                   with C(nx - 1, t+1).  The F/2 term of the velocity is left out (F at
-//                   t+1 is not known at this point).  One CTA, fixed-order reduction.
+//                   t+1 is not known at this point).  One thread per row; the partial sums
+//                   of U are added in a fixed order, so U is the same on every run.
 //   k_inlet_table   per inlet: v_b, C_b and the flux potential S_b of the uniform state C_b
 //                   (Eq. 12 without the Laplacian term), in the compute type.
 //   k_geo_prepare   C := C_b on the inlet nodes; ghost := column nx - 1.
@@ -17,64 +19,89 @@
 
 namespace nfe {
 
-template <int N, typename T, typename SF>
-__global__ void __launch_bounds__(512)
-k_outflow2d(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, const SF *__restrict__ fold,
-            SF *__restrict__ fnew, const T *__restrict__ Cold, T *__restrict__ Cnew,
-            const T *__restrict__ gh_in, T *__restrict__ gh_out) {
-    constexpr int NT = 512;
-    __shared__ double red[NT];
-    __shared__ int cnt[NT];
+// Rows per CTA of the two outflow kernels.
+constexpr int kOutflowRows = 128;
+
+// Part 1: per CTA, the sum of sum_k e_kx f_k(t+1) over the fluid nodes of column nx - 2 in its
+// rows, and their count (FP64, fixed order).
+template <typename T, typename SF>
+__global__ void __launch_bounds__(kOutflowRows)
+k_outflow_sum(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, const SF *__restrict__ fnew,
+              double *__restrict__ part) {
+    __shared__ double red[kOutflowRows];
+    __shared__ int cnt[kOutflowRows];
     const int nx = g.nx, ny = g.ny;
     const size_t n = size_t(g.n);
-    const int tid = threadIdx.x;
-    double sum = 0.0;
+    const int tid = threadIdx.x, y = blockIdx.x * kOutflowRows + tid;
+    double jx = 0.0;
     int c = 0;
-    for (int y = tid; y < ny; y += NT) {
+    if (y < ny) {
         const int s = (nx - 2) + nx * y;
-        if (node[s] != kNodeFluid) continue;
-        T jx = T(0);
+        if (node[s] == kNodeFluid) {
+            T j = T(0);
 #pragma unroll
-        for (int k = 1; k < 9; ++k)
-            if (LD2Q9::ex(k) != 0) {
-                const T fk = FStore<SF, T>::load(fnew + (k - 1) * n + s, LD2Q9::w(k), cf.finv);
-                jx += LD2Q9::ex(k) > 0 ? fk : -fk;
-            }
-        sum += double(jx);
-        ++c;
+            for (int k = 1; k < 9; ++k)
+                if (LD2Q9::ex(k) != 0) {
+                    const T fk = FStore<SF, T>::load(fnew + (k - 1) * n + s, LD2Q9::w(k), cf.finv);
+                    j += LD2Q9::ex(k) > 0 ? fk : -fk;
+                }
+            jx = double(j);
+            c = 1;
+        }
     }
-    red[tid] = sum;
+    red[tid] = jx;
     cnt[tid] = c;
     __syncthreads();
-    for (int o = NT / 2; o > 0; o >>= 1) {
+    for (int o = kOutflowRows / 2; o > 0; o >>= 1) {
         if (tid < o) { red[tid] += red[tid + o]; cnt[tid] += cnt[tid + o]; }
         __syncthreads();
     }
-    const double U = cnt[0] > 0 ? red[0] / cnt[0] : 0.0;
+    if (tid == 0) { part[2 * blockIdx.x] = red[0]; part[2 * blockIdx.x + 1] = double(cnt[0]); }
+}
+
+// Part 2: U from the partial sums (every CTA adds them in the same order), then the update of
+// its rows of column nx - 1 and of the ghost column.
+template <int N, typename T, typename SF>
+__global__ void __launch_bounds__(kOutflowRows)
+k_outflow_apply(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, const SF *__restrict__ fold,
+                SF *__restrict__ fnew, const T *__restrict__ Cold, T *__restrict__ Cnew,
+                const T *__restrict__ gh_in, T *__restrict__ gh_out, const double *__restrict__ part, int nparts) {
+    __shared__ double Us;
+    const int nx = g.nx, ny = g.ny;
+    const size_t n = size_t(g.n);
+    if (threadIdx.x == 0) {
+        double sum = 0.0, c = 0.0;
+        for (int i = 0; i < nparts; ++i) { sum += part[2 * i]; c += part[2 * i + 1]; }
+        Us = c > 0.0 ? sum / c : 0.0;
+    }
+    __syncthreads();
+    const double U = Us;
     const T u = T(U), inv = T(1.0 / (1.0 + U));
-    for (int y = tid; y < ny; y += NT) {
-        const int sN = (nx - 1) + nx * y, sM = (nx - 2) + nx * y;
-        if (node[sN] == kNodeFluid) {
+    const int y = blockIdx.x * kOutflowRows + threadIdx.x;
+    if (y >= ny) return;
+    const int sN = (nx - 1) + nx * y, sM = (nx - 2) + nx * y;
+    if (node[sN] == kNodeFluid) {
 #pragma unroll
-            for (int k = 1; k < 9; ++k) {
-                const T a = FStore<SF, T>::load(fold + (k - 1) * n + sN, LD2Q9::w(k), cf.finv);
-                const T b = FStore<SF, T>::load(fnew + (k - 1) * n + sM, LD2Q9::w(k), cf.finv);
-                FStore<SF, T>::store(fnew + (k - 1) * n + sN, (a + u * b) * inv, LD2Q9::w(k), cf.fscale);
-            }
-#pragma unroll
-            for (int e = 0; e < N - 1; ++e) Cnew[e * n + sN] = (Cold[e * n + sN] + u * Cnew[e * n + sM]) * inv;
+        for (int k = 1; k < 9; ++k) {
+            const T a = FStore<SF, T>::load(fold + (k - 1) * n + sN, LD2Q9::w(k), cf.finv);
+            const T b = FStore<SF, T>::load(fnew + (k - 1) * n + sM, LD2Q9::w(k), cf.finv);
+            FStore<SF, T>::store(fnew + (k - 1) * n + sN, (a + u * b) * inv, LD2Q9::w(k), cf.fscale);
         }
 #pragma unroll
-        for (int e = 0; e < N - 1; ++e) gh_out[e * ny + y] = (gh_in[e * ny + y] + u * Cnew[e * n + sN]) * inv;
+        for (int e = 0; e < N - 1; ++e) Cnew[e * n + sN] = (Cold[e * n + sN] + u * Cnew[e * n + sM]) * inv;
     }
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) gh_out[e * ny + y] = (gh_in[e * ny + y] + u * Cnew[e * n + sN]) * inv;
 }
 
 template <int N, typename T, typename SF>
 cudaError_t launch_outflow2d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
-    k_outflow2d<N, T, SF><<<1, 512, 0, st>>>(
+    const int blocks = (g.ny + kOutflowRows - 1) / kOutflowRows;
+    k_outflow_sum<T, SF><<<blocks, kOutflowRows, 0, st>>>(g, cf, b.node, static_cast<const SF *>(b.f[1 - cur]), b.opart);
+    k_outflow_apply<N, T, SF><<<blocks, kOutflowRows, 0, st>>>(
         g, cf, b.node, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
         static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]),
-        static_cast<const T *>(b.ghost[cur]), static_cast<T *>(b.ghost[1 - cur]));
+        static_cast<const T *>(b.ghost[cur]), static_cast<T *>(b.ghost[1 - cur]), b.opart, blocks);
     return cudaGetLastError();
 }
 

@@ -163,7 +163,8 @@ nfe_status free_all(nfe_sim *s) {
     s->event_pool.clear();
     void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
                     s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev,
-                    s->buf.g[0], s->buf.g[1], s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1]};
+                    s->buf.g[0], s->buf.g[1], s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1],
+                    s->buf.opart};
     for (void *p : ptrs) if (p) cudaFree(p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
@@ -281,8 +282,9 @@ size_t state_size(const nfe_sim *s) {
 }
 
 void geo_free(nfe_sim *s) {
-    void *ptrs[] = {s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1]};
+    void *ptrs[] = {s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1], s->buf.opart};
     for (void *p : ptrs) if (p) cudaFree(p);
+    s->buf.opart = nullptr;
     s->device_bytes -= s->geo_bytes;
     s->geo_bytes = 0;
     s->node_dev = nullptr;
@@ -594,7 +596,7 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
     out->sites = s->geom.n;
     out->omega_stab = s->tab.omega;
     out->factor_residual = s->tab.residual;
-    out->kernels_per_step = s->ops->nk + (s->buf.outflow ? 1 : 0);   // + the convective outflow
+    out->kernels_per_step = s->ops->nk + (s->buf.outflow ? 2 : 0);   // + the convective outflow
     out->variant = s->variant;
     out->nvariants = s->ops->nvariants;
     out->min_bytes_per_site = 2.0 * ((s->ops->Q - 1) * s->ops->f_elem_bytes + (s->N - 1) * s->ops->c_elem_bytes);
@@ -701,8 +703,11 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         s->ghost_bytes = size_t(N - 1) * ny * ce;
         for (int b = 0; b < 2; ++b)
             if ((st = dev_alloc(s, &s->buf.ghost[b], s->ghost_bytes)) != NFE_OK) { geo_free(s); return st; }
+        const size_t pb = size_t(2 * ((ny + 127) / 128)) * sizeof(double);
+        if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.opart), pb)) != NFE_OK) { geo_free(s); return st; }
+        s->geo_bytes += pb;
     }
-    s->geo_bytes = n + size_t(std::max(ninlets, 1)) * 2 * N * ce + 2 * s->ghost_bytes;
+    s->geo_bytes += n + size_t(std::max(ninlets, 1)) * 2 * N * ce + 2 * s->ghost_bytes;
     s->buf.node = s->node_dev;
     s->buf.inl = s->inl_dev;
     s->buf.outflow = outflow ? 1 : 0;

@@ -4,6 +4,8 @@
 
 WORKLOAD is one of: spinodal (D2Q9, N = 4, size^2), janus3d (D3Q19, N = 4, size^3),
 lens (D2Q9, N = 3, size^2, walls in y), poiseuille3d (D3Q19, N = 7, 32 x 32 x 192),
+porous (D2Q9, N = 4, (4 size) x size channel through solid posts, inlet and outflow),
+emulsion (D2Q9, N = 4, the 600 x 140 emulsion generator),
 batch (--sims D2Q9 lens/Janus simulations of mixed size and N in one batch, FP32;
 --mode persistent | per_step | auto).
 The time is taken with CUDA events around the steps, after three warm-up steps.
@@ -30,6 +32,10 @@ def make(name, size):
         return W.lens_2d(nx=size, ny=size, radius=12.0 * size / 64.0)
     if name == "poiseuille3d":
         return W.layered_poiseuille()
+    if name == "porous":
+        return W.porous_channel_2d(nx=4 * size, ny=size)
+    if name == "emulsion":
+        return W.emulsion_2d()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -56,6 +62,9 @@ def main():
     stream = torch.cuda.Stream()
     with nfe.Sim(p, args.precision, stream=stream.cuda_stream, scale_exp=10) as s:
         s.set_fields(p["C0"])
+        if "geometry" in p:
+            geo = p["geometry"]
+            s.set_geometry(geo["node"], geo["inlets"], geo["outflow"])
         s.set_variant(args.variant)
         with torch.cuda.stream(stream):
             s.step(3)

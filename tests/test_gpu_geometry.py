@@ -72,6 +72,14 @@ def test_open_channel_matches_oracle(precision, outflow):
     _check(oracle_run(p, steps), gpu_run(p, steps, precision), precision)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_porous_channel_matches_oracle(precision):
+    # the bench's porous-channel layout (posts every 16 sites, inlet column, outflow) at 130 x 44
+    p = W.porous_channel_2d(nx=130, ny=44)
+    steps = 25
+    _check(oracle_run(p, steps), gpu_run(p, steps, precision), precision)
+
+
 def test_geometry_and_fields_in_either_order():
     p = W.open_channel_2d(70, 36, 3)
     a = gpu_run(p, 10, "fp64")
