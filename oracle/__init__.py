@@ -22,10 +22,13 @@ Kusumaatmaja):
                      and the wall-gradient rule (Eqs. 44-45), periodic edges.
   * `observables` -- Sec. IV: Neumann angles (Eq. 51), the layered-Poiseuille
                      profile (Eqs. 53-58), Laplace pressure and lens angles
-                     measured from fields.
+                     measured from fields, and the domain size L_i.
+  * `boundaries`  -- Sec. III C on D2Q9: solid nodes inside the grid, velocity
+                     and volume-fraction inlets and the convective outflow (the
+                     conditions of the applications in Sec. V).
 
 Every floating-point value is numpy float64.  The time stepper keeps all Q
 populations f_k (f_0 included) and all (N-1) Q populations g_{i,k} with a
 general tau_g, streams them, and bounces them back, in the order of Sec. III.
 """
-from . import poly, thermo, lbm, observables  # noqa: F401
+from . import poly, thermo, lbm, observables, boundaries  # noqa: F401
