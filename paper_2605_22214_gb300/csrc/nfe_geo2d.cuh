@@ -20,7 +20,7 @@
 namespace nfe {
 
 // Rows per CTA of the two outflow kernels.
-constexpr int kOutflowRows = 128;
+constexpr int kOutflowRows = 32;
 
 // Part 1: per CTA, the sum of sum_k e_kx f_k(t+1) over the fluid nodes of column nx - 2 in its
 // rows, and their count (FP64, fixed order).

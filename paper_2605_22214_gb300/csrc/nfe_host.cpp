@@ -703,7 +703,7 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         s->ghost_bytes = size_t(N - 1) * ny * ce;
         for (int b = 0; b < 2; ++b)
             if ((st = dev_alloc(s, &s->buf.ghost[b], s->ghost_bytes)) != NFE_OK) { geo_free(s); return st; }
-        const size_t pb = size_t(2 * ((ny + 127) / 128)) * sizeof(double);
+        const size_t pb = size_t(2 * ((ny + 31) / 32)) * sizeof(double);   // 2 per CTA of the outflow (32 rows)
         if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.opart), pb)) != NFE_OK) { geo_free(s); return st; }
         s->geo_bytes += pb;
     }

@@ -82,7 +82,7 @@ struct Buffers {
     const void *inl;             // inlet table, compute type: per inlet vx, vy, C_b (N-1), S_b (N-1)
     void *ghost[2];              // outflow ghost column, (N-1) x ny, compute type, or null
     int outflow;                 // convective outflow on the x = nx - 1 edge
-    double *opart;               // outflow partial sums (2 per 128 rows), or null
+    double *opart;               // outflow partial sums (2 per 32 rows), or null
 };
 
 // Launchers exported by the lattice translation units.  Each returns
