@@ -85,6 +85,10 @@ class Params:
         self.m = float(p["m"])
         self.tau_g = float(p.get("tau_g", 1.0))
         self.body_force = np.asarray(p["body_force"], dtype=np.float64)
+        # a body force acting on one component, in proportion to its volume fraction
+        # (F += C_c F_c; the PaLS study of Sec. V pushes only the droplet of fluid 2)
+        self.component_force = np.asarray(p.get("component_force", (0.0, 0.0, 0.0)), dtype=np.float64)
+        self.component_force_index = int(p.get("component_force_index", 0))
         self.implicit = int(p["implicit"])
         self.evolved = [c for c in range(self.N) if c != self.implicit]
         self.tables = Tables(p["sigma"], p["D"], p["omega_stab"])
@@ -274,6 +278,8 @@ def macroscopic(prm, C, f, flux_form="literal", force_form="conservative", with_
     else:
         raise ValueError(force_form)
     F = Fs + prm.body_force.reshape(3, 1, 1, 1)
+    if np.any(prm.component_force != 0.0):
+        F = F + prm.component_force.reshape(3, 1, 1, 1) * C[prm.component_force_index]
     j = np.zeros((3,) + prm.shape)
     for k in range(1, lat.Q):
         for a in range(3):
