@@ -293,7 +293,9 @@ def run_nfe(args):
                  ("emulsion generator 600x140 D2Q9 N=4 (solid walls, 6 inlets, convective outflow)",
                   W.emulsion_2d(), "fp32", args.steps // 4, True),
                  ("porous channel 4096x1024 D2Q9 N=4 (4x4 posts every 16 sites, inlet, outflow)",
-                  W.porous_channel_2d(), "fp32", 60, False)]
+                  W.porous_channel_2d(), "fp32", 60, False),
+                 ("patterned liquid surface 400x140 D2Q9 N=4 (walls, posts, force on fluid 2)",
+                  W.pals_2d(), "fp32", args.steps // 4, True)]
         for name, q, prec, K, fl in cases:
             nq = q["nx"] * q["ny"] * q["nz"]
             with nfe.Sim(q, prec, stream=stream.cuda_stream, scale_exp=10) as sx:

@@ -112,6 +112,10 @@ typedef struct {
                                  ((N-1) x Q planes, two buffers, compute type) and run D2Q9 single
                                  simulations only: NFE_EUNSUPPORTED for D3Q19, for batches and
                                  together with NFE_NO_PHI */
+    double component_force[3];    /* a body force acting on one component in proportion to its
+                                     volume fraction, F += C_c F_c (the PaLS study of Sec. V drives
+                                     only the droplet of fluid 2); all zero = none */
+    int component_force_index;    /* c, 0 .. N-1 (user order; ignored when the force is zero) */
 } nfe_params;
 
 /* Global quantities of the current state, reduced on the GPU in FP64. */

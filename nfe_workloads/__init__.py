@@ -29,7 +29,7 @@ __all__ = [
     "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
     "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
     "batch_sweep", "random_sigma", "random_simplex_points", "phase_separation_2d", "CONFIGS",
-    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "FLUID", "SOLID", "INLET0",
+    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "pals_2d", "FLUID", "SOLID", "INLET0",
 ]
 
 # node classes of a geometry (one byte per site)
@@ -331,6 +331,48 @@ def porous_channel_2d(nx=4096, ny=1024, N=4, seed=1031, pitch=16, post=4, u=0.01
     p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, name=f"porous_{nx}x{ny}_N{N}")
     p["C0"] = C
     p["geometry"] = dict(node=node, inlets=inlets, outflow=True)
+    return p
+
+
+def pals_2d(nx=400, ny=140, force=3e-7, m=1.0 / 50.0):
+    """The patterned liquid surface of Sec. V, N = 4 (fluids 1..4 = components 0..3): halfway
+    walls at the bottom and top (y), periodic in x; eight stripes of alternating lubricants 3 and
+    4 of height 15 on the bottom wall; solid posts of 2 x 5 sites on the wall at each
+    lubricant-lubricant interface; a hemispherical droplet of fluid 2 of radius 60 resting on
+    the lubricant, in fluid 1; a horizontal body force acting on fluid 2 only (F = C_2 F_b).
+    sigma_13 = sigma_14 = sigma_23 = sigma_24 = 0.01, sigma_12 = sigma_34 = 0.005, Omega = 1/90,
+    eta = (2/300, 0.1, 2/3, 2/3) (tau = 3 eta + 1/2), Lambda_TRT = 3/16.  Interfaces are tanh
+    profiles of width 2 lu; the stripe and post placement is a reading of the figure."""
+    N = 4
+    sig = np.full((N, N), 0.005)
+    np.fill_diagonal(sig, 0.0)
+    for a, b in ((0, 2), (0, 3), (1, 2), (1, 3)):
+        sig[a, b] = sig[b, a] = 0.01
+    tau = 3.0 * np.array([2.0 / 300.0, 0.1, 2.0 / 3.0, 2.0 / 3.0]) + 0.5
+    x, y, z = _coords(nx, ny, 1)
+    h, nstripe, R = 15.0, 8, 60.0
+    width = nx / nstripe
+    lub = tanh_step(h - 0.5 - y)                                    # lubricant layer
+    stripe = (np.floor((x + 0.5) / width).astype(int) % 2 == 0)
+    xc = nx / 2.0 - 0.5
+    drop = (1.0 - lub) * tanh_step(R - np.hypot(x - xc, y - (h - 0.5)))
+    C = np.zeros((N, 1, ny, nx))
+    C[2] = lub * stripe
+    C[3] = lub * (~stripe)
+    C[1] = drop
+    C[0] = np.maximum(1.0 - C[1] - C[2] - C[3], 0.0)
+    C /= C.sum(axis=0, keepdims=True)
+    node = np.zeros((1, ny, nx), dtype=np.uint8)
+    for k in range(nstripe):
+        x0 = int(round(k * width)) - 1
+        for dx in range(2):
+            node[0, 0:5, (x0 + dx) % nx] = SOLID
+    p = base_params(D2Q9, nx, ny, 1, N, sig, tau, walls=(False, True, False), lambda_trt=3.0 / 16.0, m=m,
+                    omega_stab=1.0 / 90.0, name=f"pals_{nx}x{ny}")
+    p["C0"] = C
+    p["geometry"] = dict(node=node, inlets=np.zeros((0, 2 + N)), outflow=False)
+    p["component_force"] = (float(force), 0.0, 0.0)
+    p["component_force_index"] = 1
     return p
 
 

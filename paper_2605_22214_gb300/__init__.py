@@ -50,7 +50,8 @@ class nfe_params(C.Structure):
                 ("lambda_trt", C.c_double), ("m", C.c_double), ("D", C.c_double),
                 ("omega_stab", C.c_double), ("body_force", C.c_double * 3),
                 ("precision", C.c_int), ("implicit_component", C.c_int), ("flags", C.c_int),
-                ("scale_exp", C.c_int), ("cuda_stream", C.c_void_p), ("tau_g", C.c_double)]
+                ("scale_exp", C.c_int), ("cuda_stream", C.c_void_p), ("tau_g", C.c_double),
+                ("component_force", C.c_double * 3), ("component_force_index", C.c_int)]
 
 
 class nfe_diag(C.Structure):
@@ -171,6 +172,8 @@ def make_params(p, precision="fp64", stream=None, flags=0, scale_exp=0):
     prm.scale_exp = int(scale_exp)
     prm.cuda_stream = stream
     prm.tau_g = float(p.get("tau_g", 1.0))
+    prm.component_force = (C.c_double * 3)(*[float(b) for b in p.get("component_force", (0.0, 0.0, 0.0))])
+    prm.component_force_index = int(p.get("component_force_index", 0))
     prm._keep = (sigma, tau)
     return prm
 

@@ -242,6 +242,13 @@ __device__ __forceinline__ void site_physics(const Coef<T> &cf, const T (&c)[N],
         }
     }
     Fx += cf.fb[0]; Fy += cf.fb[1];
+    if (cf.has_fc) {
+        // body force on one component, F += C_c F_c
+        T cc = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) cc += cf.fcsel[a] * c[a];
+        Fx += cc * cf.fc[0]; Fy += cc * cf.fc[1];
+    }
     T q[N - 1];
     flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll

@@ -104,6 +104,13 @@ __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N
         }
     }
     F[0] += cf.fb[0]; F[1] += cf.fb[1]; F[2] += cf.fb[2];
+    if (cf.has_fc) {
+        // body force on one component, F += C_c F_c
+        T cc = T(0);
+#pragma unroll
+        for (int a = 0; a < N; ++a) cc += cf.fcsel[a] * c[a];
+        F[0] += cc * cf.fc[0]; F[1] += cc * cf.fc[1]; F[2] += cc * cf.fc[2];
+    }
     T q[N - 1];
     flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll

@@ -209,8 +209,11 @@ __global__ void k_moments_geo(Geom g, Coef<T> cf, const SF *__restrict__ fin, co
             if (LD2Q9::ex(k)) j0 += LD2Q9::ex(k) > 0 ? fk : -fk;
             if (LD2Q9::ey(k)) j1 += LD2Q9::ey(k) > 0 ? fk : -fk;
         }
-        v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0]);
-        v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1]);
+        T cc = T(0);                      // body force on one component, F += C_c F_c
+#pragma unroll
+        for (int a = 0; a < N; ++a) cc += cf.fcsel[a] * st.c[a];
+        v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0] + cc * cf.fc[0]);
+        v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1] + cc * cf.fc[1]);
         const T w0 = T(LD2Q9::w(0));
         P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1)) * T(1.0 / (3.0 * (1.0 - LD2Q9::w(0))));
     } else if (cls != kNodeSolid) {

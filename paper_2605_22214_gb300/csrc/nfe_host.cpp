@@ -142,6 +142,9 @@ void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
     c.m = T(p.m);
     c.d34 = T(0.75 * p.D);
     for (int d = 0; d < 3; ++d) c.fb[d] = T(p.body_force[d]);
+    c.has_fc = (p.component_force[0] != 0.0 || p.component_force[1] != 0.0 || p.component_force[2] != 0.0) ? 1 : 0;
+    for (int d = 0; d < 3; ++d) c.fc[d] = T(p.component_force[d]);
+    for (int a = 0; a < N; ++a) c.fcsel[a] = T(c.has_fc && s.uidx[a] == p.component_force_index ? 1 : 0);
     const double sc = (s.prec == NFE_FP32_F16STORE) ? std::ldexp(1.0, p.scale_exp) : 1.0;
     c.fscale = T(sc);
     c.finv = T(1.0 / sc);
@@ -353,6 +356,10 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     if (!std::isfinite(p->lambda_trt)) return fail(NFE_EINVAL, "lambda_trt must be finite");
     if (!std::isnan(p->omega_stab) && !(p->omega_stab >= 0.0)) return fail(NFE_EINVAL, "omega_stab must be >= 0 or NaN");
     for (int d = 0; d < 3; ++d) if (!std::isfinite(p->body_force[d])) return fail(NFE_EINVAL, "body force must be finite");
+    for (int d = 0; d < 3; ++d) if (!std::isfinite(p->component_force[d])) return fail(NFE_EINVAL, "component force must be finite");
+    if ((p->component_force[0] != 0.0 || p->component_force[1] != 0.0 || p->component_force[2] != 0.0) &&
+        (p->component_force_index < 0 || p->component_force_index >= N))
+        return fail(NFE_EINVAL, "component_force_index out of range");
     if (p->implicit_component < 0 || p->implicit_component >= N) return fail(NFE_EINVAL, "implicit_component out of range");
     if (p->precision < NFE_FP64 || p->precision > NFE_FP32_BF16STORE) return fail(NFE_EINVAL, "unknown precision");
     if (p->flags & ~(NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI)) return fail(NFE_EINVAL, "unknown flags");

@@ -55,6 +55,9 @@ struct Coef {
     const T *r3;                  // (N-1) x mono3r_count(N), device memory: no-phi remainder, or nullptr
     int no_phi;                   // the no-phi ablation (flux potential without phi_j)
     T gomega;                     // 1 / tau_g (stored-g path, tau_g != 1)
+    int has_fc;                   // body force on one component present
+    T fc[3];                      // that force per unit volume fraction, F += C_c F_c
+    T fcsel[kMaxN];               // 1 for the internal slot of component c, 0 elsewhere
     T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 6); last member
 };
 

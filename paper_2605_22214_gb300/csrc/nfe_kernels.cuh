@@ -343,9 +343,12 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
         if (L::ey(k)) j1 += L::ey(k) > 0 ? fk : -fk;
         if (L::ez(k)) j2 += L::ez(k) > 0 ? fk : -fk;
     }
-    const T v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0]);
-    const T v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1]);
-    const T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2]);
+    T cc = T(0);                          // body force on one component, F += C_c F_c
+#pragma unroll
+    for (int a = 0; a < N; ++a) cc += cf.fcsel[a] * st.c[a];
+    const T v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0] + cc * cf.fc[0]);
+    const T v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1] + cc * cf.fc[1]);
+    const T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2] + cc * cf.fc[2]);
     const T w0 = T(L::w(0));
     const T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) * T(1.0 / (3.0 * (1.0 - L::w(0))));
 #pragma unroll

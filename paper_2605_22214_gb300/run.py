@@ -6,6 +6,7 @@ WORKLOAD is one of: spinodal (D2Q9, N = 4, size^2), janus3d (D3Q19, N = 4, size^
 lens (D2Q9, N = 3, size^2, walls in y), poiseuille3d (D3Q19, N = 7, 32 x 32 x 192),
 porous (D2Q9, N = 4, (4 size) x size channel through solid posts, inlet and outflow),
 emulsion (D2Q9, N = 4, the 600 x 140 emulsion generator),
+pals (D2Q9, N = 4, the 400 x 140 patterned liquid surface),
 batch (--sims D2Q9 lens/Janus simulations of mixed size and N in one batch, FP32;
 --mode persistent | per_step | auto).
 The time is taken with CUDA events around the steps, after three warm-up steps.
@@ -36,6 +37,8 @@ def make(name, size):
         return W.porous_channel_2d(nx=4 * size, ny=size)
     if name == "emulsion":
         return W.emulsion_2d()
+    if name == "pals":
+        return W.pals_2d()
     raise SystemExit(f"unknown workload {name}")
 
 

@@ -96,6 +96,32 @@ def test_emulsion_layout_matches_oracle_at_full_size():
         _check(o, gpu_run(p, steps, precision), precision)
 
 
+def test_pals_layout_matches_oracle_at_full_size():
+    # the 400 x 140 patterned liquid surface: edge walls, solid posts, a body force on fluid 2
+    p = W.pals_2d()
+    steps = 10
+    o = oracle_run(p, steps)
+    for precision in ("fp64", "fp32"):
+        _check(o, gpu_run(p, steps, precision), precision)
+
+
+def test_pals_droplet_moves_with_the_force_on_it():
+    # centre-of-mass velocity of fluid 2, int C_2 v_x / int C_2 (Sec. V): pushed along +x by the
+    # force on fluid 2, far above the residual velocity of the same layout without the force
+    def vcm(force):
+        p = W.pals_2d(force=force)
+        g = p["geometry"]
+        with nfe.Sim(p, "fp32") as s:
+            s.set_fields(p["C0"])
+            s.set_geometry(g["node"], g["inlets"], g["outflow"])
+            s.step(3000)
+            s.sync()
+            C, v, _ = s.fields()
+        return float((C[1] * v[0]).sum() / C[1].sum())
+    moved, rest = vcm(3e-7), vcm(0.0)
+    assert moved > 0 and moved > 20 * abs(rest)
+
+
 def test_geometry_checkpoint_restores_bit_for_bit():
     p = W.open_channel_2d(70, 36, 4)
     g = p["geometry"]

@@ -251,6 +251,20 @@ def test_tile_variants_are_bitwise_identical(precision):
             assert np.array_equal(st, states[0])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("lattice", [9, 19])
+def test_component_force_matches_oracle(precision, lattice):
+    # a body force acting on one component in proportion to its volume fraction (F += C_c F_c)
+    if lattice == 9:
+        p = W.janus_2d(nx=48, ny=40, radius=9, offset=11)
+        p["component_force"] = (3e-6, -2e-6, 0.0)
+    else:
+        p = _mixture3d(21, 13, 18, 3, 31, (False, True, False))
+        p["component_force"] = (1e-6, 2e-6, -3e-6)
+    p["component_force_index"] = 1
+    compare(p, 40, precision)
+
+
 def _mixture3d(nx, ny, nz, N, seed, walls):
     rng = np.random.default_rng(seed)
     sig = W.random_sigma(rng, N)
