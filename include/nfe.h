@@ -28,7 +28,7 @@
  *     (Sec. II, below Eq. 3).  An absent component that must stay exactly 0.0
  *     has to be an evolved one.
  *   - The library owns all device memory it allocates (cudaMalloc at create,
- *     cudaFree at destroy).  Host buffers passed in are read or written
+ *     cudaFree at destroy, or the caller's hooks in nfe_params).  Host buffers passed in are read or written
  *     during the call only and remain the caller's.
  *   - Every call returns an nfe_status; none throws, aborts or exits.
  *     nfe_last_error() gives a one-line message for the last failure on the
@@ -89,6 +89,13 @@ typedef struct {
     unsigned wall_mask;       /* NFE_WALL_* bits; NFE_WALL_Z is invalid for D2Q9 */
 } nfe_grid;
 
+/* Device memory hooks (nfe_params.device_alloc / device_free), e.g. a framework's caching
+ * allocator.  alloc returns device memory of at least `bytes` on the current GPU, aligned to
+ * 256 bytes, or NULL (the call then fails with NFE_ENOMEM); free releases a pointer that alloc
+ * returned.  Both are called on the thread that makes the library call. */
+typedef void *(*nfe_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*nfe_free_fn)(void *ptr, void *ctx);
+
 /* Physical and numerical parameters (Sec. II and Sec. III). */
 typedef struct {
     const double *sigma;      /* N x N surface tensions, row-major, symmetric,
@@ -116,6 +123,14 @@ typedef struct {
                                      volume fraction, F += C_c F_c (the PaLS study of Sec. V drives
                                      only the droplet of fluid 2); all zero = none */
     int component_force_index;    /* c, 0 .. N-1 (user order; ignored when the force is zero) */
+    nfe_alloc_fn device_alloc;    /* state, diagnostics and geometry buffers of the simulation come
+                                     from here (both NULL: cudaMalloc / cudaFree).  Buffers are
+                                     taken at nfe_create, at the first diagnostics call and at
+                                     nfe_set_geometry, and given back at nfe_destroy (after the
+                                     stream is synchronised) or when replaced.  The cuFFT plan of
+                                     nfe_domain_size and a batch's own descriptors use cudaMalloc. */
+    nfe_free_fn device_free;      /* set both or neither (NFE_EINVAL otherwise) */
+    void *alloc_ctx;              /* passed through to both */
 } nfe_params;
 
 /* Global quantities of the current state, reduced on the GPU in FP64. */

@@ -45,13 +45,19 @@ class nfe_grid(C.Structure):
                 ("wall_mask", C.c_uint)]
 
 
+# device memory hooks (nfe_alloc_fn / nfe_free_fn)
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
 class nfe_params(C.Structure):
     _fields_ = [("sigma", C.POINTER(C.c_double)), ("tau", C.POINTER(C.c_double)),
                 ("lambda_trt", C.c_double), ("m", C.c_double), ("D", C.c_double),
                 ("omega_stab", C.c_double), ("body_force", C.c_double * 3),
                 ("precision", C.c_int), ("implicit_component", C.c_int), ("flags", C.c_int),
                 ("scale_exp", C.c_int), ("cuda_stream", C.c_void_p), ("tau_g", C.c_double),
-                ("component_force", C.c_double * 3), ("component_force_index", C.c_int)]
+                ("component_force", C.c_double * 3), ("component_force_index", C.c_int),
+                ("device_alloc", ALLOC_FN), ("device_free", FREE_FN), ("alloc_ctx", C.c_void_p)]
 
 
 class nfe_diag(C.Structure):
@@ -318,10 +324,30 @@ def nfe_bulk_potential_host(sigma, C_pts, D=4.0, omega_stab=math.nan, implicit=N
     return S
 
 
+def _allocator_hooks(allocator, stream):
+    if allocator == "torch":
+        import torch
+        tstream = torch.cuda.ExternalStream(stream) if stream else None
+        dev = torch.cuda.current_device()
+
+        def alloc(nbytes):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), device=dev, stream=tstream)
+            except RuntimeError:
+                return 0
+
+        def free(ptr):
+            torch.cuda.caching_allocator_delete(ptr)
+    else:
+        alloc, free = allocator
+    return (ALLOC_FN(lambda nbytes, ctx: alloc(nbytes) or None),
+            FREE_FN(lambda ptr, ctx: free(ptr)))
+
+
 class Sim:
     """One simulation on cuda:0 (owns an nfe_sim handle)."""
 
-    def __init__(self, p, precision="fp64", stream=None, flags=0, scale_exp=0):
+    def __init__(self, p, precision="fp64", stream=None, flags=0, scale_exp=0, allocator=None):
         self.p = p
         self.N = int(p["N"])
         self.Q = int(p["lattice"])
@@ -329,6 +355,13 @@ class Sim:
         self.shape = (int(p["nz"]), int(p["ny"]), int(p["nx"]))
         self._grid = make_grid(p)
         self._params = make_params(p, precision, stream, flags, scale_exp)
+        # allocator: None (cudaMalloc), "torch" (PyTorch's caching allocator), or a pair of
+        # callables (alloc(bytes) -> int pointer or 0, free(pointer)); the callbacks live as
+        # long as this object
+        self._hooks = None
+        if allocator is not None:
+            self._hooks = _allocator_hooks(allocator, stream)
+            self._params.device_alloc, self._params.device_free = self._hooks
         self.h = nfe_create(self._grid, self.N, self._params)
 
     def set_fields(self, Cf, v=None):

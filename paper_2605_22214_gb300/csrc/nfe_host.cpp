@@ -108,6 +108,9 @@ struct nfe_sim {
     int ninlets = 0;
     size_t ghost_bytes = 0;           // one ghost buffer ((N-1) x ny), 0 without an outflow
     size_t geo_bytes = 0;             // device bytes held by the geometry
+    nfe_alloc_fn ualloc = nullptr;    // caller's device allocator (null: cudaMalloc)
+    nfe_free_fn ufree = nullptr;
+    void *uctx = nullptr;
     size_t fields_planes = 0;
     size_t device_bytes = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -158,6 +161,12 @@ void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
         for (size_t j = 0; j < s.tab.q4.size(); ++j) c.q4c[j] = T(s.tab.q4[j]);
 }
 
+void dev_free(nfe_sim *s, void *p) {
+    if (!p) return;
+    if (s->ufree) s->ufree(p, s->uctx);
+    else cudaFree(p);
+}
+
 nfe_status free_all(nfe_sim *s) {
     for (auto &g : s->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
     for (auto &t : s->timed) { s->event_pool.push_back(t.a); s->event_pool.push_back(t.b); }
@@ -168,7 +177,7 @@ nfe_status free_all(nfe_sim *s) {
                     s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev,
                     s->buf.g[0], s->buf.g[1], s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1],
                     s->buf.opart};
-    for (void *p : ptrs) if (p) cudaFree(p);
+    for (void *p : ptrs) dev_free(s, p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
     s->r3dev = nullptr;
@@ -182,6 +191,17 @@ nfe_status free_all(nfe_sim *s) {
 }
 
 nfe_status dev_alloc(nfe_sim *s, void **p, size_t bytes) {
+    if (s->ualloc) {
+        *p = s->ualloc(bytes, s->uctx);
+        if (!*p) return fail(NFE_ENOMEM, "device_alloc returned NULL for %zu bytes", bytes);
+        if (reinterpret_cast<uintptr_t>(*p) % 256 != 0) {
+            s->ufree(*p, s->uctx);
+            *p = nullptr;
+            return fail(NFE_ENOMEM, "device_alloc returned memory not aligned to 256 bytes");
+        }
+        s->device_bytes += bytes;
+        return NFE_OK;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         *p = nullptr;
@@ -286,7 +306,7 @@ size_t state_size(const nfe_sim *s) {
 
 void geo_free(nfe_sim *s) {
     void *ptrs[] = {s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1], s->buf.opart};
-    for (void *p : ptrs) if (p) cudaFree(p);
+    for (void *p : ptrs) dev_free(s, p);
     s->buf.opart = nullptr;
     s->device_bytes -= s->geo_bytes;
     s->geo_bytes = 0;
@@ -373,8 +393,13 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     if (p->precision == NFE_FP32_F16STORE && (p->scale_exp < -20 || p->scale_exp > 20))
         return fail(NFE_EINVAL, "scale_exp outside -20..20");
 
+    if ((p->device_alloc == nullptr) != (p->device_free == nullptr))
+        return fail(NFE_EINVAL, "set both device_alloc and device_free, or neither");
     nfe_sim *s = new (std::nothrow) nfe_sim();
     if (!s) return fail(NFE_ENOMEM, "host allocation failed");
+    s->ualloc = p->device_alloc;
+    s->ufree = p->device_free;
+    s->uctx = p->alloc_ctx;
     s->grid = *grid;
     s->N = N;
     s->prec = p->precision;

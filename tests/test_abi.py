@@ -150,3 +150,31 @@ def test_library_tables_match_oracle(N, omega, imp):
     absent = ev[-1]
     pts0 = W.random_simplex_points(rng, N, 50, absent=absent)
     assert (nfe.nfe_bulk_potential_host(sig, pts0, omega_stab=omega, implicit=imp)[:, absent] == 0.0).all()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # sizes and field offsets of every public struct, from the C compiler against the ctypes mirror
+    import ctypes
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"nfe_grid": nfe.nfe_grid, "nfe_params": nfe.nfe_params, "nfe_diag": nfe.nfe_diag,
+               "nfe_info": nfe.nfe_info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "nfe.h"', 'int main(void) {']
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    subprocess.run(["gcc", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                      text=True).stdout.splitlines())
+    for name, cls in structs.items():
+        assert int(got[name]) == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert int(got[f"{name}.{field}"]) == getattr(cls, field).offset, (name, field)
