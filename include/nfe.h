@@ -193,8 +193,9 @@ nfe_status nfe_sync(nfe_sim *sim);
 nfe_status nfe_fields(nfe_sim *sim, double *C, double *v, double *P);
 
 /* Copy the populations f_k, k = 1 .. Q-1, to a host FP64 buffer ((Q-1) x n),
- * in the velocity order of Eqs. 20-21 (D2Q9) or the D3Q19 order documented
- * in the design doc.  f_0 is not kept: it feeds no moment.  Synchronises. */
+ * in the velocity order of Eqs. 20-21 (D2Q9) or, for D3Q19, +x, -x, +y, -y, +z, -z,
+ * then the xy, xz and yz diagonals, each as (+,+), (-,-), (+,-), (-,+) (the opposite of
+ * an odd k is k + 1).  f_0 is not kept: it feeds no moment.  Synchronises. */
 nfe_status nfe_populations(nfe_sim *sim, double *f);
 
 /* FP64 reductions of the current state on the GPU.  Synchronises. */

@@ -34,9 +34,8 @@ outflow Convective condition on the last column x = nx - 1 (the convective bound
         column N and is solid where column N is.  Column 0 must hold no fluid node, column
         nx - 1 no inlet node, and the x axis no edge wall.
 
-Readings: every choice above that the paper leaves open (rho_b, the sign, the composition
-inlet, U without F/2, the ghost's start and class) is listed with the others in the design
-notes.
+Every choice above that the paper leaves open (rho_b, the sign, the composition inlet, U
+without F/2, the ghost's start and class) is a reading of Sec. III C, stated where it is made.
 """
 from __future__ import annotations
 

@@ -19,7 +19,7 @@ order below (Sec. III; the paper spreads the order over its subsections):
   7. Streaming of both, halfway bounce-back at walls (Eqs. 44-45), periodic
      wrap on the other edges.
 
-Readings (listed in the design doc): rho_i = 1, so rho = 1 and grad rho = 0 and
+Readings: rho_i = 1, so rho = 1 and grad rho = 0 and
 the grad-rho terms of Eqs. 30 and 38 vanish; g^eq of Eq. 40 is read as
 C_i (delta_k0 + s_k(v)) -/+ (m S_i terms) (see `g_equilibrium`); f^eq_0 is taken as P/c_s^2 (w_0 - 1) + s_0(v)
 (f_0 feeds no moment, so this choice changes no other value; `feq0_sign`

@@ -3,7 +3,7 @@
 Oracle code (test infrastructure only).  Components are indexed 0 .. N-1
 here; the paper counts 1 .. N.  All arithmetic is float64.
 
-Readings taken where the paper leaves a choice (each is listed in the design doc):
+Readings taken where the paper leaves a choice:
   * beta_ij = 6 sigma_ij / D and kappa_ij = 3 D sigma_ij / 4, the unique
     solution of D = sqrt(8 kappa / beta) and sigma = sqrt(2 kappa beta / 9)
     (Sec. II, after Eq. 5).
