@@ -55,7 +55,7 @@ typedef enum {
     NFE_ESINGULAR = 4,     /* the alpha, Lambda or Theta system (Eqs. 8-19) has no unique solution */
     NFE_ENONFINITE = 5,    /* a kernel produced a NaN or Inf volume fraction */
     NFE_ETIMEOUT = 6,      /* a device-side wait of the batched kernel ran out of spins */
-    NFE_EUNSUPPORTED = 7   /* a valid combination this build does not implement */
+    NFE_EUNSUPPORTED = 7   /* a valid combination the library does not implement */
 } nfe_status;
 
 enum { NFE_D2Q9 = 9, NFE_D3Q19 = 19 };
