@@ -10,7 +10,8 @@ from oracle import lbm
 
 
 @pytest.mark.parametrize("make", [lambda: W.open_channel_2d(), lambda: W.open_channel_2d(outflow=False),
-                                  lambda: W.emulsion_2d(), lambda: W.porous_channel_2d(nx=256, ny=64)])
+                                  lambda: W.emulsion_2d(), lambda: W.porous_channel_2d(nx=256, ny=64),
+                                  lambda: W.pals_2d()])
 def test_layouts_are_valid_geometries(make):
     p = make()
     g = p["geometry"]
@@ -19,6 +20,7 @@ def test_layouts_are_valid_geometries(make):
     assert np.allclose(g["inlets"][:, 2:].sum(axis=1), 1.0)
     assert np.allclose(p["C0"].sum(axis=0), 1.0)
     assert geo.fluid.sum() > 0.5 * geo.fluid.size or p["name"].startswith("emulsion")
+    assert p["C0"].min() >= 0.0
 
 
 def test_emulsion_generator_dimensions():
