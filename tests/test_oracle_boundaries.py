@@ -138,3 +138,28 @@ def test_geometry_validation():
     with pytest.raises(ValueError):
         B.Geometry(prm, node)                               # inlet class without a table row
     B.Geometry(prm, node, [[0.0, 0.0, 1.0, 0.0]], outflow=True)
+
+
+def test_inlet_injects_its_composition_at_the_inflow_rate():
+    # reading of the volume-fraction inlet: links from the inlet carry the equilibrium of the
+    # prescribed state, so a channel fed at (u, 0) with C_b gains C_b u H of the inlet component
+    # per step (H rows) once the first transient has passed; the printed anti-bounce-back would
+    # carry in only the interior's own composition (no gain here)
+    N, nx, ny, u = 2, 40, 6, 0.02
+    sig = np.array([[0.0, 0.005], [0.005, 0.0]])
+    prm = lbm.Params(W.base_params(W.D2Q9, nx, ny, 1, N, sig, 0.8))
+    node = np.zeros((1, ny, nx), int)
+    node[..., 0] = B.INLET0
+    rates = []
+    for cb in (1.0, 0.4):
+        geo = B.Geometry(prm, node, [[u, 0.0, 1.0 - cb, cb]], outflow=True)
+        C0 = np.zeros((N, 1, ny, nx))
+        C0[0] = 1.0
+        v0 = np.zeros((3, 1, ny, nx))
+        v0[0] = u
+        st = B.run(prm, geo, B.init_state(prm, geo, C0, v0), 100)
+        m0 = B.fields(prm, geo, st)[0][1][geo.fluid].sum()
+        st = B.run(prm, geo, st, 150)
+        m1 = B.fields(prm, geo, st)[0][1][geo.fluid].sum()
+        rates.append((m1 - m0) / 150 / (u * ny * cb))
+    assert all(0.9 < r < 1.05 for r in rates), rates
