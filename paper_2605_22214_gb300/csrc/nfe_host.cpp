@@ -728,7 +728,6 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
     }
     geo_free(s);
     const size_t ce = s->ops->c_elem_bytes;
-    if ((st = ensure_fields(s)) != NFE_OK) return st;
     if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->node_dev), n)) != NFE_OK) return st;
     if ((st = dev_alloc(s, &s->inl_dev, size_t(std::max(ninlets, 1)) * 2 * N * ce)) != NFE_OK) { geo_free(s); return st; }
     if (outflow) {
@@ -745,14 +744,22 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
     s->buf.outflow = outflow ? 1 : 0;
     s->ninlets = ninlets;
     cudaError_t e = cudaMemcpyAsync(s->node_dev, node, n, cudaMemcpyHostToDevice, s->stream);
-    // the FP64 rows go through the fields scratch (n >= 1 doubles per plane, at least N + 7 planes)
+    // the FP64 rows go through a small temporary device buffer
+    void *rows_dev = nullptr;
     if (e == cudaSuccess && ninlets > 0) {
-        if (rows.size() > s->fields_planes * n) { geo_free(s); return fail(NFE_EINVAL, "inlet table larger than the grid scratch"); }
-        e = cudaMemcpyAsync(s->buf.fields, rows.data(), rows.size() * sizeof(double), cudaMemcpyHostToDevice, s->stream);
-        if (e == cudaSuccess) e = s->ops->inlet_table(s->coef, s->buf.fields, ninlets, s->inl_dev, s->stream);
+        const size_t rb = rows.size() * sizeof(double);
+        if ((st = dev_alloc(s, &rows_dev, rb)) != NFE_OK) { geo_free(s); return st; }
+        e = cudaMemcpyAsync(rows_dev, rows.data(), rb, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess)
+            e = s->ops->inlet_table(s->coef, static_cast<const double *>(rows_dev), ninlets, s->inl_dev, s->stream);
     }
     if (e == cudaSuccess) e = s->ops->geo_prepare(s->geom, s->buf, s->buf.cur, ninlets, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (rows_dev) {
+        cudaStreamSynchronize(s->stream);
+        dev_free(s, rows_dev);
+        s->device_bytes -= rows.size() * sizeof(double);
+    }
     if (e != cudaSuccess) { geo_free(s); return cuda_fail(e, "nfe_set_geometry"); }
     return NFE_OK;
 }
