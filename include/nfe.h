@@ -240,7 +240,10 @@ nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, do
  *   inlet nodes.  With outflow the raw state (nfe_get_state) also holds the ghost column,
  *   so set the geometry before restoring a state.
  * Errors: NFE_EUNSUPPORTED for D3Q19, tau_g != 1 or NFE_NO_PHI; NFE_EINVAL for a class
- *   outside 0 .. 1 + ninlets, a bad inlet row or a violated outflow condition; NFE_ENOMEM.
+ *   outside 0 .. 1 + ninlets, a bad inlet row or a violated outflow condition (these leave
+ *   the previous geometry in place); NFE_ENOMEM or NFE_ECUDA while the new geometry is being
+ *   uploaded, after which the simulation has no geometry (fully periodic / edge walls only)
+ *   and the caller sets one again.
  * Synchronises the stream. */
 nfe_status nfe_set_geometry(nfe_sim *sim, const uint8_t *node, int ninlets, const double *inlets, int outflow);
 
@@ -355,9 +358,11 @@ void nfe_batch_destroy(nfe_batch *b);
  * first call on each device
  * looks up the array's device address with that device current; make that
  * first call before any stream capture.
- * Errors: NFE_EINVAL when nplanes is outside 1..NFE_STATS_MAX_PLANES, n < 1
- * or a pointer is NULL (nothing is launched); NFE_ECUDA when the address
- * lookup or a launch fails.  The message is in nfe_last_error(). */
+ * A plane holding a NaN reports NaN as its sums, its largest absolute value
+ * and its smallest value.
+ * Errors: NFE_EINVAL when nplanes is outside 1..NFE_STATS_MAX_PLANES, n is
+ * outside 1..2^40 or a pointer is NULL (nothing is launched); NFE_ECUDA when
+ * the address lookup or a launch fails.  The message is in nfe_last_error(). */
 #define NFE_STATS_MAX_PLANES 16
 nfe_status nfe_field_stats_static(int nplanes, int64_t n, const double *d_planes, double *d_out,
                                   void *cuda_stream);

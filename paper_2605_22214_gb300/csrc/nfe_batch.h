@@ -1,6 +1,8 @@
 // Internal interface of the batched persistent kernel (nfe_batch.cu) and its host side.
 #pragma once
 
+#include <stddef.h>
+
 #include "nfe_internal.h"
 
 #define NFE_BATCH_ERR_TIMEOUT 1
@@ -23,14 +25,18 @@ struct __align__(16) BatchSim {
     Coef<T> coef;
 };
 
-// Grid-barrier state (device memory): arrival count, generation, error word.
+// Grid-barrier state (device memory): arrival count, generation, work-item ticket, error word.
+// Every launch resets the words before `error` (kBatchSyncResetBytes); the error word is sticky:
+// a barrier timeout stays recorded through later launches (whose barriers then release at once,
+// so they do no work) until nfe_batch_sync reports and clears it.
 struct BatchSync {
     unsigned count;
     unsigned generation;
+    unsigned long long ticket;   // work-item counter of the persistent kernel
     int error;
     int pad_;
-    unsigned long long ticket;   // work-item counter of the persistent kernel
 };
+constexpr size_t kBatchSyncResetBytes = offsetof(BatchSync, error);
 
 struct BatchLaunch {
     const void *sims;       // BatchSim<T>[nsims]

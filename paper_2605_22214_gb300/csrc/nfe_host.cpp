@@ -984,6 +984,13 @@ BatchLaunch batch_launch_args(const nfe_batch *b, int64_t nsteps, long long spin
 // other one, so the state is untouched.
 nfe_status batch_autotune(nfe_batch *b) {
     if (b->variant >= 0) return NFE_OK;
+    {
+        // a timeout still to be reported by nfe_batch_sync: the trial launches would clear it
+        BatchSync sync;
+        CK(cudaStreamSynchronize(b->stream));
+        CK(cudaMemcpy(&sync, b->d_sync, sizeof sync, cudaMemcpyDeviceToHost));
+        if (sync.error) return fail(NFE_ETIMEOUT, "a grid-barrier wait of the batched kernel ran out of spins");
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1154,7 +1161,7 @@ nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
     if (b->spin_next > 0 || b->extra_next > 0) {
         // fault-injection launch (direct, not captured)
         BatchLaunch L = batch_launch_args(b, nsteps, b->spin_next > 0 ? b->spin_next : b->spin_default, b->extra_next);
-        CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+        CK(cudaMemsetAsync(b->d_sync, 0, kBatchSyncResetBytes, b->stream));
         CK(b->ops->persistent[v](L, b->stream));
         b->spin_next = 0;
         b->extra_next = 0;
@@ -1168,7 +1175,7 @@ nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
             const BatchLauncher launch = b->form == NFE_BATCH_PER_STEP ? b->ops->per_step[v] : b->ops->persistent[v];
             cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
             if (e == cudaSuccess) {
-                cudaError_t e1 = cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream);
+                cudaError_t e1 = cudaMemsetAsync(b->d_sync, 0, kBatchSyncResetBytes, b->stream);
                 cudaError_t e2 = e1 == cudaSuccess ? launch(L, b->stream) : e1;
                 e = cudaStreamEndCapture(b->stream, &g);
                 if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
@@ -1186,7 +1193,7 @@ nfe_status nfe_batch_step(nfe_batch *b, int64_t nsteps) {
             CK(cudaGraphLaunch(it->second, b->stream));
         } else {
             BatchLaunch L = batch_launch_args(b, nsteps, b->spin_default, 0);
-            CK(cudaMemsetAsync(b->d_sync, 0, sizeof(BatchSync), b->stream));
+            CK(cudaMemsetAsync(b->d_sync, 0, kBatchSyncResetBytes, b->stream));
             CK((b->form == NFE_BATCH_PER_STEP ? b->ops->per_step[v] : b->ops->persistent[v])(L, b->stream));
         }
     }
@@ -1203,7 +1210,11 @@ nfe_status nfe_batch_sync(nfe_batch *b) {
     CK(cudaStreamSynchronize(b->stream));
     BatchSync sync;
     CK(cudaMemcpy(&sync, b->d_sync, sizeof sync, cudaMemcpyDeviceToHost));
-    if (sync.error) return fail(NFE_ETIMEOUT, "a grid-barrier wait of the batched kernel ran out of spins");
+    if (sync.error) {
+        // reported once: the error word is cleared, the state stays undefined until set_fields
+        CK(cudaMemset(&b->d_sync->error, 0, sizeof(int)));
+        return fail(NFE_ETIMEOUT, "a grid-barrier wait of the batched kernel ran out of spins");
+    }
     for (int i = 0; i < b->nsims; ++i) {
         int flag = 0;
         CK(cudaMemcpy(&flag, b->sims[i]->buf.flag, sizeof(int), cudaMemcpyDeviceToHost));

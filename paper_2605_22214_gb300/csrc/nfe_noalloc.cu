@@ -26,6 +26,11 @@ constexpr int kStatPer = 4;                      // sum, sum |.|, max |.|, min
 // 512 blocks x 16 planes x 4 values x 8 bytes = 256 KiB
 __device__ __align__(256) double g_stat_scratch[kStatBlocks * kStatMaxPlanes * kStatPer];
 
+// Largest / smallest value that lets a NaN through (fmax and fmin would drop it), so that a
+// field holding a NaN reports NaN as its largest magnitude and its minimum.
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
+__device__ __forceinline__ double nan_min(double a, double b) { return (a != a || b != b) ? NAN : fmin(a, b); }
+
 __device__ __forceinline__ void stat_reduce(double (&v)[kStatPer], double *sh) {
     const int t = threadIdx.x;
     for (int j = 0; j < kStatPer; ++j) sh[j * blockDim.x + t] = v[j];
@@ -34,8 +39,8 @@ __device__ __forceinline__ void stat_reduce(double (&v)[kStatPer], double *sh) {
         if (t < o) {
             sh[0 * blockDim.x + t] += sh[0 * blockDim.x + t + o];
             sh[1 * blockDim.x + t] += sh[1 * blockDim.x + t + o];
-            sh[2 * blockDim.x + t] = fmax(sh[2 * blockDim.x + t], sh[2 * blockDim.x + t + o]);
-            sh[3 * blockDim.x + t] = fmin(sh[3 * blockDim.x + t], sh[3 * blockDim.x + t + o]);
+            sh[2 * blockDim.x + t] = nan_max(sh[2 * blockDim.x + t], sh[2 * blockDim.x + t + o]);
+            sh[3 * blockDim.x + t] = nan_min(sh[3 * blockDim.x + t], sh[3 * blockDim.x + t + o]);
         }
         __syncthreads();
     }
@@ -53,8 +58,8 @@ __global__ void k_stats_partial(int nplanes, long long n, const double *__restri
             const double x = planes[size_t(p) * n + s];
             v[0] += x;
             v[1] += fabs(x);
-            v[2] = fmax(v[2], fabs(x));
-            v[3] = fmin(v[3], x);
+            v[2] = nan_max(v[2], fabs(x));
+            v[3] = nan_min(v[3], x);
         }
         stat_reduce(v, sh);
         if (threadIdx.x == 0)
@@ -71,8 +76,8 @@ __global__ void k_stats_final(int nplanes, int nblocks, const double *__restrict
             const double *q = scratch + (size_t(b) * kStatMaxPlanes + p) * kStatPer;
             v[0] += q[0];
             v[1] += q[1];
-            v[2] = fmax(v[2], q[2]);
-            v[3] = fmin(v[3], q[3]);
+            v[2] = nan_max(v[2], q[2]);
+            v[3] = nan_min(v[3], q[3]);
         }
         stat_reduce(v, sh);
         if (threadIdx.x == 0)
@@ -93,7 +98,7 @@ extern "C" nfe_status nfe_field_stats_static(int nplanes, int64_t n, const doubl
                                              void *cuda_stream) {
     if (nplanes < 1 || nplanes > kStatMaxPlanes)
         return set_error(NFE_EINVAL, "nfe_field_stats_static: nplanes must be 1..16 (the static scratch holds 16 planes)");
-    if (n < 1 || n > (int64_t(1) << 40)) return set_error(NFE_EINVAL, "nfe_field_stats_static: n must be >= 1");
+    if (n < 1 || n > (int64_t(1) << 40)) return set_error(NFE_EINVAL, "nfe_field_stats_static: n must be 1..2^40");
     if (!d_planes || !d_out) return set_error(NFE_EINVAL, "nfe_field_stats_static: NULL pointer");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {

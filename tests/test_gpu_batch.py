@@ -1,12 +1,13 @@
-"""The batched persistent kernel against the single-simulation path, and its
+"""The batched sweep against the FP64 oracle and against the single-simulation path, and its
 bounded grid barrier (a wait that runs out is reported, the GPU stays usable)."""
 import numpy as np
 import pytest
 
 import nfe_workloads as W
 import paper_2605_22214_gb300 as nfe
+from oracle import lbm
 
-from ._lib import lib
+from ._lib import lib, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +62,53 @@ def test_batch_matches_single_simulations(precision, mode):
         assert info["nsims"] == len(sims) and info["tile_x"] == 32
 
 
+def _oracle_members():
+    # N = 2..5, ragged sizes (not multiples of the 32 x TY tile), walls in y on two members,
+    # TRT with unequal tau, a body force, and Omega != 0 (the stabiliser of Eq. 17) on two members
+    a = _mixture(37, 21, 2, 21)
+    b = _mixture(45, 34, 3, 22)
+    b["omega_stab"] = 1.0 / 90.0
+    c = _mixture(29, 41, 4, 23)
+    c["body_force"] = (2e-6, -1e-6, 0.0)
+    d = _mixture(50, 19, 5, 24)
+    d["omega_stab"] = 1.0 / 90.0
+    e = W.lens_2d(nx=35, ny=30, radius=7)
+    return [a, b, c, d, e]
+
+
+@pytest.fixture(scope="module")
+def oracle_members():
+    sims = _oracle_members()
+    out = []
+    for p in sims:
+        prm = lbm.Params(p)
+        st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), 41, flux_form="factored")
+        C, v, P, _ = lbm.fields(prm, st, flux_form="factored")
+        out.append(dict(C=C, v=v, P=P))
+    return sims, out
+
+
+@pytest.mark.parametrize("precision,tol_c,tol_v", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)])
+@pytest.mark.parametrize("mode", [nfe.NFE_BATCH_PERSISTENT, nfe.NFE_BATCH_PER_STEP])
+def test_batch_members_match_oracle(oracle_members, precision, tol_c, tol_v, mode):
+    # every member of one batch (its own tile code: L2-only loads, the descriptor in shared memory,
+    # quartic coefficients from device memory) element by element against the FP64 oracle
+    sims, ref = oracle_members
+    with nfe.Batch(sims, precision) as b:
+        b.set_mode(mode)
+        for i, p in enumerate(sims):
+            b.set_fields(i, p["C0"])
+        b.step(17)
+        b.step(24)
+        b.sync()
+        for i, o in enumerate(ref):
+            Cb, vb, Pb = b.fields(i)
+            errs = dict(C=rel(Cb, o["C"]), v=rel(vb, o["v"]), P=rel(Pb, o["P"]))
+            assert errs["C"] <= tol_c, (i, errs)
+            assert errs["v"] <= tol_v and errs["P"] <= tol_v, (i, errs)
+            assert b.diagnostics(i)["step"] == 41
+
+
 def test_set_fields_after_odd_steps_and_absent_component():
     sims = _sims()[:3]
     q = sims[0]
@@ -97,9 +145,11 @@ def test_barrier_timeout_is_reported_and_gpu_stays_usable():
         b.set_mode(nfe.NFE_BATCH_PERSISTENT)
         b.set_barrier_test(20000, 1)
         b.step(4)
+        b.step(2)          # an ordinary launch queued behind it keeps the timeout recorded
         with pytest.raises(nfe.NfeError) as e:
             b.sync()
         assert e.value.status == 6
+        b.sync()           # reported once
         # the context is still usable: reset and step normally
         for i, p in enumerate(sims):
             b.set_fields(i, p["C0"])

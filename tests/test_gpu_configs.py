@@ -20,10 +20,8 @@ def _built():
 
 
 def test_lens_c1_parity_and_neumann_angle():
-    # 64 x 64 lens, FP64, 2000 steps: GPU vs oracle fields, and the lens angle of both against
-    # each other (1 %) and against the Neumann triangle of Eq. 51 (102.64 deg; the 64^2 grid with a
-    # radius-12 lens and 2000 steps is far from the paper's converged 300 x 150 runs, so the
-    # theory check is loose).
+    # 64 x 64 lens, FP64, 2000 steps (the c1 length): GPU vs oracle fields and the lens angle of
+    # both (1 %); then the GPU run continued to equilibrium against the Neumann triangle of Eq. 51.
     p = W.lens_2d()
     steps = 2000
     prm = lbm.Params(p)
@@ -41,33 +39,90 @@ def test_lens_c1_parity_and_neumann_angle():
     print(f"lens c1: GPU angle {ang_g:.2f}, oracle {ang_o:.2f}, theory {theory:.2f}, "
           f"rel C {rel(Cg, Co):.2e}, rel v {rel(vg, vo):.2e}")
     assert abs(ang_g - ang_o) / ang_o < 0.01
-    assert abs(ang_g - theory) < 15.0
+    # after 2000 steps the lens is still relaxing (GPU and oracle agree on 114.1 deg); continued to
+    # 1e5 steps the 64^2 lens settles at 102.61 deg against 102.64 deg from Eq. 51 (the paper's
+    # Table 1 agrees within 1 deg)
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(p["C0"])
+        s.step(100000)
+        C, _, _ = s.fields()
+    ang = observables.lens_angle(C[2, 0])
+    print(f"lens c1 after 1e5 steps: GPU angle {ang:.3f}, theory {theory:.3f}")
+    assert abs(ang - theory) < 0.5
+
+
+@pytest.fixture(scope="module")
+def spinodal_c2_oracle_100():
+    # the oracle on the full 512 x 512 c2 input, 100 steps (shared by the FP64 and FP32 cases)
+    p = W.spinodal_2d()
+    prm = lbm.Params(p)
+    st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), 100, flux_form="factored")
+    C, v, P, _ = lbm.fields(prm, st, flux_form="factored")
+    return p, dict(C=C, v=v, P=P, f=st.f[1:], diag=lbm.diagnostics(prm, st, flux_form="factored"))
+
+
+@pytest.mark.parametrize("precision,tol_c,tol_f", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)])
+def test_spinodal_c2_full_size_parity_100_steps(spinodal_c2_oracle_100, precision, tol_c, tol_f):
+    # c2 at its full size (512 x 512, N = 4) element by element after 100 steps: FP64 within
+    # 1e-12 and FP32 within 1e-5 of the oracle (C), the populations, v and P relative to their
+    # own largest values, and every global sum of nfe_diagnostics.
+    from .test_gpu_parity import compare_diagnostics
+    p, o = spinodal_c2_oracle_100
+    with nfe.Sim(p, precision) as s:
+        s.set_fields(p["C0"])
+        s.step(100)
+        C, v, P = s.fields()
+        f = s.populations()
+        d = s.diagnostics()
+    errs = dict(C=rel(C, o["C"]), f=rel(f, o["f"]), v=rel(v, o["v"]), P=rel(P, o["P"]))
+    print(f"spinodal c2 512^2 {precision}, 100 steps: {errs}")
+    assert errs["C"] <= tol_c, errs
+    assert max(errs["f"], errs["v"], errs["P"]) <= tol_f, errs
+    compare_diagnostics(d, o["diag"], precision, 512 * 512)
+
+
+# Bound on the relative change of any component's mass after t FP32 c2 steps, divided by t.  The
+# FP32 update keeps every link's two contributions exactly opposite, but the final C + dC is
+# rounded to FP32; where dC is below half an ulp of C (the bulk of the nearly pure domains, whose
+# composition creeps towards its equilibrium value with one sign) the increment is dropped, so
+# the loss has a sign instead of averaging out.  Measured over the 20000 steps: at most 1.05e-9
+# per step (in the first steps, while the mixture separates), 4.4e-6 in total after 20000 steps.
+FP32_MASS_DRIFT_PER_STEP = 2e-9
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_spinodal_c2_conservation_over_long_run(precision):
-    # 512 x 512, N = 4: per-component mass constant and no momentum from the surface-tension
-    # force (Eq. 34 sums to zero on a periodic grid), checked every 100 steps over 5000 steps.
-    # FP64: round-off only (1e-12 overall).  FP32: the update is written so that every link's
-    # contributions cancel exactly, which leaves the rounding of C + dC to FP32; near C = 1/4
-    # (the spinodal mean, a binade edge) it drifts by about 1e-9 of the mass per step; the
-    # bound below is 1e-8 per step.
+def test_spinodal_c2_conservation_every_step_20000(precision):
+    # c2 (512 x 512, N = 4) for its full 20000 steps, with per-component mass and total momentum
+    # checked after every step.  FP64: mass to 1e-12 relative; the surface-tension force sums to
+    # zero (Eq. 34 on a periodic grid: |sum F_s| <= 1e-13 sum |F_s|) and the total momentum stays at
+    # round-off.  FP32 (FP64 reductions): the force sums to zero within FP32 rounding of the link
+    # fluxes (1e-5 of sum |F_s|); mass within the stated drift per step.
     p = W.spinodal_2d()
+    steps = 20000
     with nfe.Sim(p, precision) as s:
         s.set_fields(p["C0"])
         d0 = s.diagnostics()
-        for it in range(1, 51):
-            s.step(100)
+        worst_m = worst_f = worst_p = 0.0
+        for t in range(1, steps + 1):
+            s.step(1)
             d = s.diagnostics()
-            tol_m = 1e-12 if precision == "fp64" else 1e-8 * 100 * it
-            np.testing.assert_allclose(d["mass"], d0["mass"], rtol=tol_m)
+            assert d["step"] == t and d["nonfinite"] == 0
+            dm = np.abs(d["mass"] - d0["mass"]).max() / d0["mass"].max()
             fabs = d["force_abs_sum"].sum()
-            assert np.abs(d["force_sum"]).max() <= (1e-13 if precision == "fp64" else 1e-5) * fabs
-            assert np.abs(d["momentum"]).max() <= (1e-12 if precision == "fp64" else 1e-4) * max(fabs, 1e-30) * 100
-            assert d["nonfinite"] == 0
-        drift = np.abs(d["mass"] - d0["mass"]).max() / d0["mass"].max() / 5000
-        print(f"spinodal c2 {precision}: mass drift per step {drift:.2e}, |sum F_s| / sum|F_s| "
-              f"{np.abs(d['force_sum']).max() / d['force_abs_sum'].sum():.2e}")
+            rf = np.abs(d["force_sum"]).max() / fabs
+            rp = np.abs(d["momentum"]).max() / fabs
+            worst_m, worst_f, worst_p = max(worst_m, dm / t), max(worst_f, rf), max(worst_p, rp)
+            if precision == "fp64":
+                assert dm <= 1e-12, (t, dm)
+                assert rf <= 1e-13, (t, rf)
+                assert rp <= 1e-11, (t, rp)
+            else:
+                assert dm <= FP32_MASS_DRIFT_PER_STEP * t, (t, dm)
+                assert rf <= 1e-5, (t, rf)
+                assert rp <= 1e-3, (t, rp)
+    print(f"spinodal c2 {precision}, {steps} steps: worst mass drift per step {worst_m:.2e}, "
+          f"|sum F_s| / sum |F_s| {worst_f:.2e}, |sum v| / sum |F_s| {worst_p:.2e}, "
+          f"final mass change {np.abs(d['mass'] - d0['mass']).max() / d0['mass'].max():.2e}")
 
 
 def test_spinodal_c2_parity_window_fp64():
@@ -93,33 +148,87 @@ def _poiseuille_column(nz=192):
     return W.layered_poiseuille(nx=2, ny=2, nz=nz)
 
 
-def test_poiseuille_c3_parity_with_oracle():
+@pytest.fixture(scope="module")
+def poiseuille_column_oracle():
     p = _poiseuille_column()
-    steps = 1000
     prm = lbm.Params(p)
-    st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), steps, flux_form="factored")
-    Co, vo, Po, _ = lbm.fields(prm, st, flux_form="factored")
-    for precision, tol in (("fp64", 1e-10), ("fp32", 1e-4)):
+    st = lbm.init_state(prm, p["C0"], flux_form="factored")
+    out = {}
+    t = 0
+    for target in (100, 1000):
+        st = lbm.run(prm, st, target - t, flux_form="factored")
+        t = target
+        C, v, P, _ = lbm.fields(prm, st, flux_form="factored")
+        out[target] = dict(C=C, v=v, P=P)
+    return out
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_poiseuille_c3_parity_100_steps_full_size(poiseuille_column_oracle, precision, tol):
+    # c3 after 100 steps: the layered flow depends on z only, so every (x, y) column of the full
+    # 32 x 32 x 192 run equals the oracle's 2 x 2 x 192 column; FP64 within 1e-12 and FP32 within
+    # 1e-5 (C and v relative to their largest values), seventh component exactly 0.0.
+    o = poiseuille_column_oracle[100]
+    p = W.layered_poiseuille()
+    with nfe.Sim(p, precision) as s:
+        s.set_fields(p["C0"])
+        s.step(100)
+        Cg, vg, Pg = s.fields()
+    Co = np.broadcast_to(o["C"][:, :, :1, :1], Cg.shape)
+    vo = np.broadcast_to(o["v"][:, :, :1, :1], vg.shape)
+    Po = np.broadcast_to(o["P"][:, :1, :1], Pg.shape)
+    errs = dict(C=rel(Cg, Co), vx=rel(vg[0], vo[0]), v=rel(vg, vo), P=rel(Pg, Po))
+    print(f"poiseuille c3 32x32x192 {precision}, 100 steps: {errs}")
+    assert errs["C"] < tol and errs["vx"] < tol, errs
+    assert errs["P"] < (1e-10 if precision == "fp64" else 1e-3), errs
+    assert (Cg[6] == 0.0).all()
+
+
+def test_poiseuille_c3_parity_1000_steps_column(poiseuille_column_oracle):
+    # 1000 steps on the column.  FP64 within 1e-12.  FP32: the velocity grows from zero under the
+    # body force and its relative error grows with the number of FP32 roundings of the populations
+    # (about 1e-7 of |f| per step, so about 1e-4 of the still small v after 1000 steps).
+    o = poiseuille_column_oracle[1000]
+    p = _poiseuille_column()
+    for precision, tol_c, tol_v in (("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-4)):
         with nfe.Sim(p, precision) as s:
             s.set_fields(p["C0"])
-            s.step(steps)
+            s.step(1000)
             Cg, vg, Pg = s.fields()
-        print(f"poiseuille c3 column {precision}: rel C {rel(Cg, Co):.2e} rel vx {rel(vg[0], vo[0]):.2e}")
-        assert rel(Cg, Co) < tol
-        assert rel(vg[0], vo[0]) < tol
+        print(f"poiseuille c3 column {precision}, 1000 steps: rel C {rel(Cg, o['C']):.2e} "
+              f"rel vx {rel(vg[0], o['v'][0]):.2e}")
+        assert rel(Cg, o["C"]) < tol_c
+        assert rel(vg[0], o["v"][0]) < tol_v
         assert (Cg[6] == 0.0).all()          # the absent seventh component
 
 
-def test_poiseuille_c3_full_size_against_analytic_profile():
-    # 32 x 32 x 192 (FP32): after 2e5 steps the centre profile matches the piecewise parabola of
-    # Eq. 56 with eta_i v'' = -F (the physical sign) within 2 % of its maximum; the seventh
-    # component stays exactly zero; every column carries the same profile.
+@pytest.fixture(scope="module")
+def poiseuille_fp32_steady():
     p = W.layered_poiseuille()
     with nfe.Sim(p, "fp32") as s:
         s.set_fields(p["C0"])
         s.step(200000)
         s.sync()
-        C, v, P = s.fields()
+        return p, s.fields()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_poiseuille_c3_full_size_against_analytic_profile(poiseuille_fp32_steady, precision):
+    # 32 x 32 x 192: the layered flow needs about 2e5 steps to reach its steady profile.  FP32 runs
+    # them from the initial layers; FP64 (about 50 times slower per step at N = 7) starts from the
+    # FP32 run's C and v and runs 2e4 steps (ten viscous times of the thickest layer) to its own
+    # steady state.  The profile matches the piecewise parabola of Eq. 56 with eta_i v'' = -F (the
+    # physical sign) within 2 % of its maximum; the seventh component stays exactly zero; every
+    # column carries the same profile.
+    p, (C32, v32, _) = poiseuille_fp32_steady
+    if precision == "fp32":
+        C, v = C32, v32
+    else:
+        with nfe.Sim(p, "fp64") as s:
+            s.set_fields(C32, v32)
+            s.step(20000)
+            s.sync()
+            C, v, P = s.fields()
     assert (C[6] == 0.0).all()
     vx = v[0]
     prof = vx.mean(axis=(1, 2))
@@ -130,8 +239,63 @@ def test_poiseuille_c3_full_size_against_analytic_profile():
     zs = np.arange(nz) + 0.5              # halfway walls at z = -1/2 and nz - 1/2
     ref = observables.poiseuille_profile(zs, [width * b for b in range(1, 6)], eta, 1e-6, nz, sign=-1.0)
     err = np.abs(prof - ref).max() / np.abs(ref).max()
-    print(f"poiseuille c3 full size: max |v - analytic| / max|analytic| = {err:.4f}, vmax {np.abs(prof).max():.4e}")
+    print(f"poiseuille c3 full size {precision}: max |v - analytic| / max|analytic| = {err:.4f}, "
+          f"vmax {np.abs(prof).max():.4e}")
     assert err < 0.02, err
+
+
+@pytest.mark.parametrize("precision,tol_c,tol_f", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)])
+def test_janus_c4_layout_parity_32cube(precision, tol_c, tol_f):
+    # The c4 layout (four Janus drops, sigma ~ U(0.004, 0.012) from seed 1004, so Omega = 1/90 and
+    # the stabiliser xi_j of Eq. 17 is active) on a 32^3 cube with drops of radius 4, 60 steps,
+    # element by element against the oracle, with every global sum of nfe_diagnostics.
+    from .test_gpu_parity import compare
+    p = W.janus_3d(n=32, radius=4.0)
+    _, _, errs = compare(p, 60, precision)
+    print(f"janus c4 layout 32^3 {precision}, 60 steps: {errs}")
+
+
+# Largest domain-averaged |v_x| of the non-conservative run must exceed this.  Measured on the
+# paper's 100 x 100 layout: 3.3e-5 after 4500 steps (the domain-wide momentum the force of Eq. 31
+# creates), 1.1e-4 after 1.3e5 steps; the conservative run stays below 1e-18.
+JANUS_DRIFT_MIN = 1e-5
+
+
+def _janus_drift(force_form, steps, every):
+    # mean velocity of the paper's Janus droplet (Sec. IV A: 100 x 100 periodic, fluid 2 disc of
+    # radius 20, fluids 3 and 4 discs 25 lu to the right and left, sigma14 = sigma24 = 0.0095, the
+    # others 0.005), FP64, sampled every `every` steps: over the whole domain (total momentum / n)
+    # and over the drop (v_x weighted by the drop's volume fraction 1 - C_1)
+    p = W.janus_2d()
+    flags = nfe.NFE_NONCONSERVATIVE_FORCE if force_form == "nonconservative" else 0
+    n = 100 * 100
+    out = []
+    with nfe.Sim(p, "fp64", flags=flags) as s:
+        s.set_fields(p["C0"])
+        for t in range(every, steps + 1, every):
+            s.step(every)
+            d = s.diagnostics()
+            C, v, _ = s.fields()
+            drop = 1.0 - C[0]
+            out.append((t, d["momentum"][:2] / n, float((v[0] * drop).sum() / drop.sum())))
+    return out
+
+
+def test_janus_drift_nonconservative_vs_conservative():
+    # Sec. IV A (Fig. of the Janus droplet): with the non-conservative force of Eq. 31 the
+    # asymmetric Janus drop drifts; with the conservative force of Eq. 34 the mean velocity stays
+    # at machine precision.
+    steps, every = 20000, 500
+    ncon = _janus_drift("nonconservative", steps, every)
+    cons = _janus_drift("conservative", steps, every)
+    vn = max(abs(u[0]) for _, u, _ in ncon)
+    vd = max(abs(ud) for _, _, ud in ncon)
+    vc = max(np.abs(u).max() for _, u, _ in cons)
+    print("janus drift, (t, domain mean v_x, drop mean v_x) non-conservative:",
+          [(t, f"{u[0]:.3e}", f"{ud:.3e}") for t, u, ud in ncon[::4]])
+    print(f"janus drift: max |mean v_x| non-conservative {vn:.3e} (drop {vd:.3e}), conservative {vc:.3e}")
+    assert vc < 1e-16
+    assert vn > JANUS_DRIFT_MIN
 
 
 @pytest.mark.parametrize("precision", ["fp32", "f16", "bf16"])

@@ -25,12 +25,13 @@ def _built():
     lib()
 
 
-def oracle_run(p, steps):
+def oracle_run(p, steps, force_form="conservative"):
     prm = lbm.Params(p)
     st = lbm.init_state(prm, p["C0"], flux_form="factored")
-    st = lbm.run(prm, st, steps, flux_form="factored")
-    C, v, P, _ = lbm.fields(prm, st, flux_form="factored")
-    return dict(C=C, v=v, P=P, f=st.f[1:])
+    st = lbm.run(prm, st, steps, flux_form="factored", force_form=force_form)
+    C, v, P, _ = lbm.fields(prm, st, flux_form="factored", force_form=force_form)
+    diag = lbm.diagnostics(prm, st, flux_form="factored", force_form=force_form)
+    return dict(C=C, v=v, P=P, f=st.f[1:], diag=diag)
 
 
 def gpu_run(p, steps, precision="fp64", **kw):
@@ -40,17 +41,42 @@ def gpu_run(p, steps, precision="fp64", **kw):
         s.sync()
         C, v, P = s.fields()
         f = s.populations()
-    return dict(C=C, v=v, P=P, f=f)
+        diag = s.diagnostics()
+    return dict(C=C, v=v, P=P, f=f, diag=diag)
 
 
-def compare(p, steps, precision):
-    o = oracle_run(p, steps)
-    g = gpu_run(p, steps, precision)
+def compare_diagnostics(dg, do, precision, n):
+    """nfe_diagnostics against the oracle's global sums (the FP64 reductions of step a7).
+
+    Mass, the force sums and the extrema are compared with the field tolerances; the momentum
+    sum, a sum of n small velocities, within n times the velocity tolerance of its largest
+    site value."""
+    tol = TOL[precision]
+    assert dg["step"] == do["step"]
+    assert dg["nonfinite"] == do["nonfinite"] == 0
+    np.testing.assert_allclose(dg["mass"], do["mass"], rtol=tol["C"], atol=0)
+    cmax = np.abs(do["max_abs_C"]).max()
+    assert np.abs(dg["max_abs_C"] - do["max_abs_C"]).max() <= tol["C"] * cmax
+    assert np.abs(dg["min_C"] - do["min_C"]).max() <= tol["C"] * cmax
+    fabs = do["force_abs_sum"].sum()
+    np.testing.assert_allclose(dg["force_abs_sum"], do["force_abs_sum"], rtol=tol["f"], atol=tol["f"] * fabs)
+    assert np.abs(dg["force_sum"] - do["force_sum"]).max() <= tol["f"] * fabs
+    vmax = do["max_speed"]
+    assert abs(dg["max_speed"] - vmax) <= tol["f"] * vmax + 1e-300
+    assert np.abs(dg["momentum"] - do["momentum"]).max() <= tol["f"] * n * vmax + 1e-300
+
+
+def compare(p, steps, precision, force_form="conservative", **kw):
+    o = oracle_run(p, steps, force_form)
+    if force_form == "nonconservative":
+        kw["flags"] = kw.get("flags", 0) | nfe.NFE_NONCONSERVATIVE_FORCE
+    g = gpu_run(p, steps, precision, **kw)
     tol = TOL[precision]
     errs = {k: rel(g[k], o[k]) for k in ("C", "f", "v", "P")}
     assert errs["C"] <= tol["C"], errs
     for k in ("f", "v", "P"):
         assert errs[k] <= tol["f"], errs
+    compare_diagnostics(g["diag"], o["diag"], precision, p["nx"] * p["ny"] * p["nz"])
     return o, g, errs
 
 
@@ -86,6 +112,16 @@ def test_fp64_parity_100_steps(case):
 @pytest.mark.parametrize("case", ["lens_walls_N3", "spinodal_N4", "janus3d_N4", "poiseuille3d_N7"])
 def test_fp32_parity_100_steps(case):
     compare(CASES[case](), 100, "fp32")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["janus_N4", "mixture_N5_trt_omega_wallsx", "janus3d_N4", "d3q19_walls_N4"])
+def test_nonconservative_force_parity_100_steps(case, precision):
+    # The non-conservative surface-tension force of Eq. 31 (F_s = sum_i mu_i grad C_i, the
+    # paper's negative control, NFE_NONCONSERVATIVE_FORCE) on D2Q9 and D3Q19 against the oracle's
+    # literal Eq. 31 with the chemical potentials of Eq. 7.
+    p = _mixture3d(19, 13, 14, 4, 51, (True, False, True)) if case == "d3q19_walls_N4" else CASES[case]()
+    compare(p, 100, precision, force_form="nonconservative")
 
 
 @pytest.mark.parametrize("shape,walls,N", [((3, 5), (False, True), 2), ((5, 1), (False, False), 3),

@@ -60,3 +60,15 @@ def test_static_stats_reject_too_many_planes():
         nfe.nfe_field_stats_static(17, 10, buf.data_ptr(), out.data_ptr(), None)
     assert e.value.status == 1
     assert "16" in str(e.value)
+
+
+def test_static_stats_report_a_nan():
+    # a NaN anywhere in a plane shows in every statistic of that plane (a health check on the
+    # largest magnitude must not miss it); the other planes are unaffected
+    lib()
+    planes = np.linspace(-1.0, 2.0, 3 * 1000).reshape(3, 1000)
+    planes[1, 617] = np.nan
+    out = _stats_on_device(planes)
+    assert np.isnan(out[1]).all()
+    np.testing.assert_allclose(out[[0, 2], 2], np.abs(planes[[0, 2]]).max(axis=1), rtol=0)
+    np.testing.assert_allclose(out[[0, 2], 3], planes[[0, 2]].min(axis=1), rtol=0)
