@@ -1,18 +1,24 @@
 // Fused D3Q19 time step: one kernel per step.  A CTA owns a TX x TY column of
 // the grid over a chunk of z-planes and marches up in z with shared-memory
 // ring buffers:
-//   A ring (5 planes, tile + 2-site ring in x/y): evolved C and the bulk energy
-//     E_B (Eq. 5), computed once per site;
-//   B ring (3 planes, tile + 1-site ring): evolved C, v and the flux potential S.
+//   A ring (4 planes, tile + 2-site ring in x/y): evolved C, staged from HBM by
+//     cp.async two planes ahead of use, and the bulk energy E_B (Eq. 5) computed
+//     once per site from the staged values;
+//   B ring (3 planes, tile + 1-site ring): evolved C, v, the flux potential S and |v|^2.
 // For every plane z of the chunk the CTA
-//   1. fills A-plane z+2 from HBM,
+//   1. completes A-plane z+2 (its cp.async copies, then E_B),
 //   2. computes B-plane z+1: isotropic grad / Laplacian (Eqs. 35-36) from A-planes
 //      z..z+2, S_i = C_i q_i(C) + (3D/4) lap C_i (Eq. 12), the force of Eq. 34,
 //      moments of f (Eqs. 37-38); the own sites of plane z+1 are collided (TRT with
 //      forcing, Eqs. 23-30) and push-streamed with bounce-back (Eqs. 44-45),
-//   3. computes C(t+1) of plane z from B-planes z-1..z+1 (Eqs. 39-41, tau_g = 1).
+//   3. starts the copies of A-plane z+3 and the loads of the populations of plane z+2,
+//   4. computes C(t+1) of plane z from B-planes z-1..z+1 (Eqs. 39-41, tau_g = 1).
 // Only f (18 populations) and the N-1 evolved C cross HBM; the redundant work is
 // the x/y ring only, the z direction is streamed.
+//
+// In FP32 the stencil sums, the moments, the collision and the Cahn-Hilliard gather run on
+// packed FP32x2 instructions (two record values, two direction pairs or two components per
+// instruction); FP64 takes the same steps one value at a time.
 #pragma once
 
 #include "nfe_fused2d.cuh"
@@ -23,61 +29,172 @@ template <int N, typename T, int TX, int TY>
 struct Fused3DShape {
     static constexpr int AX = TX + 4, AY = TY + 4, APLANE = AX * AY;
     static constexpr int BX = TX + 2, BY = TY + 2, BPLANE = BX * BY;
+    static constexpr int ASLOTS = 4, BSLOTS = 3;
     using RA = SRec<T, N>;               // evolved C (N-1), E_B
     using RB = SRec<T, 2 * N + 2>;       // evolved C (N-1), vx, vy, vz, S (N-1), |v|^2
     static constexpr int A_SLOT = RA::NVP * APLANE;
     static constexpr int B_SLOT = RB::NVP * BPLANE;
-    static constexpr size_t BYTES = sizeof(T) * size_t(5 * A_SLOT + 3 * B_SLOT);
+    static constexpr size_t BYTES = sizeof(T) * size_t(ASLOTS * A_SLOT + BSLOTS * B_SLOT);
     static constexpr int NHALO = BPLANE - TX * TY;
 };
 
-__device__ __forceinline__ int slotA(int z) { return (z + 10) % 5; }   // z >= -2
-__device__ __forceinline__ int slotB(int z) { return (z + 9) % 3; }    // z >= -1
+__device__ __forceinline__ int slotA(int z) { return (z + 8) & 3; }   // z >= -2
+__device__ __forceinline__ int slotB(int z) { return (z + 9) % 3; }   // z >= -1
 
-// 3-D stencil from three A-planes (below, centre, above) at in-plane index ia.
-template <int N, typename T, int AX, bool CHECK>
-__device__ __forceinline__ void stencil3d(const T *pm, const T *p0, const T *pp, int count, int ia, unsigned wall,
-                                          T (&c)[N], T (&lap)[N], T (&g)[N][3], T (&gE)[3]) {
-    using RA = SRec<T, N>;
-    T r0[RA::NVP];
-    srec_load<T, N>(p0, count, ia, r0);
-    T acc[N][4];          // lap, gx, gy, gz sums (N-1 = bulk energy: gradient only)
+// Asynchronous global -> shared copies of one 4- or 8-byte value (cp.async, L1-allocating).
+template <typename T>
+__device__ __forceinline__ void cp_async_value(T *dst_smem, const T *src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte values");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ----------------------------------------------------------------------------
+// Stencil (Eqs. 35-36) from three A-planes (below, centre, above) at in-plane index ia.
+// Out: the N volume fractions, their Laplacian and gradient (the implicit component's are
+// minus the sums of the others), and grad E_B.  A neighbour beyond a wall contributes no
+// difference (psi there := psi(x), Sec. III C).  With D3Q19 weights w_axis = 2 w_diag, every
+// sum is accumulated in units of w_diag = 1/36: lap = 6 w_diag sum' = sum' / 6 and
+// grad = 3 w_diag sum' = sum' / 12, where sum' counts axis neighbours twice.
+// ----------------------------------------------------------------------------
+template <int N, int AX, bool CHECK>
+__device__ __forceinline__ void stencil3d_packed(const float *pm, const float *p0, const float *pp, int count, int ia,
+                                                 unsigned wall, float (&c)[N], float (&lap)[N], float (&g)[N][3],
+                                                 float (&gE)[3]) {
+    using RA = SRec<float, N>;
+    constexpr int NPU = (N + 1) / 2;     // value pairs holding the N used record values
+    float r0[RA::NVP];
+    srec_load<float, N>(p0, count, ia, r0);
+    float2 L[NPU], GX[NPU], GY[NPU], GZ[NPU];
 #pragma unroll
-    for (int a = 0; a < N; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = T(0);
+    for (int p = 0; p < NPU; ++p) L[p] = GX[p] = GY[p] = GZ[p] = make_float2(0.0f, 0.0f);
+    const float2 two = dup2(2.0f), mtwo = dup2(-2.0f);
     sfor<1, 19, 1>([&](auto kc_) {
         constexpr int k = decltype(kc_)::value;
-        if (CHECK && ((wall >> k) & 1u)) return;     // psi beyond a wall := psi(x)
-        const T *pl = LD3Q19::ez(k) > 0 ? pp : (LD3Q19::ez(k) < 0 ? pm : p0);
-        T r[RA::NVP];
-        srec_load<T, N>(pl, count, ia + LD3Q19::ex(k) + AX * LD3Q19::ey(k), r);
-        const T wk = T(LD3Q19::w(k));
+        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+        constexpr bool axis = k < 7;
+        if (CHECK && ((wall >> k) & 1u)) return;
+        const float *pl = ez > 0 ? pp : (ez < 0 ? pm : p0);
+        float r[RA::NVP];
+        srec_load<float, N>(pl, count, ia + ex + AX * ey, r);
 #pragma unroll
-        for (int a = 0; a < N; ++a) {
-            const T d = r[a] - r0[a];
-            if (a < N - 1) acc[a][0] += wk * d;
-            if (LD3Q19::ex(k)) acc[a][1] += (LD3Q19::ex(k) > 0 ? wk : -wk) * d;
-            if (LD3Q19::ey(k)) acc[a][2] += (LD3Q19::ey(k) > 0 ? wk : -wk) * d;
-            if (LD3Q19::ez(k)) acc[a][3] += (LD3Q19::ez(k) > 0 ? wk : -wk) * d;
+        for (int p = 0; p < NPU; ++p) {
+            const float2 d = sub2(make_float2(r[2 * p], r[2 * p + 1]), make_float2(r0[2 * p], r0[2 * p + 1]));
+            if constexpr (axis) {
+                L[p] = fma2(two, d, L[p]);
+                if constexpr (ex != 0) GX[p] = fma2(ex > 0 ? two : mtwo, d, GX[p]);
+                if constexpr (ey != 0) GY[p] = fma2(ey > 0 ? two : mtwo, d, GY[p]);
+                if constexpr (ez != 0) GZ[p] = fma2(ez > 0 ? two : mtwo, d, GZ[p]);
+            } else {
+                L[p] = add2(L[p], d);
+                if constexpr (ex != 0) GX[p] = ex > 0 ? add2(GX[p], d) : sub2(GX[p], d);
+                if constexpr (ey != 0) GY[p] = ey > 0 ? add2(GY[p], d) : sub2(GY[p], d);
+                if constexpr (ez != 0) GZ[p] = ez > 0 ? add2(GZ[p], d) : sub2(GZ[p], d);
+            }
         }
     });
-    T sl = T(0), sx = T(0), sy = T(0), sz = T(0), rest = T(0);
+    const float2 sixth = dup2(1.0f / 6.0f), twelfth = dup2(1.0f / 12.0f);
+    float Lv[2 * NPU], Xv[2 * NPU], Yv[2 * NPU], Zv[2 * NPU];
+#pragma unroll
+    for (int p = 0; p < NPU; ++p) {
+        const float2 l = mul2(sixth, L[p]), x = mul2(twelfth, GX[p]), y = mul2(twelfth, GY[p]), z = mul2(twelfth, GZ[p]);
+        Lv[2 * p] = l.x; Lv[2 * p + 1] = l.y;
+        Xv[2 * p] = x.x; Xv[2 * p + 1] = x.y;
+        Yv[2 * p] = y.x; Yv[2 * p + 1] = y.y;
+        Zv[2 * p] = z.x; Zv[2 * p + 1] = z.y;
+    }
+    float sl = 0.0f, sx = 0.0f, sy = 0.0f, sz = 0.0f, rest = 0.0f;
 #pragma unroll
     for (int a = 0; a < N - 1; ++a) {
         c[a] = r0[a];
         rest += r0[a];
-        lap[a] = T(6) * acc[a][0];
-        g[a][0] = T(3) * acc[a][1]; g[a][1] = T(3) * acc[a][2]; g[a][2] = T(3) * acc[a][3];
+        lap[a] = Lv[a]; g[a][0] = Xv[a]; g[a][1] = Yv[a]; g[a][2] = Zv[a];
+        sl += Lv[a]; sx += Xv[a]; sy += Yv[a]; sz += Zv[a];
+    }
+    c[N - 1] = 1.0f - rest;
+    lap[N - 1] = -sl; g[N - 1][0] = -sx; g[N - 1][1] = -sy; g[N - 1][2] = -sz;
+    gE[0] = Xv[N - 1]; gE[1] = Yv[N - 1]; gE[2] = Zv[N - 1];
+}
+
+template <int N, typename T, int AX, bool CHECK>
+__device__ __forceinline__ void stencil3d(const T *pm, const T *p0, const T *pp, int count, int ia, unsigned wall,
+                                          T (&c)[N], T (&lap)[N], T (&g)[N][3], T (&gE)[3]) {
+    if constexpr (sizeof(T) == 4) {
+        stencil3d_packed<N, AX, CHECK>(pm, p0, pp, count, ia, wall, c, lap, g, gE);
+        return;
+    }
+    using RA = SRec<T, N>;
+    T r0[RA::NVP];
+    srec_load<T, N>(p0, count, ia, r0);
+    T acc[N][4];          // lap, gx, gy, gz sums in units of w_diag (value N-1 = bulk energy: gradient only)
+#pragma unroll
+    for (int a = 0; a < N; ++a) acc[a][0] = acc[a][1] = acc[a][2] = acc[a][3] = T(0);
+    sfor<1, 19, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
+        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+        constexpr bool axis = k < 7;
+        if (CHECK && ((wall >> k) & 1u)) return;     // psi beyond a wall := psi(x)
+        const T *pl = ez > 0 ? pp : (ez < 0 ? pm : p0);
+        T r[RA::NVP];
+        srec_load<T, N>(pl, count, ia + ex + AX * ey, r);
+        const T wk = axis ? T(2) : T(1);
+#pragma unroll
+        for (int a = 0; a < N; ++a) {
+            const T d = r[a] - r0[a];
+            if (a < N - 1) acc[a][0] += wk * d;
+            if constexpr (ex != 0) acc[a][1] += (ex > 0 ? wk : -wk) * d;
+            if constexpr (ey != 0) acc[a][2] += (ey > 0 ? wk : -wk) * d;
+            if constexpr (ez != 0) acc[a][3] += (ez > 0 ? wk : -wk) * d;
+        }
+    });
+    T sl = T(0), sx = T(0), sy = T(0), sz = T(0), rest = T(0);
+    const T sixth = T(1) / T(6), twelfth = T(1) / T(12);
+#pragma unroll
+    for (int a = 0; a < N - 1; ++a) {
+        c[a] = r0[a];
+        rest += r0[a];
+        lap[a] = sixth * acc[a][0];
+        g[a][0] = twelfth * acc[a][1]; g[a][1] = twelfth * acc[a][2]; g[a][2] = twelfth * acc[a][3];
         sl += lap[a]; sx += g[a][0]; sy += g[a][1]; sz += g[a][2];
     }
     c[N - 1] = T(1) - rest;
     lap[N - 1] = -sl; g[N - 1][0] = -sx; g[N - 1][1] = -sy; g[N - 1][2] = -sz;
-    gE[0] = T(3) * acc[N - 1][1]; gE[1] = T(3) * acc[N - 1][2]; gE[2] = T(3) * acc[N - 1][3];
+    gE[0] = twelfth * acc[N - 1][1]; gE[1] = twelfth * acc[N - 1][2]; gE[2] = twelfth * acc[N - 1][3];
 }
 
+// Sums and differences of the direction pairs (k, k+1), k odd: sp[j] = f_k + f_k+1 and
+// dm[j] = f_k - f_k+1 for pair j = (k - 1) / 2.  The moments and the TRT collision use only these.
+template <typename T>
+__device__ __forceinline__ void pair_sums(const T (&f)[19], T (&sp)[9], T (&dm)[9]) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int j = 0; j < 9; j += 2) {
+            if (j + 1 < 9) {
+                const float2 a = make_float2(f[2 * j + 1], f[2 * j + 3]), b = make_float2(f[2 * j + 2], f[2 * j + 4]);
+                const float2 s = add2(a, b), d = sub2(a, b);
+                sp[j] = s.x; sp[j + 1] = s.y; dm[j] = d.x; dm[j + 1] = d.y;
+            } else {
+                sp[j] = f[2 * j + 1] + f[2 * j + 2];
+                dm[j] = f[2 * j + 1] - f[2 * j + 2];
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) { sp[j] = f[2 * j + 1] + f[2 * j + 2]; dm[j] = f[2 * j + 1] - f[2 * j + 2]; }
+    }
+}
+
+// Force (Eq. 34, or Eq. 31 with cf.nonconservative), body forces, flux potential (Eq. 12)
+// and moments (Eqs. 37-38) at one site.  f holds f_1..f_18; sp / dm are returned for the collision.
 template <int N, typename T, int Q4>
 __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N], const T (&lap)[N],
                                                const T (&g)[N][3], const T (&gE)[3], const T (&f)[19],
-                                               T (&S)[N - 1], T (&F)[3], T (&v)[3], T &P) {
+                                               T (&S)[N - 1], T (&F)[3], T (&v)[3], T &P, T (&sp)[9], T (&dm)[9]) {
     if (!cf.nonconservative) {
         F[0] = gE[0]; F[1] = gE[1]; F[2] = gE[2];
 #pragma unroll
@@ -115,19 +232,222 @@ __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N
     flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
-    T j0 = T(0), j1 = T(0), j2 = T(0), sumf = T(0);
+    // moments from the pair sums: pairs (1,2) (3,4) (5,6) are the axes, then xy (+,+) (+,-),
+    // xz (+,+) (+,-), yz (+,+) (+,-), each pair's first direction listed
+    pair_sums<T>(f, sp, dm);
+    const T sumf = ((sp[0] + sp[1]) + (sp[2] + sp[3])) + ((sp[4] + sp[5]) + (sp[6] + sp[7])) + sp[8];
+    const T jx = (dm[0] + (dm[3] + dm[4])) + (dm[5] + dm[6]);
+    const T jy = (dm[1] + (dm[3] - dm[4])) + (dm[7] + dm[8]);
+    const T jz = (dm[2] + (dm[5] - dm[6])) + (dm[7] - dm[8]);
+    v[0] = jx + T(0.5) * F[0];
+    v[1] = jy + T(0.5) * F[1];
+    v[2] = jz + T(0.5) * F[2];
+    // P = c_s^2 / (1 - w_0) [sum_{k != 0} f_k + s_0(v)], s_0 = -w_0 |v|^2 / (2 c_s^2)
+    P = (sumf - T(0.5) * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])) * T(0.5);
+}
+
+// TRT collision with forcing (Eqs. 23-30) of one site, regrouped so that per-site factors are
+// formed once: for a pair (k, kbar), with s = f_k + f_kbar and d = f_k - f_kbar,
+//   sym  = w_k [X + e.v (Y e.v + Z e.F)] - (op / 2) s
+//   anti = w_k (U e.v + V e.F) - (om / 2) d
+// where X = op (3P - 1.5 v.v) - 3 ap v.F, Y = 4.5 op, Z = 9 ap, U = 3 om, V = 3 am
+// (ap = 1 - op / 2, am = 1 - om / 2).  Post-collision values replace f.
+template <int N, typename T>
+__device__ __forceinline__ void collide3d(const Coef<T> &cf, const T (&c)[N], const T (&v)[3], const T (&F)[3], T P,
+                                          const T (&sp)[9], const T (&dm)[9], T (&f)[19]) {
+    T op, om;
+    relaxation<N, T>(cf, c, op, om);
+    const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
+    const T vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+    const T vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
+    const T X = op * (T(3) * P - T(1.5) * vv) - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om,
+            V = T(3) * am;
+    const T hop = T(0.5) * op, hom = T(0.5) * om;
+    // e.v and e.F of the first direction of every pair
+    const T eu[9] = {v[0], v[1], v[2], v[0] + v[1], v[0] - v[1], v[0] + v[2], v[0] - v[2], v[1] + v[2], v[1] - v[2]};
+    const T eF[9] = {F[0], F[1], F[2], F[0] + F[1], F[0] - F[1], F[0] + F[2], F[0] - F[2], F[1] + F[2], F[1] - F[2]};
+    if constexpr (sizeof(T) == 4) {
+        // two pairs of one weight class per instruction: (1,2)+(3,4), then (5,6) alone, then
+        // the six diagonal pairs two by two
+        const float2 mhop = dup2(-hop), mhom = dup2(-hom);
+        auto two_pairs = [&](float wk, int j0, int j1) {
+            const float2 e_u = make_float2(eu[j0], eu[j1]), e_F = make_float2(eF[j0], eF[j1]);
+            const float2 s = make_float2(sp[j0], sp[j1]), d = make_float2(dm[j0], dm[j1]);
+            const float2 sym = fma2(mhop, s, fma2(e_u, fma2(dup2(wk * Y), e_u, mul2(dup2(wk * Z), e_F)), dup2(wk * X)));
+            const float2 anti = fma2(mhom, d, fma2(dup2(wk * U), e_u, mul2(dup2(wk * V), e_F)));
+            const float2 fk = make_float2(f[2 * j0 + 1], f[2 * j1 + 1]), fkb = make_float2(f[2 * j0 + 2], f[2 * j1 + 2]);
+            const float2 pk = add2(fk, add2(sym, anti)), pkb = add2(fkb, sub2(sym, anti));
+            f[2 * j0 + 1] = pk.x; f[2 * j1 + 1] = pk.y; f[2 * j0 + 2] = pkb.x; f[2 * j1 + 2] = pkb.y;
+        };
+        const float wa = float(LD3Q19::w(1)), wd = float(LD3Q19::w(7));
+        two_pairs(wa, 0, 1);
+        {
+            const float sym = (wa * X + eu[2] * ((wa * Y) * eu[2] + (wa * Z) * eF[2])) - hop * sp[2];
+            const float anti = ((wa * U) * eu[2] + (wa * V) * eF[2]) - hom * dm[2];
+            f[5] = f[5] + (sym + anti);
+            f[6] = f[6] + (sym - anti);
+        }
+        two_pairs(wd, 3, 4);
+        two_pairs(wd, 5, 6);
+        two_pairs(wd, 7, 8);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const T wk = j < 3 ? T(LD3Q19::w(1)) : T(LD3Q19::w(7));
+            const T sym = (wk * X + eu[j] * ((wk * Y) * eu[j] + (wk * Z) * eF[j])) - hop * sp[j];
+            const T anti = ((wk * U) * eu[j] + (wk * V) * eF[j]) - hom * dm[j];
+            f[2 * j + 1] = f[2 * j + 1] + (sym + anti);
+            f[2 * j + 2] = f[2 * j + 2] + (sym - anti);
+        }
+    }
+}
+
+// |v|^2 with an explicit operation order, so that every kernel that forms it (the fused step's
+// record, the split form's gather staging) gets the same bits.
+template <typename T>
+__device__ __forceinline__ T vsq3(T a, T b, T c) {
+    if constexpr (sizeof(T) == 4) return __fmaf_rn(c, c, __fmaf_rn(b, b, __fmul_rn(a, a)));
+    else return __fma_rn(c, c, __fma_rn(b, b, __dmul_rn(a, a)));
+}
+
+// Push-streaming of the post-collision populations of one own site s0 (in-plane wrapped
+// coordinates sx, sy, plane zw) with halfway bounce-back (Eqs. 44-45) where wall0 has bit k set.
+// The periodic wrap is folded into six per-site neighbour offsets, so every site of a warp runs
+// the same store sequence; only sites next to a wall take the bounce-back form.
+template <typename T, typename SF>
+__device__ __forceinline__ void push_store3d(const Coef<T> &cf, SF *__restrict__ fout, int n, int nx, int ny, int nz,
+                                             int sx, int sy, int zw, int s0, unsigned wall0, const T (&f)[19]) {
+    const int nxy = nx * ny;
+    const int dxp = sx == nx - 1 ? 1 - nx : 1, dxm = sx == 0 ? nx - 1 : -1;
+    const int dyp = sy == ny - 1 ? nx - nxy : nx, dym = sy == 0 ? nxy - nx : -nx;
+    const int dzp = zw == nz - 1 ? nxy - n : nxy, dzm = zw == 0 ? n - nxy : -nxy;
+    auto target = [&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
+        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+        int t = s0;
+        if constexpr (ex != 0) t += ex > 0 ? dxp : dxm;
+        if constexpr (ey != 0) t += ey > 0 ? dyp : dym;
+        if constexpr (ez != 0) t += ez > 0 ? dzp : dzm;
+        return t;
+    };
+    if (wall0 == 0u) {
+        sfor<1, 19, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
+            FStore<SF, T>::store(fout + (k - 1) * n + target(kc_), f[k], LD3Q19::w(k), cf.fscale);
+        });
+    } else {
+        sfor<1, 19, 1>([&](auto kc_) {
+            constexpr int k = decltype(kc_)::value;
+            constexpr int kb = opp(k);
+            // halfway bounce-back: f_kbar(x, t+1) = post_k(x)
+            if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k], LD3Q19::w(kb), cf.fscale);
+            else FStore<SF, T>::store(fout + (k - 1) * n + target(kc_), f[k], LD3Q19::w(k), cf.fscale);
+        });
+    }
+}
+
+// Shared-memory / scratch record of NV values: full 16-byte chunks in separate planes and, when
+// NV is not a whole number of chunks (FP32 with NV = 2 mod 4), an 8-byte plane for the last two.
+template <typename T, int NV>
+struct TRec {
+    static constexpr int PER = 16 / sizeof(T);
+    static constexpr int NC = NV / PER;            // full chunks
+    static constexpr int TAIL = NV - NC * PER;     // 0, or 2 values (FP32)
+    static constexpr int NVP = NC * PER + TAIL;
+    static_assert(TAIL == 0 || (TAIL == 2 && sizeof(T) == 4), "records of an even number of values");
+};
+
+template <typename T, int NV>
+__device__ __forceinline__ void trec_load(const T *base, int count, int i, T (&out)[TRec<T, NV>::NVP]) {
+    using R = TRec<T, NV>;
+    using V = typename Vec16<T>::type;
+#pragma unroll
+    for (int c = 0; c < R::NC; ++c) {
+        const V v = reinterpret_cast<const V *>(base + size_t(c) * count * R::PER)[i];
+        if constexpr (sizeof(T) == 4) {
+            out[4 * c + 0] = v.x; out[4 * c + 1] = v.y; out[4 * c + 2] = v.z; out[4 * c + 3] = v.w;
+        } else {
+            out[2 * c + 0] = v.x; out[2 * c + 1] = v.y;
+        }
+    }
+    if constexpr (R::TAIL == 2) {
+        const float2 v = reinterpret_cast<const float2 *>(base + size_t(R::NC) * count * R::PER)[i];
+        out[R::NC * 4] = v.x; out[R::NC * 4 + 1] = v.y;
+    }
+}
+
+// The B record (C, v, S, |v|^2) of one site in its layout: SRec planes (fused step, TAILREC false)
+// or TRec planes (split step, TAILREC true).
+template <typename T, int NV, bool TAILREC>
+struct BRec {
+    static constexpr int NVP = TAILREC ? TRec<T, NV>::NVP : SRec<T, NV>::NVP;
+    __device__ __forceinline__ static void load(const T *base, int count, int i, T (&out)[NVP]) {
+        if constexpr (TAILREC) trec_load<T, NV>(base, count, i, out);
+        else srec_load<T, NV>(base, count, i, out);
+    }
+};
+
+// Cahn-Hilliard update (Eqs. 39-41, tau_g = 1) of one site from the (C, v, S, |v|^2) records of
+// three planes (below, centre, above) at in-plane index ib (row pitch BX):
+// C_i(x, t+1) = C_i(x) + sum_k C_i(y) s_k(v(y)) + m sum_{k != 0} w_k (S_i(x) - S_i(y)), y = x - e_k,
+// the increments gathered before C(x) is added and the S Laplacian as link differences, so
+// that every link's two contributions cancel exactly.  A source beyond a wall bounces back:
+// the link then carries g^eq_kbar(x), i.e. C_i(x) s_kbar(v(x)) and no S difference.
+template <int N, typename T, int BX, bool CHECK, bool TAILREC = false>
+__device__ __forceinline__ void gather3d(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned wall0,
+                                         T m, T (&out)[N - 1]) {
+    using RB = BRec<T, 2 * N + 2, TAILREC>;
+    constexpr int E = N - 1;             // evolved components
+    T r0[RB::NVP];
+    RB::load(b0, bplane, ib, r0);
+    const T vv0 = r0[2 * N + 1];
+    const T w0 = T(1) / T(3);
+    T acc[E], lapS[E];
+    // rest population's increment: C_i(x) s_0(v(x))
+#pragma unroll
+    for (int e = 0; e < E; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * vv0); lapS[e] = T(0); }
     sfor<1, 19, 1>([&](auto kc_) {
         constexpr int k = decltype(kc_)::value;
-        sumf += f[k];
-        if (LD3Q19::ex(k)) j0 += LD3Q19::ex(k) > 0 ? f[k] : -f[k];
-        if (LD3Q19::ey(k)) j1 += LD3Q19::ey(k) > 0 ? f[k] : -f[k];
-        if (LD3Q19::ez(k)) j2 += LD3Q19::ez(k) > 0 ? f[k] : -f[k];
+        constexpr int kb = opp(k);                  // source x - e_k = x + e_kbar
+        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+        const T wk = T(LD3Q19::w(k));
+        if (CHECK && ((wall0 >> kb) & 1u)) {
+            const T eu = -(T(ex) * r0[N - 1] + T(ey) * r0[N] + T(ez) * r0[N + 1]);
+            const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
+#pragma unroll
+            for (int e = 0; e < E; ++e) acc[e] += r0[e] * sk;      // S difference is zero
+        } else {
+            const T *pl = LD3Q19::ez(kb) > 0 ? bp : (LD3Q19::ez(kb) < 0 ? bm : b0);
+            T r[RB::NVP];
+            RB::load(pl, bplane, ib + LD3Q19::ex(kb) + BX * LD3Q19::ey(kb), r);
+            // e_k . v(y) with the constant components folded (each is 0 or +-1)
+            T eu = T(0);
+            if constexpr (ex != 0) eu = ex > 0 ? r[N - 1] : -r[N - 1];
+            if constexpr (ey != 0) eu = ey > 0 ? eu + r[N] : eu - r[N];
+            if constexpr (ez != 0) eu = ez > 0 ? eu + r[N + 1] : eu - r[N + 1];
+            // s_k = w_k (3 eu + 4.5 eu^2 - 1.5 |v|^2) = eu (3 w_k + 4.5 w_k eu) - 1.5 w_k |v|^2
+            const T sk = eu * (T(3.0 * LD3Q19::w(k)) + T(4.5 * LD3Q19::w(k)) * eu) - T(1.5 * LD3Q19::w(k)) * r[2 * N + 1];
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int e = 0; e + 1 < E; e += 2) {
+                    const float2 cy = make_float2(r[e], r[e + 1]);
+                    const float2 ds = sub2(make_float2(r[N + 2 + e], r[N + 3 + e]), make_float2(r0[N + 2 + e], r0[N + 3 + e]));
+                    const float2 a = fma2(cy, dup2(sk), make_float2(acc[e], acc[e + 1]));
+                    const float2 l = fma2(dup2(float(LD3Q19::w(k))), ds, make_float2(lapS[e], lapS[e + 1]));
+                    acc[e] = a.x; acc[e + 1] = a.y; lapS[e] = l.x; lapS[e + 1] = l.y;
+                }
+                if constexpr (E % 2 == 1) {
+                    acc[E - 1] += r[E - 1] * sk;
+                    lapS[E - 1] += wk * (r[N + 1 + E] - r0[N + 1 + E]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
+            }
+        }
     });
-    v[0] = j0 + T(0.5) * F[0];
-    v[1] = j1 + T(0.5) * F[1];
-    v[2] = j2 + T(0.5) * F[2];
-    const T w0 = T(1) / T(3);
-    P = (sumf - T(1.5) * w0 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2])) * T(1.0 / (3.0 * (1.0 - 1.0 / 3.0)));
+#pragma unroll
+    for (int e = 0; e < E; ++e) out[e] = r0[e] + (acc[e] - m * lapS[e]);   // S Laplacian as link differences (mass-exact)
 }
 
 // Bit k set when x + e_k lies beyond a wall.
@@ -167,12 +487,13 @@ struct Fused3DTile {
     // own site in the plane, and this thread's ring site
     int tx, ty, gx0, gy0, sx, sy, sxy, bx, by, hx, hy, hxy;
     bool own_xy, ring_xy_ok;
+    int aoff[ITER];      // in-plane index (x + nx y) of this thread's A-sites, -1 past the plane
 
     __device__ __forceinline__ Fused3DTile(const Geom &g_, const Coef<T> &cf_, const SF *fin_, SF *fout_,
                                            const T *Cin_, T *Cout_, int *flag_, unsigned char *smem, int zchunk)
         : g(g_), cf(cf_), fin(fin_), fout(fout_), Cin(Cin_), Cout(Cout_), flag(flag_) {
         sA = reinterpret_cast<T *>(smem);
-        sB = sA + 5 * Sh::A_SLOT;
+        sB = sA + Sh::ASLOTS * Sh::A_SLOT;
         nx = g.nx; ny = g.ny; nz = g.nz;
         nxy = nx * ny;
         n = int(g.n);
@@ -202,20 +523,8 @@ struct Fused3DTile {
         hy = y0 + by - 1;
         ring_xy_ok = has_ring && !(edge && ((g.wx && (hx < 0 || hx >= nx)) || (g.wy && (hy < 0 || hy >= ny))));
         hxy = edge ? pwrap(hx, nx, tiny) + nx * pwrap(hy, ny, tiny) : hx + nx * hy;
-    }
-
-    // Periodic plane index of z in [z_lo - 2, z_hi + 2) without a division.
-    __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
-
-    // Loads are issued one plane ahead (load_A / load_F) and consumed by fill_A /
-    // fill_B in the next iteration, so HBM latency overlaps the previous plane's work.
-    // load_A / fill_A: A-plane za (C and E_B on the tile + 2-ring).
-    // load_F: f of the own site and of the ring site of plane zb.
-    // fill_B: B-plane zb (S, v; for own planes also collide + push-stream).
-    // ch: Cahn-Hilliard update of plane zc from B-planes zc-1..zc+1.
-    __device__ __forceinline__ void load_A(int za, T (&cl)[ITER][N - 1]) {
-        if (g.wz && (za < 0 || za >= nz)) return;
-        const int zw = zwrap(za);
+        // the A-sites this thread copies and completes in every plane (the same ones: the
+        // completion reads only this thread's own copies, so it needs no barrier)
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
             const int i = tid + it * NT;
@@ -226,34 +535,60 @@ struct Fused3DTile {
                     gx = g.wx ? min(max(gx, 0), nx - 1) : pwrap(gx, nx, tiny);
                     gy = g.wy ? min(max(gy, 0), ny - 1) : pwrap(gy, ny, tiny);
                 }
-                const int s = gx + nx * gy + nxy * zw;
-#pragma unroll
-                for (int a = 0; a < N - 1; ++a) cl[it][a] = Cin[a * n + s];
+                aoff[it] = gx + nx * gy;
+            } else {
+                aoff[it] = -1;
             }
         }
     }
 
-    __device__ __forceinline__ void fill_A(int za, const T (&cl)[ITER][N - 1]) {
+    // Periodic plane index of z in [z_lo - 2, z_hi + 2) without a division.
+    __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
+
+    // copy_A: start the cp.async copies of the evolved C of A-plane za (tile + 2-ring) into its
+    // slot and commit them as one group (an empty group beyond a z wall: never read).
+    __device__ __forceinline__ void copy_A(int za) {
+        if (!(g.wz && (za < 0 || za >= nz))) {
+            const int zo = nxy * zwrap(za);
+            T *base = sA + slotA(za) * Sh::A_SLOT;
+#pragma unroll
+            for (int it = 0; it < ITER; ++it) {
+                const int i = tid + it * NT;
+                if (aoff[it] >= 0) {
+                    const int s = aoff[it] + zo;
+#pragma unroll
+                    for (int a = 0; a < N - 1; ++a)
+                        cp_async_value<T>(base + (a / RA::PER) * Sh::APLANE * RA::PER + i * RA::PER + (a % RA::PER),
+                                          Cin + size_t(a) * n + s);
+                }
+            }
+        }
+        cp_async_commit();
+    }
+
+    // finish_A: after this thread's copies of A-plane za have landed, E_B (Eq. 5) of its A-sites.
+    __device__ __forceinline__ void finish_A(int za) {
         if (g.wz && (za < 0 || za >= nz)) return;      // beyond a wall: never read
         T *base = sA + slotA(za) * Sh::A_SLOT;
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
             const int i = tid + it * NT;
-            if (i < Sh::APLANE) {
+            if (aoff[it] >= 0) {
                 T rec[RA::NVP];
+                srec_load<T, N>(base, Sh::APLANE, i, rec);
                 T cc[N];
                 T rest = T(0);
 #pragma unroll
-                for (int a = 0; a < N - 1; ++a) { cc[a] = cl[it][a]; rec[a] = cc[a]; rest += cc[a]; }
+                for (int a = 0; a < N - 1; ++a) { cc[a] = rec[a]; rest += rec[a]; }
                 cc[N - 1] = T(1) - rest;
-                rec[N - 1] = bulk_energy<N, T>(cc, cf);
-#pragma unroll
-                for (int a = N; a < RA::NVP; ++a) rec[a] = T(0);
-                srec_store<T, N>(base, Sh::APLANE, i, rec);
+                base[((N - 1) / RA::PER) * Sh::APLANE * RA::PER + i * RA::PER + ((N - 1) % RA::PER)] =
+                    bulk_energy<N, T>(cc, cf);
             }
         }
     }
 
+    // load_F: f of the own site and of the ring site of plane zb into registers (consumed by
+    // fill_B one iteration later, so that HBM latency overlaps the gather of the plane below).
     __device__ __forceinline__ void load_F(int zb, T (&fo)[19], T (&fr)[19]) {
         fo[0] = fr[0] = T(0);
         if (g.wz && (zb < 0 || zb >= nz)) return;
@@ -264,6 +599,18 @@ struct Fused3DTile {
             const int s = hxy + nxy * zw;
             sfor<1, 19, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; fr[k] = FStore<SF, T>::load(fin + (k - 1) * n + s, LD3Q19::w(k), cf.finv); });
         }
+    }
+
+    // B record of one site: C, v, S and |v|^2 (read 18 times by the gather)
+    __device__ __forceinline__ void store_B(T *bbase, int ib, const T (&c)[N], const T (&v)[3], const T (&S)[N - 1]) {
+        T rec[RB::NVP];
+#pragma unroll
+        for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
+        rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
+        rec[2 * N + 1] = vsq3<T>(v[0], v[1], v[2]);
+#pragma unroll
+        for (int a = 2 * N + 2; a < RB::NVP; ++a) rec[a] = T(0);
+        srec_store<T, 2 * N + 2>(bbase, Sh::BPLANE, ib, rec);
     }
 
     // fo is consumed: the collision leaves post-collision values in it
@@ -285,132 +632,40 @@ struct Fused3DTile {
             const int ia = (ty + 2) * Sh::AX + (tx + 2);
             if (check) stencil3d<N, T, Sh::AX, true>(pm, p0, pp, Sh::APLANE, ia, wall0, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::AX, false>(pm, p0, pp, Sh::APLANE, ia, 0u, c, lap, gr, gE);
-            T S[N - 1], F[3], v[3], P;
-            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, f, S, F, v, P);
-            T rec[RB::NVP];
-#pragma unroll
-            for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
-            rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
-            rec[2 * N + 1] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];   // read 18 times by the gather
-#pragma unroll
-            for (int a = 2 * N + 2; a < RB::NVP; ++a) rec[a] = T(0);
-            srec_store<T, 2 * N + 2>(bbase, Sh::BPLANE, (ty + 1) * Sh::BX + (tx + 1), rec);
+            T S[N - 1], F[3], v[3], P, sp[9], dm[9];
+            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, f, S, F, v, P, sp, dm);
+            store_B(bbase, (ty + 1) * Sh::BX + (tx + 1), c, v, S);
             if (collide && own_xy) {
-                T op, om;
-                relaxation<N, T>(cf, c, op, om);
-                const T ap = T(1) - T(0.5) * op, am = T(1) - T(0.5) * om;
-                const T vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                const T vF = v[0] * F[0] + v[1] * F[1] + v[2] * F[2];
-                const T base = T(3) * P - T(1.5) * vv;
-                // TRT with forcing (Eqs. 23-30) regrouped so that per-site factors are formed once:
-                // for a pair (k, kbar), with s = f_k + f_kbar and d = f_k - f_kbar,
-                //   sym  = w_k [X + e.v (Y e.v + Z e.F)] - (op / 2) s
-                //   anti = w_k (U e.v + V e.F) - (om / 2) d
-                // where X = op (3P - 1.5 v.v) - 3 ap v.F, Y = 4.5 op, Z = 9 ap, U = 3 om, V = 3 am;
-                // w_k X ... w_k V are shared by all pairs of one weight class.
-                const T hop = T(0.5) * op, hom = T(0.5) * om;
-                const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
-                // no wrap and no wall for any target: the site is inside the domain by one site
-                const bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && zw > 0 && zw < nz - 1;
-                sfor<1, 19, 2>([&](auto kc_) {
-                    constexpr int k = decltype(kc_)::value;
-                    const int kb = k + 1;
-                    const T wk = T(LD3Q19::w(k));
-                    const T eu = T(LD3Q19::ex(k)) * v[0] + T(LD3Q19::ey(k)) * v[1] + T(LD3Q19::ez(k)) * v[2];
-                    const T eF = T(LD3Q19::ex(k)) * F[0] + T(LD3Q19::ey(k)) * F[1] + T(LD3Q19::ez(k)) * F[2];
-                    const T sp = f[k] + f[kb], dm = f[k] - f[kb];
-                    const T sym = (wk * X + eu * ((wk * Y) * eu + (wk * Z) * eF)) - hop * sp;
-                    const T anti = ((wk * U) * eu + (wk * V) * eF) - hom * dm;
-                    // post-collision values replace f in place (each pair is read once)
-                    f[k] = f[k] + sym + anti;
-                    f[kb] = f[kb] + sym - anti;
-                });
-                // one branch around the whole store block: inside the unrolled loop the
-                // compiler would predicate both forms for every site
-                if (fast) {
-                    sfor<1, 19, 1>([&](auto kc_) {
-                        constexpr int k = decltype(kc_)::value;
-                        constexpr int dk0 = LD3Q19::ex(k);
-                        const int dk = dk0 + nx * LD3Q19::ey(k) + nxy * LD3Q19::ez(k);
-                        FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), f[k], LD3Q19::w(k), cf.fscale);
-                    });
-                } else {
-                    sfor<1, 19, 1>([&](auto kc_) {
-                        constexpr int k = decltype(kc_)::value;
-                        constexpr int kb = opp(k);
-                        if ((wall0 >> k) & 1u) {
-                            // halfway bounce-back: f_kbar(x, t+1) = post_k(x)
-                            FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k], LD3Q19::w(kb), cf.fscale);
-                        } else {
-                            const int t = wrap(sx + LD3Q19::ex(k), nx) + nx * wrap(sy + LD3Q19::ey(k), ny) +
-                                          nxy * wrap(zw + LD3Q19::ez(k), nz);
-                            FStore<SF, T>::store(fout + (k - 1) * n + t, f[k], LD3Q19::w(k), cf.fscale);
-                        }
-                    });
-                }
+                collide3d<N, T>(cf, c, v, F, P, sp, dm, f);
+                push_store3d<T, SF>(cf, fout, n, nx, ny, nz, sx, sy, zw, s0, wall0, f);
             }
         }
         // ring site
         if (ring_xy_ok) {
-            const T (&f)[19] = fr;
             const unsigned wall = check ? wall_mask3(g, hx, hy, zb) : 0u;
             T c[N], lap[N], gr[N][3], gE[3];
             const int ia = (by + 1) * Sh::AX + (bx + 1);
             if (check) stencil3d<N, T, Sh::AX, true>(pm, p0, pp, Sh::APLANE, ia, wall, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::AX, false>(pm, p0, pp, Sh::APLANE, ia, 0u, c, lap, gr, gE);
-            T S[N - 1], F[3], v[3], P;
-            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, f, S, F, v, P);
-            T rec[RB::NVP];
-#pragma unroll
-            for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
-            rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
-            rec[2 * N + 1] = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-#pragma unroll
-            for (int a = 2 * N + 2; a < RB::NVP; ++a) rec[a] = T(0);
-            srec_store<T, 2 * N + 2>(bbase, Sh::BPLANE, by * Sh::BX + bx, rec);
+            T S[N - 1], F[3], v[3], P, sp[9], dm[9];
+            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, fr, S, F, v, P, sp, dm);
+            store_B(bbase, by * Sh::BX + bx, c, v, S);
         }
     }
 
+    // Cahn-Hilliard update of the own site of plane zc from B-planes zc-1..zc+1
     template <bool CHECK>
     __device__ __forceinline__ void ch_impl(int zc, unsigned wall0) {
-        const T *bm = sB + slotB(zc - 1) * Sh::B_SLOT;
-        const T *b0 = sB + slotB(zc) * Sh::B_SLOT;
-        const T *bp = sB + slotB(zc + 1) * Sh::B_SLOT;
-        const int ib = (ty + 1) * Sh::BX + (tx + 1);
-        T r0[RB::NVP];
-        srec_load<T, 2 * N + 2>(b0, Sh::BPLANE, ib, r0);
-        const T vv0 = r0[2 * N + 1];
-        const T w0 = T(1) / T(3);
-        T acc[N - 1], lapS[N - 1];
-#pragma unroll
-        for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * vv0); lapS[e] = T(0); }   // increments only
-        sfor<1, 19, 1>([&](auto kc_) {
-            constexpr int k = decltype(kc_)::value;
-            const T wk = T(LD3Q19::w(k));
-            const int kb = opp(k);                  // source x - e_k = x + e_kbar
-            if (CHECK && ((wall0 >> kb) & 1u)) {
-                const T eu = -(T(LD3Q19::ex(k)) * r0[N - 1] + T(LD3Q19::ey(k)) * r0[N] + T(LD3Q19::ez(k)) * r0[N + 1]);
-                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
-#pragma unroll
-                for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;      // S difference is zero
-            } else {
-                const T *pl = LD3Q19::ez(kb) > 0 ? bp : (LD3Q19::ez(kb) < 0 ? bm : b0);
-                T r[RB::NVP];
-                srec_load<T, 2 * N + 2>(pl, Sh::BPLANE, ib + LD3Q19::ex(kb) + Sh::BX * LD3Q19::ey(kb), r);
-                const T eu = T(LD3Q19::ex(k)) * r[N - 1] + T(LD3Q19::ey(k)) * r[N] + T(LD3Q19::ez(k)) * r[N + 1];
-                const T uu = r[2 * N + 1];
-                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * uu);
-#pragma unroll
-                for (int e = 0; e < N - 1; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
-            }
-        });
+        T out[N - 1];
+        gather3d<N, T, Sh::BX, CHECK>(sB + slotB(zc - 1) * Sh::B_SLOT, sB + slotB(zc) * Sh::B_SLOT,
+                                      sB + slotB(zc + 1) * Sh::B_SLOT, Sh::BPLANE, (ty + 1) * Sh::BX + (tx + 1),
+                                      wall0, cf.m, out);
         const int s0 = sxy + nxy * zc;
         bool bad = false;
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) {
-            const T out = r0[e] + (acc[e] - cf.m * lapS[e]);   // S Laplacian as link differences (mass-exact)
-            Cout[e * n + s0] = out;
-            bad |= !isfinite(out);
+            Cout[e * n + s0] = out[e];
+            bad |= !isfinite(out[e]);
         }
         if (bad) atomicOr(flag, 1);
     }
@@ -425,30 +680,30 @@ struct Fused3DTile {
     }
 
     __device__ __forceinline__ void march() {
-        // warm-up: A-planes z_lo-2 .. z_lo+1, B-planes z_lo-1 and z_lo
-        T cl[ITER][N - 1];
         T fo[19], fr[19];
+        // warm-up: A-planes z_lo-2 .. z_lo+1 (all four slots), B-planes z_lo-1 and z_lo
 #pragma unroll 1
-        for (int za = z_lo - 2; za <= z_lo + 1; ++za) {
-            load_A(za, cl);
-            fill_A(za, cl);
-        }
-        __syncthreads();
+        for (int za = z_lo - 2; za <= z_lo + 1; ++za) copy_A(za);
         load_F(z_lo - 1, fo, fr);
+        cp_async_wait_all();
+#pragma unroll 1
+        for (int za = z_lo - 2; za <= z_lo + 1; ++za) finish_A(za);
+        __syncthreads();
         fill_B(z_lo - 1, false, fo, fr);
         load_F(z_lo, fo, fr);
         fill_B(z_lo, true, fo, fr);
-        load_A(z_lo + 2, cl);
+        __syncthreads();                      // A-plane z_lo - 2 is free
+        copy_A(z_lo + 2);
         load_F(z_lo + 1, fo, fr);
-        __syncthreads();
 #pragma unroll 1
         for (int zc = z_lo; zc < z_hi; ++zc) {
-            fill_A(zc + 2, cl);
+            cp_async_wait_all();
+            finish_A(zc + 2);
             __syncthreads();
             fill_B(zc + 1, zc + 1 < z_hi, fo, fr);
             __syncthreads();
-            if (zc + 1 < z_hi) {               // next plane's loads fly while this plane is gathered
-                load_A(zc + 3, cl);
+            if (zc + 1 < z_hi) {               // next plane's copies and loads fly while this plane is gathered
+                copy_A(zc + 3);
                 load_F(zc + 2, fo, fr);
             }
             ch(zc);
@@ -474,20 +729,50 @@ k_fused3d(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
     t.march();
 }
 
+// Number of z-chunks of a z-marching kernel over `tiles` x/y tiles: the count (1 .. nz / 8)
+// that best fills whole waves of `slots` resident CTAs, each chunk paying `warm` planes'
+// worth of warm-up work.
+inline int zchunks_for(int tiles, int nz, int slots, double warm) {
+    int best = 1;
+    double best_eff = -1.0;
+    const int cmax = max(1, min(nz / 8, 512));
+    for (int c = 1; c <= cmax; ++c) {
+        const int zc = (nz + c - 1) / c;
+        const int cc = (nz + zc - 1) / zc;
+        const long long ctas = (long long)tiles * cc;
+        const long long waves = (ctas + slots - 1) / slots;
+        const double eff = double(ctas) / double(waves * slots) * double(nz) / (double(cc) * (double(zc) + warm));
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = cc; }
+    }
+    return best;
+}
+
+// Resident CTAs of `kernel` on the whole GPU (SM count x CTAs per SM at this block and
+// shared-memory size).
+template <typename K>
+inline int resident_ctas(K kernel, int threads, size_t smem) {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 304;
+    }
+    return max(1, sms * max(1, per_sm));
+}
+
 template <int N, typename T, typename SF, int TX, int TY, int Q4>
 cudaError_t launch_fused3d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Fused3DShape<N, T, TX, TY>;
-    static bool attr_done = false;
-    if (!attr_done) {
+    static int slots = 0;
+    if (!slots) {
         cudaError_t e = cudaFuncSetAttribute(k_fused3d<N, T, SF, TX, TY, Q4>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
-        attr_done = true;
+        slots = resident_ctas(k_fused3d<N, T, SF, TX, TY, Q4>, TX * TY, Sh::BYTES);
     }
     const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
-    // z-chunks: enough CTAs for about three per SM, but chunks of at least 8 planes
-    int chunks = (3 * 152 + tiles - 1) / tiles;
-    chunks = max(1, min(chunks, g.nz / 8));
+    // z-chunks filling whole waves; the warm-up (4 A-planes, 2 B-planes) costs about 2.5 planes
+    int chunks = zchunks_for(tiles, g.nz, slots, 2.5);
     const int zchunk = (g.nz + chunks - 1) / chunks;
     chunks = (g.nz + zchunk - 1) / zchunk;
     const dim3 grid((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
@@ -497,24 +782,336 @@ cudaError_t launch_fused3d(const Geom &g, const Coef<T> &cf, const Buffers &b, i
     return cudaGetLastError();
 }
 
-// D3Q19 dispatch: the fused step with two tile shapes (32 x 4 and 32 x 8; the
-// wider one only where its rings fit the 227 KB of shared memory of a CTA).
+// ----------------------------------------------------------------------------
+// Split D3Q19 step: the same site arithmetic as the fused step in two z-marching kernels.
+//   k_split3d_phys: per own site, the stencil, force, flux potential and moments (from a
+//     shared-memory ring of (C, E_B) on the tile + 1-site ring, staged by cp.async), the TRT
+//     collision and push-streaming of f, and v and S written to a scratch array in HBM;
+//   k_split3d_gather: per own site, C(t+1) from a shared-memory ring of those records on the
+//     tile + 1-site ring (16-byte cp.async copies of the scratch array).
+// The scratch array holds per site the gather's whole record (C, v, S, |v|^2) in TRec planes, so
+// the gather stages it with 16- and 8-byte copies and reads every neighbour with two 16-byte
+// and one 8-byte shared load (N = 4).  No site is computed twice (the fused step recomputes S
+// and v on the tile's ring), at the cost of the record crossing HBM (write + read).  Every value
+// is computed by the same device functions in the same order as in the fused step, so both forms
+// give the same bits.
+// ----------------------------------------------------------------------------
+template <int N, typename T, int TX, int TY>
+struct Split3DShape {
+    static constexpr int RX = TX + 2, RY = TY + 2, PLANE = RX * RY;   // tile + 1-ring
+    static constexpr int SLOTS = 4;
+    static constexpr int NT = TX * TY;
+    static constexpr int ITER = (PLANE + NT - 1) / NT;
+    using RA = SRec<T, N>;               // evolved C (N-1), E_B
+    using RB = TRec<T, 2 * N + 2>;       // evolved C (N-1), vx, vy, vz, S (N-1), |v|^2
+    static constexpr size_t BYTES_A = sizeof(T) * size_t(SLOTS * RA::NVP * PLANE);
+    static constexpr size_t BYTES_B = sizeof(T) * size_t(SLOTS * RB::NVP * PLANE);
+};
+
+
+__device__ __forceinline__ int slot4(int z) { return (z + 8) & 3; }   // z >= -1
+
+// Where one CTA of a split kernel is and which ring sites it stages.
+template <int TX, int TY, int ITER, int PLANE, int RX>
+struct SplitTile {
+    int nx, ny, nz, nxy, n, tid, x0, y0, z_lo, z_hi, tx, ty, gx0, gy0, sx, sy, sxy;
+    bool edge, wallt, tiny, own_xy;
+    int roff[ITER];      // in-plane index (x + nx y) of this thread's ring sites, -1 past the plane
+
+    __device__ __forceinline__ SplitTile(const Geom &g, int zchunk) {
+        nx = g.nx; ny = g.ny; nz = g.nz;
+        nxy = nx * ny;
+        n = int(g.n);
+        tid = threadIdx.x;
+        x0 = blockIdx.x * TX;
+        y0 = blockIdx.y * TY;
+        z_lo = blockIdx.z * zchunk;
+        z_hi = min(z_lo + zchunk, nz);
+        edge = (x0 - 1 < 0) || (x0 + TX + 1 > nx) || (y0 - 1 < 0) || (y0 + TY + 1 > ny);
+        wallt = (g.wx && ((x0 - 1 < 0) || (x0 + TX + 1 > nx))) || (g.wy && ((y0 - 1 < 0) || (y0 + TY + 1 > ny)));
+        tiny = nx < TX + 2 || ny < TY + 2;
+        tx = tid % TX;
+        ty = tid / TX;
+        gx0 = x0 + tx;
+        gy0 = y0 + ty;
+        own_xy = gx0 < nx && gy0 < ny;
+        sx = edge ? pwrap(gx0, nx, tiny) : gx0;
+        sy = edge ? pwrap(gy0, ny, tiny) : gy0;
+        sxy = sx + nx * sy;
+#pragma unroll
+        for (int it = 0; it < ITER; ++it) {
+            const int i = tid + it * TX * TY;
+            if (i < PLANE) {
+                const int ly = i / RX, lx = i - ly * RX;
+                int gx = x0 + lx - 1, gy = y0 + ly - 1;
+                if (edge) {
+                    // periodic wrap; beyond a wall (or a ragged far edge) clamp to a real site:
+                    // such entries are never used by a real site
+                    gx = g.wx ? min(max(gx, 0), nx - 1) : pwrap(gx, nx, tiny);
+                    gy = g.wy ? min(max(gy, 0), ny - 1) : pwrap(gy, ny, tiny);
+                }
+                roff[it] = gx + nx * gy;
+            } else {
+                roff[it] = -1;
+            }
+        }
+    }
+    __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
+};
+
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 / (TX * TY) : 256 / (TX * TY)))
+k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
+               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk) {
+    using Sh = Split3DShape<N, T, TX, TY>;
+    using RA = typename Sh::RA;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sA = reinterpret_cast<T *>(smem_raw);
+    constexpr int ASLOT = RA::NVP * Sh::PLANE;
+    const SplitTile<TX, TY, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
+    const int n = t.n, nz = t.nz;
+
+    // start the copies of the evolved C of plane za (tile + 1-ring), one group
+    auto copy_A = [&](int za) {
+        if (!(g.wz && (za < 0 || za >= nz))) {
+            const int zo = t.nxy * t.zwrap(za);
+            T *base = sA + slot4(za) * ASLOT;
+#pragma unroll
+            for (int it = 0; it < Sh::ITER; ++it) {
+                const int i = t.tid + it * Sh::NT;
+                if (t.roff[it] >= 0) {
+#pragma unroll
+                    for (int a = 0; a < N - 1; ++a)
+                        cp_async_value<T>(base + (a / RA::PER) * Sh::PLANE * RA::PER + i * RA::PER + (a % RA::PER),
+                                          Cin + size_t(a) * n + (t.roff[it] + zo));
+                }
+            }
+        }
+        cp_async_commit();
+    };
+    // E_B of this thread's staged sites of plane za (its own copies have landed)
+    auto finish_A = [&](int za) {
+        if (g.wz && (za < 0 || za >= nz)) return;
+        T *base = sA + slot4(za) * ASLOT;
+#pragma unroll
+        for (int it = 0; it < Sh::ITER; ++it) {
+            const int i = t.tid + it * Sh::NT;
+            if (t.roff[it] >= 0) {
+                T rec[RA::NVP];
+                srec_load<T, N>(base, Sh::PLANE, i, rec);
+                T cc[N];
+                T rest = T(0);
+#pragma unroll
+                for (int a = 0; a < N - 1; ++a) { cc[a] = rec[a]; rest += rec[a]; }
+                cc[N - 1] = T(1) - rest;
+                base[((N - 1) / RA::PER) * Sh::PLANE * RA::PER + i * RA::PER + ((N - 1) % RA::PER)] =
+                    bulk_energy<N, T>(cc, cf);
+            }
+        }
+    };
+    auto load_F = [&](int zb, T (&f)[19]) {
+        f[0] = T(0);
+        if (!t.own_xy || zb >= t.z_hi) return;
+        const int s0 = t.sxy + t.nxy * zb;
+        sfor<1, 19, 1>([&](auto kc_) { constexpr int k = decltype(kc_)::value; f[k] = FStore<SF, T>::load(fin + (k - 1) * n + s0, LD3Q19::w(k), cf.finv); });
+    };
+
+    T fo[19], fn[19];
+    copy_A(t.z_lo - 1);
+    copy_A(t.z_lo);
+    load_F(t.z_lo, fo);
+    cp_async_wait_all();
+    finish_A(t.z_lo - 1);
+    finish_A(t.z_lo);
+    copy_A(t.z_lo + 1);
+#pragma unroll 1
+    for (int z = t.z_lo; z < t.z_hi; ++z) {
+        cp_async_wait_all();
+        finish_A(z + 1);
+        __syncthreads();                  // A(z-1..z+1) complete; every thread is past plane z-1
+        copy_A(z + 2);
+        load_F(z + 1, fn);
+        if (t.own_xy) {
+            const bool check = t.wallt || (g.wz && (z == 0 || z == nz - 1));
+            const unsigned wall0 = check ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
+            const T *pm = sA + slot4(z - 1) * ASLOT, *p0 = sA + slot4(z) * ASLOT, *pp = sA + slot4(z + 1) * ASLOT;
+            const int ia = (t.ty + 1) * Sh::RX + (t.tx + 1);
+            T c[N], lap[N], gr[N][3], gE[3];
+            if (check) stencil3d<N, T, Sh::RX, true>(pm, p0, pp, Sh::PLANE, ia, wall0, c, lap, gr, gE);
+            else       stencil3d<N, T, Sh::RX, false>(pm, p0, pp, Sh::PLANE, ia, 0u, c, lap, gr, gE);
+            T S[N - 1], F[3], v[3], P, sp[9], dm[9];
+            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, fo, S, F, v, P, sp, dm);
+            const int s0 = t.sxy + t.nxy * z;
+            {
+                // the gather record (C, v, S, |v|^2) of this site, TRec planes over the grid
+                using RB = typename Sh::RB;
+                T rec[RB::NVP];
+#pragma unroll
+                for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
+                rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
+                rec[2 * N + 1] = vsq3<T>(v[0], v[1], v[2]);
+                using V = typename Vec16<T>::type;
+#pragma unroll
+                for (int ch = 0; ch < RB::NC; ++ch) {
+                    V w;
+                    if constexpr (sizeof(T) == 4) { w.x = rec[4 * ch]; w.y = rec[4 * ch + 1]; w.z = rec[4 * ch + 2]; w.w = rec[4 * ch + 3]; }
+                    else { w.x = rec[2 * ch]; w.y = rec[2 * ch + 1]; }
+                    reinterpret_cast<V *>(vs + size_t(ch) * n * RB::PER)[s0] = w;
+                }
+                if constexpr (RB::TAIL == 2)
+                    reinterpret_cast<float2 *>(vs + size_t(RB::NC) * n * RB::PER)[s0] = make_float2(rec[4 * RB::NC], rec[4 * RB::NC + 1]);
+            }
+            collide3d<N, T>(cf, c, v, F, P, sp, dm, fo);
+            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, fo);
+        }
+#pragma unroll
+        for (int k = 0; k < 19; ++k) fo[k] = fn[k];
+    }
+    cp_async_wait_all();                  // no copy outlives the CTA
+}
+
+// SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
+// translation units apart: each sets the shared-memory attribute of the kernel it launches.
+template <int N, typename T, typename SF, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 / (TX * TY) : 512 / (TX * TY)))
+k_split3d_gather(Geom g, T m, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk) {
+    using Sh = Split3DShape<N, T, TX, TY>;
+    using RB = typename Sh::RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sB = reinterpret_cast<T *>(smem_raw);
+    constexpr int BSLOT = RB::NVP * Sh::PLANE;
+    const SplitTile<TX, TY, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
+    const int n = t.n, nz = t.nz;
+
+    // start the copies of the records of plane zb (tile + 1-ring), one group
+    auto copy_B = [&](int zb) {
+        if (!(g.wz && (zb < 0 || zb >= nz))) {
+            const int zo = t.nxy * t.zwrap(zb);
+            T *base = sB + slot4(zb) * BSLOT;
+#pragma unroll
+            for (int it = 0; it < Sh::ITER; ++it) {
+                const int i = t.tid + it * Sh::NT;
+                if (t.roff[it] >= 0) {
+                    const int s = t.roff[it] + zo;
+#pragma unroll
+                    for (int ch = 0; ch < RB::NC; ++ch) {
+                        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(base + size_t(ch) * Sh::PLANE * RB::PER + size_t(i) * RB::PER));
+                        const T *src = vs + size_t(ch) * n * RB::PER + size_t(s) * RB::PER;
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+                    }
+                    if constexpr (RB::TAIL == 2) {
+                        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(base + size_t(RB::NC) * Sh::PLANE * RB::PER + size_t(i) * 2));
+                        const T *src = vs + size_t(RB::NC) * n * RB::PER + size_t(s) * 2;
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+                    }
+                }
+            }
+        }
+        cp_async_commit();
+    };
+
+    copy_B(t.z_lo - 1);
+    copy_B(t.z_lo);
+    copy_B(t.z_lo + 1);
+#pragma unroll 1
+    for (int z = t.z_lo; z < t.z_hi; ++z) {
+        cp_async_wait_all();
+        __syncthreads();                  // B(z-1..z+1) complete; every thread is past plane z-1
+        copy_B(z + 2);
+        if (t.own_xy) {
+            const unsigned wall0 = (t.wallt || (g.wz && (z == 0 || z == nz - 1))) ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
+            const T *bm = sB + slot4(z - 1) * BSLOT, *b0 = sB + slot4(z) * BSLOT, *bp = sB + slot4(z + 1) * BSLOT;
+            const int ib = (t.ty + 1) * Sh::RX + (t.tx + 1);
+            T out[N - 1];
+            // the wall-free form carries no bounce-back code; the form is decided per site
+            if (wall0) gather3d<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wall0, m, out);
+            else       gather3d<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, m, out);
+            const int s0 = t.sxy + t.nxy * z;
+            bool bad = false;
+#pragma unroll
+            for (int e = 0; e < N - 1; ++e) {
+                Cout[size_t(e) * n + s0] = out[e];
+                bad |= !isfinite(out[e]);
+            }
+            if (bad) atomicOr(flag, 1);
+        }
+    }
+    cp_async_wait_all();                  // no copy outlives the CTA
+}
+
+// z-chunks of a split kernel filling whole waves of `slots` resident CTAs (the warm-up of a
+// chunk, two staged planes, costs about half a plane of work)
+inline dim3 split3d_grid(const Geom &g, int TX, int TY, int slots, int &zchunk) {
+    const int tiles = ((g.nx + TX - 1) / TX) * ((g.ny + TY - 1) / TY);
+    int chunks = zchunks_for(tiles, g.nz, slots, 0.5);
+    zchunk = (g.nz + chunks - 1) / chunks;
+    chunks = (g.nz + zchunk - 1) / zchunk;
+    return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
+}
+
+template <int N, typename T, typename SF, int TX, int TY, int Q4>
+cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
+    using Sh = Split3DShape<N, T, TX, TY>;
+    static int slots = 0;
+    if (!slots) {
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_phys<N, T, SF, TX, TY, Q4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES_A));
+        if (e != cudaSuccess) return e;
+        slots = resident_ctas(k_split3d_phys<N, T, SF, TX, TY, Q4>, TX * TY, Sh::BYTES_A);
+    }
+    int zchunk = 0;
+    const dim3 grid = split3d_grid(g, TX, TY, slots, zchunk);
+    k_split3d_phys<N, T, SF, TX, TY, Q4><<<grid, TX * TY, Sh::BYTES_A, st>>>(
+        g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]), static_cast<const T *>(b.C[cur]),
+        static_cast<T *>(b.vs), zchunk);
+    return cudaGetLastError();
+}
+
+template <int N, typename T, typename SF, int TX, int TY>
+cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
+    using Sh = Split3DShape<N, T, TX, TY>;
+    static int slots = 0;
+    if (!slots) {
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES_B));
+        if (e != cudaSuccess) return e;
+        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TY>, TX * TY, Sh::BYTES_B);
+    }
+    int zchunk = 0;
+    const dim3 grid = split3d_grid(g, TX, TY, slots, zchunk);
+    k_split3d_gather<N, T, SF, TX, TY><<<grid, TX * TY, Sh::BYTES_B, st>>>(
+        g, cf.m, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk);
+    return cudaGetLastError();
+}
+
+// D3Q19 dispatch.  Variants 0, 1: the fused step (32 x 4, 32 x 8; the wider one only where its
+// rings fit the 227 KB of shared memory of a CTA).  Variants 2, 3: the split step (32 x 8, 32 x 4),
+// two kernels per step (kern[0]: physics and streaming, kern[1]: the Cahn-Hilliard gather).
 template <int N, typename T, typename SF>
 struct Fused3DLaunch {
     static constexpr bool kWideFits = Fused3DShape<N, T, 32, 8>::BYTES <= 220 * 1024;
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        if (variant == 2) return launch_split3d_phys<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
+        if (variant == 3) return launch_split3d_phys<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
         if constexpr (kWideFits) {
             if (variant == 1) return launch_fused3d<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
         }
         return launch_fused3d<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
     }
+    static cudaError_t gather(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, 4>(g, cf, b, cur, st);
+        return launch_split3d_gather<N, T, SF, 32, 8>(g, cf, b, cur, st);
+    }
     static const Ops *ops(int prec) {
         using B = Launch<LD3Q19, N, T, SF>;
-        static const Ops o = {19, 3, N, prec, 1, {K_FUSED, K_FUSED}, {&step, nullptr}, 2,
-                              {"fused3d 32x4", "fused3d 32x8", nullptr, nullptr},
+        static const Ops o = {19, 3, N, prec, 1, {K_FUSED, K_FUSED}, {&step, &gather}, 4,
+                              {"fused3d 32x4", "fused3d 32x8", "split3d 32x8", "split3d 32x4"},
                               &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
-                              int(sizeof(SF)), int(sizeof(T))};
+                              int(sizeof(SF)), int(sizeof(T)), nullptr, nullptr, nullptr,
+                              {1, 1, 2, 2}, {{K_FUSED, K_FUSED}, {K_FUSED, K_FUSED}, {K_PHYS, K_GATHER}, {K_PHYS, K_GATHER}},
+                              TRec<T, 2 * N + 2>::NVP};
         return &o;
     }
 };

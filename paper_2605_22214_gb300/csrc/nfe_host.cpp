@@ -37,6 +37,7 @@ nfe_status fail(nfe_status s, const char *fmt, ...) {
 }
 
 nfe_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();   // a non-sticky error is reported here once, not again by the next call
     return fail(NFE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -176,7 +177,7 @@ nfe_status free_all(nfe_sim *s) {
     void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
                     s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev,
                     s->buf.g[0], s->buf.g[1], s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1],
-                    s->buf.opart};
+                    s->buf.opart, s->buf.vs};
     for (void *p : ptrs) dev_free(s, p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
@@ -225,13 +226,17 @@ cudaEvent_t get_event(nfe_sim *s) {
 
 // one time step from buffer `cur`, optionally with events around each kernel
 nfe_status launch_step(nfe_sim *s, int cur, bool timed, int variant) {
-    for (int i = 0; i < s->ops->nk; ++i) {
+    const int v = variant < 0 ? 0 : variant;
+    const bool own_list = s->ops->vnk[v] > 0;            // a variant with its own kernel list
+    const int nk = own_list ? s->ops->vnk[v] : s->ops->nk;
+    const int *kinds = own_list ? s->ops->vkinds[v] : s->ops->kinds;
+    for (int i = 0; i < nk; ++i) {
         cudaEvent_t a = nullptr, b = nullptr;
         if (timed) { a = get_event(s); b = get_event(s); CK(cudaEventRecord(a, s->stream)); }
         CK(s->ops->kern[i](s->geom, s->coef, s->buf, cur, s->stream, variant));
         if (timed) {
             CK(cudaEventRecord(b, s->stream));
-            s->timed.push_back({s->ops->kinds[i], a, b});
+            s->timed.push_back({kinds[i], a, b});
         }
     }
     return NFE_OK;
@@ -274,7 +279,7 @@ nfe_status ensure_graph(nfe_sim *s, int cur) {
     nfe_status st = launch_step(s, cur, false, s->variant);
     if (st == NFE_OK) st = launch_step(s, 1 - cur, false, s->variant);
     cudaError_t e = cudaStreamEndCapture(s->stream, &g);
-    if (st != NFE_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (st != NFE_OK) { if (g) cudaGraphDestroy(g); cudaGetLastError(); return st; }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(&s->graph[cur], g, 0);
     cudaGraphDestroy(g);
@@ -442,6 +447,7 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
         ALLOC(s->buf.g[0], s->gplanes_bytes);
         ALLOC(s->buf.g[1], s->gplanes_bytes);
     }
+    if (s->ops->scratch_planes > 0) ALLOC(s->buf.vs, size_t(s->ops->scratch_planes) * n * ce);
     if (!s->tab.q4.empty()) ALLOC(s->q4dev, s->tab.q4.size() * ce);
     if (!s->tab.r3.empty()) ALLOC(s->r3dev, s->tab.r3.size() * ce);
 #undef ALLOC
@@ -628,7 +634,8 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
     out->sites = s->geom.n;
     out->omega_stab = s->tab.omega;
     out->factor_residual = s->tab.residual;
-    out->kernels_per_step = s->ops->nk + (s->buf.outflow ? 2 : 0);   // + the convective outflow
+    const int v = s->variant < 0 ? 0 : s->variant;
+    out->kernels_per_step = (s->ops->vnk[v] > 0 ? s->ops->vnk[v] : s->ops->nk) + (s->buf.outflow ? 2 : 0);   // + the convective outflow
     out->variant = s->variant;
     out->nvariants = s->ops->nvariants;
     out->min_bytes_per_site = 2.0 * ((s->ops->Q - 1) * s->ops->f_elem_bytes + (s->N - 1) * s->ops->c_elem_bytes);

@@ -67,7 +67,8 @@ constexpr unsigned char kNodeFluid = 0, kNodeSolid = 1, kNodeInlet0 = 2, kNodeGh
 constexpr int kMaxInlets = 64;
 
 // One kernel kind for profiling.
-enum KernelKind { K_FUSED = 0, K_MOMENTS = 1, K_REDUCE = 2, K_NKINDS = 3 };
+// K_PHYS / K_GATHER: the two kernels of the split D3Q19 step.
+enum KernelKind { K_FUSED = 0, K_MOMENTS = 1, K_REDUCE = 2, K_PHYS = 3, K_GATHER = 4, K_NKINDS = 5 };
 extern const char *kKernelNames[K_NKINDS];
 
 // Device buffers of one simulation.
@@ -86,6 +87,7 @@ struct Buffers {
     void *ghost[2];              // outflow ghost column, (N-1) x ny, compute type, or null
     int outflow;                 // convective outflow on the x = nx - 1 edge
     double *opart;               // outflow partial sums (2 per 32 rows), or null
+    void *vs;                    // split D3Q19 step: per-site gather records (C, v, S, |v|^2), compute type, or null
 };
 
 // Launchers exported by the lattice translation units.  Each returns
@@ -122,6 +124,11 @@ struct Ops {
     cudaError_t (*inlet_table)(const void *coef, const double *rows, int ninl, void *out, cudaStream_t);
     cudaError_t (*geo_prepare)(const Geom &, const Buffers &, int cur, int ninl, cudaStream_t);
     cudaError_t (*moments_geo)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);
+    // variants whose step is a different number of kernels (0: nk and kinds above): kern[0 ..
+    // vnk[v] - 1] with kinds vkinds[v]
+    int vnk[kMaxVariants];
+    int vkinds[kMaxVariants][2];
+    int scratch_planes;   // planes of the compute type per site for Buffers::vs (0: none)
 };
 
 // One translation unit per lattice and precision (compiled in parallel).

@@ -5,7 +5,7 @@
 
 namespace nfe {
 
-const char *kKernelNames[K_NKINDS] = {"fused_step", "moments", "reduce"};
+const char *kKernelNames[K_NKINDS] = {"fused_step", "moments", "reduce", "step_physics", "step_gather"};
 
 // kind of diag value q: 0 = sum, 1 = sum of |.|, 2 = max |.|, 3 = min, 4 = max speed
 __device__ __forceinline__ void diag_source(int q, int N, int &plane, int &kind) {

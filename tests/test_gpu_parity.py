@@ -34,9 +34,11 @@ def oracle_run(p, steps, force_form="conservative"):
     return dict(C=C, v=v, P=P, f=st.f[1:], diag=diag)
 
 
-def gpu_run(p, steps, precision="fp64", **kw):
+def gpu_run(p, steps, precision="fp64", variant=None, **kw):
     with nfe.Sim(p, precision, **kw) as s:
         s.set_fields(p["C0"])
+        if variant is not None:
+            s.set_variant(variant)
         s.step(steps)
         s.sync()
         C, v, P = s.fields()
@@ -321,19 +323,35 @@ def test_d3q19_ragged_and_walls_fp64(shape, walls, N):
     compare(_mixture3d(nx, ny, nz, N, 40 + N, walls), 25, "fp64")
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_d3q19_variants_are_bitwise_identical(precision):
-    p = _mixture3d(37, 11, 19, 4, 9, (False, True, True))
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+@pytest.mark.parametrize("case", ["walls_yz_N4", "periodic_N5_omega"])
+def test_d3q19_variants_are_bitwise_identical(precision, case):
+    # the fused step (32x4, 32x8) and the split step (physics + gather kernels, 32x8, 32x4)
+    # compute every site with the same arithmetic
+    if case == "walls_yz_N4":
+        p = _mixture3d(37, 11, 19, 4, 9, (False, True, True))
+    else:
+        p = _mixture3d(33, 21, 17, 5, 10, (False, False, False))
+        p["omega_stab"] = 1.0 / 90.0
     states = []
     with nfe.Sim(p, precision) as s:
         nv = s.info()["nvariants"]
-        assert nv == 2
+        assert nv == 4
         for v in range(nv):
             s.set_fields(p["C0"])
             s.set_variant(v)
             s.step(13)
+            assert s.info()["kernels_per_step"] == (2 if v >= 2 else 1)
             states.append(s.get_state())
-    assert np.array_equal(states[0], states[1])
+    for st in states[1:]:
+        assert np.array_equal(st, states[0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("variant", [2, 3])
+def test_d3q19_split_step_parity_with_oracle(precision, variant):
+    # the split D3Q19 step (v and S through HBM) against the oracle directly, with walls and TRT
+    compare(_mixture3d(35, 9, 10, 4, 44, (True, True, False)), 40, precision, variant=variant)
 
 
 def test_nonfinite_flag_reported():
