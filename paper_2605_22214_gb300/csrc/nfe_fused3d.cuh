@@ -387,67 +387,160 @@ struct BRec {
     }
 };
 
+// Order in which the Cahn-Hilliard gather visits its 18 sources y = x - e_k: the directions k
+// sorted by the source offset -e_k in (z, y, x) order.  A gather of two sites stacked in y visits
+// the union of their sources in the same order, so each site sums its terms in this order too.
+constexpr int kGatherOrder[18] = {15, 11, 5, 14, 18, 7, 3, 10, 1, 2, 9, 4, 8, 17, 13, 6, 12, 16};
+
+// The D3Q19 direction k with e_k = (x, y, z): 1..18, 0 for the rest velocity, -1 if none.
+__host__ __device__ constexpr int d3q19_dir(int x, int y, int z) {
+    for (int k = 0; k < 19; ++k)
+        if (LD3Q19::ex(k) == x && LD3Q19::ey(k) == y && LD3Q19::ez(k) == z) return k;
+    return -1;
+}
+
+// One source term of the Cahn-Hilliard gather: record r of the source y = x - e_k adds
+// C_i(y) s_k(v(y)) to acc and w_k (S_i(y) - S_i(x)) to lapS (r0: the record of x).
+template <int N, typename T, int k, int NVP>
+__device__ __forceinline__ void gather_term(const T (&r)[NVP], const T (&r0)[NVP], T (&acc)[N - 1], T (&lapS)[N - 1]) {
+    constexpr int E = N - 1;
+    constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+    const T wk = T(LD3Q19::w(k));
+    // e_k . v(y) with the constant components folded (each is 0 or +-1)
+    T eu = T(0);
+    if constexpr (ex != 0) eu = ex > 0 ? r[N - 1] : -r[N - 1];
+    if constexpr (ey != 0) eu = ey > 0 ? eu + r[N] : eu - r[N];
+    if constexpr (ez != 0) eu = ez > 0 ? eu + r[N + 1] : eu - r[N + 1];
+    // s_k = w_k (3 eu + 4.5 eu^2 - 1.5 |v|^2) = eu (3 w_k + 4.5 w_k eu) - 1.5 w_k |v|^2
+    const T sk = eu * (T(3.0 * LD3Q19::w(k)) + T(4.5 * LD3Q19::w(k)) * eu) - T(1.5 * LD3Q19::w(k)) * r[2 * N + 1];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int e = 0; e + 1 < E; e += 2) {
+            const float2 cy = make_float2(r[e], r[e + 1]);
+            const float2 ds = sub2(make_float2(r[N + 2 + e], r[N + 3 + e]), make_float2(r0[N + 2 + e], r0[N + 3 + e]));
+            const float2 a = fma2(cy, dup2(sk), make_float2(acc[e], acc[e + 1]));
+            const float2 l = fma2(dup2(float(LD3Q19::w(k))), ds, make_float2(lapS[e], lapS[e + 1]));
+            acc[e] = a.x; acc[e + 1] = a.y; lapS[e] = l.x; lapS[e + 1] = l.y;
+        }
+        if constexpr (E % 2 == 1) {
+            acc[E - 1] += r[E - 1] * sk;
+            lapS[E - 1] += wk * (r[N + 1 + E] - r0[N + 1 + E]);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
+    }
+}
+
+// The bounce-back term of direction k (source beyond a wall): the link carries g^eq_kbar(x),
+// C_i(x) s_kbar(v(x)), and no S difference.
+template <int N, typename T, int k, int NVP>
+__device__ __forceinline__ void bounce_term(const T (&r0)[NVP], T (&acc)[N - 1]) {
+    const T wk = T(LD3Q19::w(k));
+    const T eu = -(T(LD3Q19::ex(k)) * r0[N - 1] + T(LD3Q19::ey(k)) * r0[N] + T(LD3Q19::ez(k)) * r0[N + 1]);
+    const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * r0[2 * N + 1]);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;
+}
+
+// Start of a gather: the rest population's increment C_i(x) s_0(v(x)).
+template <int N, typename T, int NVP>
+__device__ __forceinline__ void gather_init(const T (&r0)[NVP], T (&acc)[N - 1], T (&lapS)[N - 1]) {
+    const T w0 = T(1) / T(3);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * r0[2 * N + 1]); lapS[e] = T(0); }
+}
+
+// End of a gather: C(x) + increments, the S Laplacian as link differences (mass-exact).
+template <int N, typename T, int NVP>
+__device__ __forceinline__ void gather_final(const T (&r0)[NVP], const T (&acc)[N - 1], const T (&lapS)[N - 1], T m,
+                                             T (&out)[N - 1]) {
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) out[e] = r0[e] + (acc[e] - m * lapS[e]);
+}
+
 // Cahn-Hilliard update (Eqs. 39-41, tau_g = 1) of one site from the (C, v, S, |v|^2) records of
 // three planes (below, centre, above) at in-plane index ib (row pitch BX):
 // C_i(x, t+1) = C_i(x) + sum_k C_i(y) s_k(v(y)) + m sum_{k != 0} w_k (S_i(x) - S_i(y)), y = x - e_k,
 // the increments gathered before C(x) is added and the S Laplacian as link differences, so
-// that every link's two contributions cancel exactly.  A source beyond a wall bounces back:
-// the link then carries g^eq_kbar(x), i.e. C_i(x) s_kbar(v(x)) and no S difference.
+// that every link's two contributions cancel exactly.  A source beyond a wall bounces back
+// (wall0 bit kbar set for the source x - e_k = x + e_kbar).
 template <int N, typename T, int BX, bool CHECK, bool TAILREC = false>
 __device__ __forceinline__ void gather3d(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned wall0,
                                          T m, T (&out)[N - 1]) {
     using RB = BRec<T, 2 * N + 2, TAILREC>;
-    constexpr int E = N - 1;             // evolved components
     T r0[RB::NVP];
     RB::load(b0, bplane, ib, r0);
-    const T vv0 = r0[2 * N + 1];
-    const T w0 = T(1) / T(3);
-    T acc[E], lapS[E];
-    // rest population's increment: C_i(x) s_0(v(x))
-#pragma unroll
-    for (int e = 0; e < E; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * vv0); lapS[e] = T(0); }
-    sfor<1, 19, 1>([&](auto kc_) {
-        constexpr int k = decltype(kc_)::value;
-        constexpr int kb = opp(k);                  // source x - e_k = x + e_kbar
-        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
-        const T wk = T(LD3Q19::w(k));
+    T acc[N - 1], lapS[N - 1];
+    gather_init<N, T>(r0, acc, lapS);
+    sfor<0, 18, 1>([&](auto jc_) {
+        constexpr int k = kGatherOrder[decltype(jc_)::value];
+        constexpr int kb = opp(k);
         if (CHECK && ((wall0 >> kb) & 1u)) {
-            const T eu = -(T(ex) * r0[N - 1] + T(ey) * r0[N] + T(ez) * r0[N + 1]);
-            const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * vv0);
-#pragma unroll
-            for (int e = 0; e < E; ++e) acc[e] += r0[e] * sk;      // S difference is zero
+            bounce_term<N, T, k>(r0, acc);
         } else {
             const T *pl = LD3Q19::ez(kb) > 0 ? bp : (LD3Q19::ez(kb) < 0 ? bm : b0);
             T r[RB::NVP];
             RB::load(pl, bplane, ib + LD3Q19::ex(kb) + BX * LD3Q19::ey(kb), r);
-            // e_k . v(y) with the constant components folded (each is 0 or +-1)
-            T eu = T(0);
-            if constexpr (ex != 0) eu = ex > 0 ? r[N - 1] : -r[N - 1];
-            if constexpr (ey != 0) eu = ey > 0 ? eu + r[N] : eu - r[N];
-            if constexpr (ez != 0) eu = ez > 0 ? eu + r[N + 1] : eu - r[N + 1];
-            // s_k = w_k (3 eu + 4.5 eu^2 - 1.5 |v|^2) = eu (3 w_k + 4.5 w_k eu) - 1.5 w_k |v|^2
-            const T sk = eu * (T(3.0 * LD3Q19::w(k)) + T(4.5 * LD3Q19::w(k)) * eu) - T(1.5 * LD3Q19::w(k)) * r[2 * N + 1];
-            if constexpr (sizeof(T) == 4) {
+            gather_term<N, T, k>(r, r0, acc, lapS);
+        }
+    });
+    gather_final<N, T>(r0, acc, lapS, m, out);
+}
+
+// The same update for two sites stacked in y (a at ib, b at ib + BX), sharing the loads of the
+// records both need: 28 record loads for the two instead of 38.  Each site sums its terms in the
+// order of kGatherOrder, as the one-site form does, so both give the same bits.
+template <int N, typename T, int BX, bool CHECK, bool TAILREC>
+__device__ __forceinline__ void gather3d_pair(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned walla,
+                                              unsigned wallb, T m, T (&outa)[N - 1], T (&outb)[N - 1]) {
+    using RB = BRec<T, 2 * N + 2, TAILREC>;
+    T ra[RB::NVP], rb[RB::NVP];
+    RB::load(b0, bplane, ib, ra);
+    RB::load(b0, bplane, ib + BX, rb);
+    T acca[N - 1], lapa[N - 1], accb[N - 1], lapb[N - 1];
+    gather_init<N, T>(ra, acca, lapa);
+    gather_init<N, T>(rb, accb, lapb);
+    // positions (dx, dy, dz) relative to site a, dz then dy in -1..2 then dx ascending
+    sfor<0, 36, 1>([&](auto pc_) {
+        constexpr int pidx = decltype(pc_)::value;
+        constexpr int dz = pidx / 12 - 1, dy = (pidx / 3) % 4 - 1, dx = pidx % 3 - 1;
+        // a source of site a / of site b: a D3Q19 neighbour offset (not the site itself)
+        constexpr int ka = d3q19_dir(-dx, -dy, -dz);
+        constexpr int kb2 = d3q19_dir(-dx, 1 - dy, -dz);
+        if constexpr (ka > 0 || kb2 > 0) {
+            // source beyond a wall: bounce-back instead of the neighbour's record
+            const bool bba = CHECK && ka > 0 && ((walla >> (ka > 0 ? opp(ka) : 0)) & 1u);
+            const bool bbb = CHECK && kb2 > 0 && ((wallb >> (kb2 > 0 ? opp(kb2) : 0)) & 1u);
+            // the records of the two sites themselves are already in registers
+            constexpr bool is_a = dx == 0 && dy == 0 && dz == 0, is_b = dx == 0 && dy == 1 && dz == 0;
+            T r[RB::NVP];
+            if constexpr (is_a) {
 #pragma unroll
-                for (int e = 0; e + 1 < E; e += 2) {
-                    const float2 cy = make_float2(r[e], r[e + 1]);
-                    const float2 ds = sub2(make_float2(r[N + 2 + e], r[N + 3 + e]), make_float2(r0[N + 2 + e], r0[N + 3 + e]));
-                    const float2 a = fma2(cy, dup2(sk), make_float2(acc[e], acc[e + 1]));
-                    const float2 l = fma2(dup2(float(LD3Q19::w(k))), ds, make_float2(lapS[e], lapS[e + 1]));
-                    acc[e] = a.x; acc[e + 1] = a.y; lapS[e] = l.x; lapS[e + 1] = l.y;
-                }
-                if constexpr (E % 2 == 1) {
-                    acc[E - 1] += r[E - 1] * sk;
-                    lapS[E - 1] += wk * (r[N + 1 + E] - r0[N + 1 + E]);
-                }
+                for (int q = 0; q < RB::NVP; ++q) r[q] = ra[q];
+            } else if constexpr (is_b) {
+#pragma unroll
+                for (int q = 0; q < RB::NVP; ++q) r[q] = rb[q];
             } else {
 #pragma unroll
-                for (int e = 0; e < E; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
+                for (int q = 0; q < RB::NVP; ++q) r[q] = T(0);
+                if ((ka > 0 && !bba) || (kb2 > 0 && !bbb)) {
+                    const T *pl = dz > 0 ? bp : (dz < 0 ? bm : b0);
+                    RB::load(pl, bplane, ib + dx + BX * dy, r);
+                }
+            }
+            if constexpr (ka > 0) {
+                if (bba) bounce_term<N, T, ka>(ra, acca);
+                else gather_term<N, T, ka>(r, ra, acca, lapa);
+            }
+            if constexpr (kb2 > 0) {
+                if (bbb) bounce_term<N, T, kb2>(rb, accb);
+                else gather_term<N, T, kb2>(r, rb, accb, lapb);
             }
         }
     });
-#pragma unroll
-    for (int e = 0; e < E; ++e) out[e] = r0[e] + (acc[e] - m * lapS[e]);   // S Laplacian as link differences (mass-exact)
+    gather_final<N, T>(ra, acca, lapa, m, outa);
+    gather_final<N, T>(rb, accb, lapb, m, outb);
 }
 
 // Bit k set when x + e_k lies beyond a wall.
@@ -803,16 +896,16 @@ struct Split3DShape {
     static constexpr int NT = TX * TY;
     static constexpr int ITER = (PLANE + NT - 1) / NT;
     using RA = SRec<T, N>;               // evolved C (N-1), E_B
-    using RB = TRec<T, 2 * N + 2>;       // evolved C (N-1), vx, vy, vz, S (N-1), |v|^2
+    using RB = TRec<T, 2 * N + 2>;       // the gather record written to the scratch array
     static constexpr size_t BYTES_A = sizeof(T) * size_t(SLOTS * RA::NVP * PLANE);
-    static constexpr size_t BYTES_B = sizeof(T) * size_t(SLOTS * RB::NVP * PLANE);
 };
 
 
 __device__ __forceinline__ int slot4(int z) { return (z + 8) & 3; }   // z >= -1
 
-// Where one CTA of a split kernel is and which ring sites it stages.
-template <int TX, int TY, int ITER, int PLANE, int RX>
+// Where one CTA of a split kernel is and which ring sites it stages: a TX x TY tile of sites,
+// NT threads (thread t owns site (t % TX, t / TX) when NT = TX * TY).
+template <int TX, int TY, int NT, int ITER, int PLANE, int RX>
 struct SplitTile {
     int nx, ny, nz, nxy, n, tid, x0, y0, z_lo, z_hi, tx, ty, gx0, gy0, sx, sy, sxy;
     bool edge, wallt, tiny, own_xy;
@@ -840,7 +933,7 @@ struct SplitTile {
         sxy = sx + nx * sy;
 #pragma unroll
         for (int it = 0; it < ITER; ++it) {
-            const int i = tid + it * TX * TY;
+            const int i = tid + it * NT;
             if (i < PLANE) {
                 const int ly = i / RX, lx = i - ly * RX;
                 int gx = x0 + lx - 1, gy = y0 + ly - 1;
@@ -868,7 +961,7 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sA = reinterpret_cast<T *>(smem_raw);
     constexpr int ASLOT = RA::NVP * Sh::PLANE;
-    const SplitTile<TX, TY, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
+    const SplitTile<TX, TY, Sh::NT, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
     const int n = t.n, nz = t.nz;
 
     // start the copies of the evolved C of plane za (tile + 1-ring), one group
@@ -970,18 +1063,36 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
     cp_async_wait_all();                  // no copy outlives the CTA
 }
 
+// Shape of the gather kernel: TX x (2 TYT) sites, TX x TYT threads, two sites stacked in y each.
+template <int N, typename T, int TX, int TYT>
+struct Gather3DShape {
+    static constexpr int TY = 2 * TYT;
+    static constexpr int RX = TX + 2, RY = TY + 2, PLANE = RX * RY;   // tile + 1-ring
+    static constexpr int SLOTS = 4;
+    static constexpr int NT = TX * TYT;
+    static constexpr int ITER = (PLANE + NT - 1) / NT;
+    using RB = TRec<T, 2 * N + 2>;
+    static constexpr size_t BYTES = sizeof(T) * size_t(SLOTS * RB::NVP * PLANE);
+};
+
 // SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
 // translation units apart: each sets the shared-memory attribute of the kernel it launches.
-template <int N, typename T, typename SF, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 768 / (TX * TY) : 512 / (TX * TY)))
+template <int N, typename T, typename SF, int TX, int TYT>
+__global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 ? 512 / (TX * TYT) : 256 / (TX * TYT)))
 k_split3d_gather(Geom g, T m, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk) {
-    using Sh = Split3DShape<N, T, TX, TY>;
+    using Sh = Gather3DShape<N, T, TX, TYT>;
     using RB = typename Sh::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sB = reinterpret_cast<T *>(smem_raw);
     constexpr int BSLOT = RB::NVP * Sh::PLANE;
-    const SplitTile<TX, TY, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
-    const int n = t.n, nz = t.nz;
+    const SplitTile<TX, Sh::TY, Sh::NT, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
+    const int n = t.n, nz = t.nz, nx = t.nx, ny = t.ny;
+    // this thread's two sites: column tx, rows 2 r and 2 r + 1 of the tile
+    const int tx = t.tid % TX, tr = t.tid / TX;
+    const int gx = t.x0 + tx, gya = t.y0 + 2 * tr, gyb = gya + 1;
+    const bool own_a = gx < nx && gya < ny, own_b = gx < nx && gyb < ny;
+    const int sxa = t.edge ? pwrap(gx, nx, t.tiny) : gx;
+    const int sya = t.edge ? pwrap(gya, ny, t.tiny) : gya, syb = t.edge ? pwrap(gyb, ny, t.tiny) : gyb;
 
     // start the copies of the records of plane zb (tile + 1-ring), one group
     auto copy_B = [&](int zb) {
@@ -1018,20 +1129,29 @@ k_split3d_gather(Geom g, T m, const T *__restrict__ vs, T *__restrict__ Cout, in
         cp_async_wait_all();
         __syncthreads();                  // B(z-1..z+1) complete; every thread is past plane z-1
         copy_B(z + 2);
-        if (t.own_xy) {
-            const unsigned wall0 = (t.wallt || (g.wz && (z == 0 || z == nz - 1))) ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
+        if (own_a) {
+            const bool check = t.wallt || (g.wz && (z == 0 || z == nz - 1));
+            const unsigned wa = check ? wall_mask3(g, gx, gya, z) : 0u;
+            const unsigned wb = check && own_b ? wall_mask3(g, gx, gyb, z) : 0u;
             const T *bm = sB + slot4(z - 1) * BSLOT, *b0 = sB + slot4(z) * BSLOT, *bp = sB + slot4(z + 1) * BSLOT;
-            const int ib = (t.ty + 1) * Sh::RX + (t.tx + 1);
-            T out[N - 1];
-            // the wall-free form carries no bounce-back code; the form is decided per site
-            if (wall0) gather3d<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wall0, m, out);
-            else       gather3d<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, m, out);
-            const int s0 = t.sxy + t.nxy * z;
+            const int ib = (2 * tr + 1) * Sh::RX + (tx + 1);
+            T outa[N - 1], outb[N - 1];
+            // the wall-free form carries no bounce-back code; the form is decided per thread
+            if (wa | wb) gather3d_pair<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wa, wb, m, outa, outb);
+            else         gather3d_pair<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, 0u, m, outa, outb);
+            const int sa = sxa + nx * sya + t.nxy * z, sb = sxa + nx * syb + t.nxy * z;
             bool bad = false;
 #pragma unroll
             for (int e = 0; e < N - 1; ++e) {
-                Cout[size_t(e) * n + s0] = out[e];
-                bad |= !isfinite(out[e]);
+                Cout[size_t(e) * n + sa] = outa[e];
+                bad |= !isfinite(outa[e]);
+            }
+            if (own_b) {
+#pragma unroll
+                for (int e = 0; e < N - 1; ++e) {
+                    Cout[size_t(e) * n + sb] = outb[e];
+                    bad |= !isfinite(outb[e]);
+                }
             }
             if (bad) atomicOr(flag, 1);
         }
@@ -1067,19 +1187,19 @@ cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers 
     return cudaGetLastError();
 }
 
-template <int N, typename T, typename SF, int TX, int TY>
+template <int N, typename T, typename SF, int TX, int TYT>
 cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
-    using Sh = Split3DShape<N, T, TX, TY>;
+    using Sh = Gather3DShape<N, T, TX, TYT>;
     static int slots = 0;
     if (!slots) {
-        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES_B));
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
-        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TY>, TX * TY, Sh::BYTES_B);
+        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT>, TX * TYT, Sh::BYTES);
     }
     int zchunk = 0;
-    const dim3 grid = split3d_grid(g, TX, TY, slots, zchunk);
-    k_split3d_gather<N, T, SF, TX, TY><<<grid, TX * TY, Sh::BYTES_B, st>>>(
+    const dim3 grid = split3d_grid(g, TX, Sh::TY, slots, zchunk);
+    k_split3d_gather<N, T, SF, TX, TYT><<<grid, TX * TYT, Sh::BYTES, st>>>(
         g, cf.m, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk);
     return cudaGetLastError();
 }
@@ -1090,6 +1210,10 @@ cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffer
 template <int N, typename T, typename SF>
 struct Fused3DLaunch {
     static constexpr bool kWideFits = Fused3DShape<N, T, 32, 8>::BYTES <= 220 * 1024;
+    template <int TYT> static constexpr bool gather_fits = Gather3DShape<N, T, 32, TYT>::BYTES <= 220 * 1024;
+    static constexpr int kGatherLarge = gather_fits<8> ? 8 : (gather_fits<4> ? 4 : 2);
+    static constexpr int kGatherSmall = gather_fits<4> ? 4 : 2;
+    static_assert(gather_fits<2>, "the smallest gather tile fits");
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         if (variant == 2) return launch_split3d_phys<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
@@ -1101,8 +1225,10 @@ struct Fused3DLaunch {
     }
     static cudaError_t gather(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
-        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, 4>(g, cf, b, cur, st);
-        return launch_split3d_gather<N, T, SF, 32, 8>(g, cf, b, cur, st);
+        // two sites per thread: 32 x 16 sites on 256 threads (variant 2), 32 x 8 on 128 (variant 3),
+        // or the next smaller tile whose four record planes fit a CTA's shared memory
+        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, kGatherSmall>(g, cf, b, cur, st);
+        return launch_split3d_gather<N, T, SF, 32, kGatherLarge>(g, cf, b, cur, st);
     }
     static const Ops *ops(int prec) {
         using B = Launch<LD3Q19, N, T, SF>;
