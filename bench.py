@@ -5,16 +5,18 @@ Headline workload: four Janus droplets in a 256^3 periodic box, D3Q19, N = 4
 (drops of radius 32 split by the plane x = x_c, sigma_ij ~ U(0.004, 0.012)
 from seed 1004, tau = 1, m = 1/50), FP32 path.  One bench step = one time step
 of the whole lattice (stencils, flux potential, conservative force,
-collide+stream of f, Cahn-Hilliard update of C): one launch of the fused
-D3Q19 kernel.  The working set (two 1.4 GB state buffers) is far larger than
-the 129 MB L2, so steps run back to back; CUDA events on the library's
+collide+stream of f, Cahn-Hilliard update of C): the form of the D3Q19 step
+the library's autotuner picked (the fused kernel, or the split physics and
+gather kernels).  The working set (two 1.4 GB state buffers) is far larger
+than the 129 MB L2, so steps run back to back; CUDA events on the library's
 stream bracket the timed steps.
 
 Metric: MLUPS x N (million lattice-site updates per second times the number
 of components) of the FP32 path (headline `value`), the FP64 path on the same
-lattice beside it (`fp64_path`).  `roofline`: the fused kernel's algorithmic
-bytes (each population and volume fraction read once and written once) per
-launch over its launch time, against the measured HBM copy bandwidth.
+lattice beside it (`fp64_path`).  `roofline`: the step's algorithmic bytes
+(each population and volume fraction read once and written once) over the
+step's time, against the measured HBM copy bandwidth, with every kernel of
+the step beside it (`per_kernel`, each with its own algorithmic bytes).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl nfe|reference]
 
@@ -95,9 +97,9 @@ def _sources_sha(files):
 
 
 def captured_traffic(name, variant):
-    """DRAM bytes per launch of a kernel from a committed ncu capture (profiles/<name>.json, one
-    value per tile shape), or None when the kernel sources changed since that capture or the
-    shape was not captured."""
+    """DRAM bytes of one time step (summed over its launches) from a committed ncu capture
+    (profiles/<name>.json, per tile-shape variant), or None when the kernel sources changed since
+    that capture or the variant was not captured."""
     path = os.path.join(ROOT, "profiles", name + ".json")
     if not os.path.exists(path):
         return None
@@ -105,7 +107,8 @@ def captured_traffic(name, variant):
         rec = json.load(fh)
     if _sources_sha(rec["sources"]) != rec["source_sha256"]:
         return None
-    return rec["dram_bytes_per_launch"].get(str(variant))
+    v = rec["dram_bytes_per_step"].get(str(variant))
+    return None if v is None else float(sum(v.values()))
 
 
 def _dist():
@@ -412,21 +415,42 @@ def run_nfe(args):
     e2e_val = ws * n * Ke * N / e2e_s / 1e6
     del hbuf
 
-    def roofline(r, traffic_name=None):
+    def kernel_bytes(kind, info, prec):
+        """Algorithmic bytes per site of one kernel of the step: every array it must read or write,
+        once (the split D3Q19 step moves its gather records through HBM)."""
+        fb = {"fp64": 8, "fp32": 4, "f16": 2, "bf16": 2}[prec]
+        cb = 8 if prec == "fp64" else 4
+        Q = 19
+        rec = 2 * N + 2
+        if kind == "step_physics":
+            return 2 * (Q - 1) * fb + (N - 1) * cb + rec * cb
+        if kind == "step_gather":
+            return rec * cb + (N - 1) * cb
+        return info["min_bytes_per_site"]
+
+    def roofline(r, prec, traffic_name=None):
+        """The step against the HBM roofline: its algorithmic bytes (each population and volume
+        fraction read once and written once) over the step's time from the timed region's events
+        (which bracket every launch of the step), and the same for each kernel of the step with its
+        own algorithmic bytes and its library-event time."""
         kt = r["kt"]
-        dom = max(kt, key=lambda k: kt[k][0] * kt[k][1])
-        bps = r["info"]["min_bytes_per_site"]
-        # one fused launch per step: the timed region's CUDA events bracket exactly its launches
-        one = r["info"]["kernels_per_step"] == 1
-        kms = r["ms_step"] if one else kt[dom][1]
-        ach = bps * n / (kms * 1e-3) / 1e9
-        traffic = captured_traffic(traffic_name, r["info"]["variant"]) if traffic_name else None
-        return dict(bound="hbm", kernel=dom, variant=r["info"]["variant"], bytes_per_site=bps,
-                    algorithmic_bytes=bps * n, achieved=round(ach, 1), peak=hbm, unit="GB/s",
-                    frac=round(ach / hbm, 4), peak_source=peak_kind, traffic=traffic,
-                    kernel_ms=round(kms, 5), kernel_ms_profile_events=round(kt[dom][1], 5),
-                    timing="CUDA events over the timed region on the library stream" if one else
-                           "library CUDA events around each launch")
+        info = r["info"]
+        bps = info["min_bytes_per_site"]
+        step_ms = r["ms_step"]
+        ach = bps * n / (step_ms * 1e-3) / 1e9
+        traffic = captured_traffic(traffic_name, info["variant"]) if traffic_name else None
+        per_kernel = {}
+        for kind, (cnt, ms) in kt.items():
+            kb = kernel_bytes(kind, info, prec)
+            a = kb * n / (ms * 1e-3) / 1e9
+            per_kernel[kind] = dict(launches=cnt, avg_ms=round(ms, 5), bytes_per_site=kb, achieved=round(a, 1),
+                                    frac=round(a / hbm, 4))
+        return dict(bound="hbm", kernel=" + ".join(sorted(kt)), variant=info["variant"],
+                    launches_per_step=info["kernels_per_step"], bytes_per_site=bps, algorithmic_bytes=bps * n,
+                    achieved=round(ach, 1), peak=hbm, unit="GB/s", frac=round(ach / hbm, 4), peak_source=peak_kind,
+                    traffic=traffic, step_ms=round(step_ms, 5),
+                    timing="CUDA events around the timed steps on the library stream",
+                    per_kernel=per_kernel)
 
     def path_summary(r):
         mlups = ws * n / (r["ms_step"] * 1e-3) / 1e6
@@ -438,7 +462,7 @@ def run_nfe(args):
 
     s32 = path_summary(r32)
     s64 = path_summary(results["fp64"])
-    s64["roofline"] = roofline(results["fp64"])
+    s64["roofline"] = roofline(results["fp64"], "fp64")
     line = {
         "metric": METRIC,
         "value": s32["value"],
@@ -456,7 +480,7 @@ def run_nfe(args):
         "mlups": s32["mlups"],
         "effective_gbs": s32["effective_gbs"],
         "effective_frac": s32["effective_frac"],
-        "roofline": roofline(r32, "traffic_fused3d_janus256_N4"),
+        "roofline": roofline(r32, "fp32", "traffic_step3d_janus256_N4"),
         "kernels": s32["kernels"],
         "fp64_path": s64,
         "e2e": {"value": round(e2e_val, 1), "unit": UNIT, "h2d_bytes_per_step": nbytes,
