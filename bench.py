@@ -387,6 +387,8 @@ def run_nfe(args):
         K = args.steps if prec == "fp32" else max(1, args.steps // 4)
         sim = nfe.Sim(p, prec, stream=stream.cuda_stream)
         sim.set_fields(p["C0"])
+        if prec == "fp32" and args.variant >= 0:
+            sim.set_variant(args.variant)       # a fixed form instead of the autotuner's pick
         clocks = Clocks(local) if prec == "fp32" else None
         ms_total = max_over_ranks(timed(sim, K, args.warmup, clocks))
         info = sim.info()
@@ -753,6 +755,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workloads, sizes and formats")
     ap.add_argument("--batch-steps", type=int, default=5000, help="steps of the batched sweep (c5: 5000)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="form of the headline FP32 step (-1: the library's autotuner picks; a profiler "
+                         "distorts the autotuner's trial timings, so profiled runs name the form)")
     ap.add_argument("--precision-study", action="store_true",
                     help="also run the c4 precision study at 256^3, radius 32, 5000 steps (a few minutes)")
     args = ap.parse_args()

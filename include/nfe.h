@@ -74,8 +74,8 @@ enum {
     NFE_NONCONSERVATIVE_FORCE = 1,  /* F_s = sum_i mu_i grad C_i (Eq. 31) instead of Eq. 34 */
     NFE_NO_PHI = 2                  /* drop phi_j from the flux potential (Eq. 12): the ablation in
                                        which an absent component nucleates at interfaces (Sec. IV).
-                                       D2Q9 single simulations only; nfe_create returns
-                                       NFE_EUNSUPPORTED for D3Q19, nfe_batch_create for batches */
+                                       Single simulations only (D3Q19: the split form of the step);
+                                       nfe_batch_create returns NFE_EUNSUPPORTED for batches */
 };
 
 #define NFE_MAX_N 8
@@ -116,9 +116,9 @@ typedef struct {
     double tau_g;             /* relaxation time of the component populations g (Sec. III B); 0 or 1
                                  selects tau_g = 1, where g* = g^eq and g needs no storage.  Other
                                  values (> 1/2) store the N-1 evolved components' g populations
-                                 ((N-1) x Q planes, two buffers, compute type) and run D2Q9 single
-                                 simulations only: NFE_EUNSUPPORTED for D3Q19, for batches and
-                                 together with NFE_NO_PHI */
+                                 ((N-1) x Q planes, two buffers, compute type); single simulations
+                                 only (D3Q19: the split form of the step): NFE_EUNSUPPORTED for
+                                 batches, with a geometry and together with NFE_NO_PHI */
     double component_force[3];    /* a body force acting on one component in proportion to its
                                      volume fraction, F += C_c F_c (the PaLS study of Sec. V drives
                                      only the droplet of fluid 2); all zero = none */

@@ -4,6 +4,10 @@
 #include "nfe_fused2d.cuh"
 
 namespace nfe {
-const Ops *ops_d2q9_fp64_hi(int N);
-const Ops *ops_d2q9_fp64(int N) { return N <= 4 ? ops_fused2d_lo<double, double>(N, NFE_FP64) : ops_d2q9_fp64_hi(N); }
+const Ops *ops_d2q9_fp64_n56(int N);
+const Ops *ops_d2q9_fp64_n78(int N);
+const Ops *ops_d2q9_fp64(int N) {
+    if (N <= 4) return ops_fused2d_lo<double, double>(N, NFE_FP64);
+    return N <= 6 ? ops_d2q9_fp64_n56(N) : ops_d2q9_fp64_n78(N);
+}
 }  // namespace nfe

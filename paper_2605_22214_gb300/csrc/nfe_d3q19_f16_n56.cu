@@ -1,0 +1,9 @@
+// D3Q19 time-step kernels, N = 5, 6, f16 storage/arithmetic variant.
+#include "nfe_fused3d.cuh"
+
+namespace nfe {
+const Ops *ops_d3q19_f16_n56(int N) {
+    if (N == 5) return ops_fused3d_one<5, float, __half>(NFE_FP32_F16STORE); if (N == 6) return ops_fused3d_one<6, float, __half>(NFE_FP32_F16STORE);
+    return nullptr;
+}
+}  // namespace nfe

@@ -1,8 +1,19 @@
-// D3Q19 time-step kernels, N = 2 .. 4, fp64 storage/arithmetic variant (fused z-marching
-// step, two tile shapes), and the dispatch over N.
+// D3Q19 time-step kernels, N = 2, 3, fp64 storage/arithmetic variant, and the dispatch over N
+// (N = 4, 5..6 and 7..8 are compiled in their own translation units, in parallel).
 #include "nfe_fused3d.cuh"
 
 namespace nfe {
-const Ops *ops_d3q19_fp64_hi(int N);
-const Ops *ops_d3q19_fp64(int N) { return N <= 4 ? ops_fused3d_lo<double, double>(N, NFE_FP64) : ops_d3q19_fp64_hi(N); }
+const Ops *ops_d3q19_fp64_n4(int N);
+const Ops *ops_d3q19_fp64_n56(int N);
+const Ops *ops_d3q19_fp64_n78(int N);
+const Ops *ops_d3q19_fp64(int N) {
+    switch (N) {
+        case 2: return ops_fused3d_one<2, double, double>(NFE_FP64);
+        case 3: return ops_fused3d_one<3, double, double>(NFE_FP64);
+        case 4: return ops_d3q19_fp64_n4(N);
+        case 5: case 6: return ops_d3q19_fp64_n56(N);
+        case 7: case 8: return ops_d3q19_fp64_n78(N);
+        default: return nullptr;
+    }
+}
 }  // namespace nfe

@@ -514,10 +514,13 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         // w_k X ... w_k V are shared by all pairs of one weight class.
         const T hop = T(0.5) * op, hom = T(0.5) * om;
         const T X = op * base - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om, V = T(3) * am;
-        // no wrap and no wall for any target: the site is inside the domain by one site
-        bool fast = sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && (!GEO || open0 == 0u);
-        // GEO: the general store block gives the same stores for a fast site; one choice per warp
-        if constexpr (GEO) fast = __all_sync(__activemask(), fast);
+        // GEO: plain neighbour offsets for a site inside the domain by one site with only fluid
+        // neighbours (the general store block gives the same stores there; one choice per warp).
+        // Otherwise every site without an adjacent wall takes one store sequence with the periodic
+        // wrap folded into its neighbour offsets, so the sites of a warp do not diverge at the edges.
+        bool fast;
+        if constexpr (GEO) fast = __all_sync(__activemask(), sx > 0 && sx < nx - 1 && sy > 0 && sy < ny - 1 && open0 == 0u);
+        else fast = wall0 == 0u;
         if constexpr (sizeof(T) == 4) {
             // FP32: the two pairs of one weight class share every instruction, pair (1, 2) or
             // (5, 6) in the first lane and (3, 4) or (7, 8) in the second
@@ -550,12 +553,25 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
         // one branch around the whole store block: inside the unrolled loop the compiler
         // would predicate both forms for every site
         if (fast) {
-            sfor<1, 9, 1>([&](auto kc_) {
-                constexpr int k = decltype(kc_)::value;
-                constexpr int dk0 = LD2Q9::ex(k);
-                const int dk = dk0 + nx * LD2Q9::ey(k);
-                FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), f[k], LD2Q9::w(k), cf.fscale);
-            });
+            if constexpr (GEO) {
+                sfor<1, 9, 1>([&](auto kc_) {
+                    constexpr int k = decltype(kc_)::value;
+                    constexpr int dk0 = LD2Q9::ex(k);
+                    const int dk = dk0 + nx * LD2Q9::ey(k);
+                    FStore<SF, T>::store(fout + (k - 1) * n + (s0 + dk), f[k], LD2Q9::w(k), cf.fscale);
+                });
+            } else {
+                const int dxp = sx == nx - 1 ? 1 - nx : 1, dxm = sx == 0 ? nx - 1 : -1;
+                const int dyp = sy == ny - 1 ? nx - n : nx, dym = sy == 0 ? n - nx : -nx;
+                sfor<1, 9, 1>([&](auto kc_) {
+                    constexpr int k = decltype(kc_)::value;
+                    constexpr int ex = LD2Q9::ex(k), ey = LD2Q9::ey(k);
+                    int t = s0;
+                    if constexpr (ex != 0) t += ex > 0 ? dxp : dxm;
+                    if constexpr (ey != 0) t += ey > 0 ? dyp : dym;
+                    FStore<SF, T>::store(fout + (k - 1) * n + t, f[k], LD2Q9::w(k), cf.fscale);
+                });
+            }
         } else if constexpr (GEO) {
             const int ia = (ty + 2) * Sh::AX + (tx + 2);
             sfor<1, 9, 1>([&](auto kc_) {
@@ -812,15 +828,8 @@ const Ops *ops_fused2d_lo(int N, int prec) {
     }
 }
 
-template <typename T, typename SF>
-const Ops *ops_fused2d_hi(int N, int prec) {
-    switch (N) {
-        case 5: return Fused2DLaunch<5, T, SF>::ops(prec);
-        case 6: return Fused2DLaunch<6, T, SF>::ops(prec);
-        case 7: return Fused2DLaunch<7, T, SF>::ops(prec);
-        case 8: return Fused2DLaunch<8, T, SF>::ops(prec);
-        default: return nullptr;
-    }
-}
+// One component count per call (the N = 5..8 translation units instantiate two counts each).
+template <int NN, typename T, typename SF>
+const Ops *ops_fused2d_one(int prec) { return Fused2DLaunch<NN, T, SF>::ops(prec); }
 
 }  // namespace nfe

@@ -232,6 +232,7 @@ __device__ __forceinline__ void site_physics3d(const Coef<T> &cf, const T (&c)[N
     flux_poly<N, T, Q4>(c, cf, q);
 #pragma unroll
     for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e] + cf.d34 * lap[e];
+    flux_rest<N, T, Q4>(c, cf, S);     // the no-phi ablation's remainder (Q4_NOPHI only)
     // moments from the pair sums: pairs (1,2) (3,4) (5,6) are the axes, then xy (+,+) (+,-),
     // xz (+,+) (+,-), yz (+,+) (+,-), each pair's first direction listed
     pair_sums<T>(f, sp, dm);
@@ -486,6 +487,78 @@ __device__ __forceinline__ void gather3d(const T *bm, const T *b0, const T *bp, 
         }
     });
     gather_final<N, T>(r0, acc, lapS, m, out);
+}
+
+// Stored component populations (tau_g != 1, Sec. III B), one site x with global index s0 (in-plane
+// wrapped coordinates sx, sy, plane z): g_{i,k}(x, t+1) = g*_{i,k}(x - e_k), g* = g + (g^eq - g) / tau_g,
+// with g^eq_{i,k}(x - e_k) (Eq. 40 as read: C_i s_k(v) - w_k m S_i, and C_i (1 + s_0(v)) + (1 - w_0) m S_i
+// for k = 0) from the source's record in shared memory and g from gin; a source beyond a wall gives
+// g*_{i,kbar}(x) (Eqs. 44-45).  Writes all 19 populations of every evolved component to gout and
+// returns C_i(x, t+1) = sum_k g_{i,k}(x, t+1) (Eq. 41).  Layout of g: plane (i 19 + k).
+template <int N, typename T, int BX, bool CHECK, bool TAILREC>
+__device__ __forceinline__ void gather3d_taug(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned wall0,
+                                              T m, T omg, const T *__restrict__ gin, T *__restrict__ gout, int n,
+                                              int nx, int ny, int nz, int sx, int sy, int z, int s0, T (&out)[N - 1]) {
+    using RB = BRec<T, 2 * N + 2, TAILREC>;
+    constexpr int E = N - 1;
+    const int nxy = nx * ny;
+    // offsets to the sources x - e_k, periodic wrap folded in
+    const int sxm = sx == 0 ? nx - 1 : -1, sxp = sx == nx - 1 ? 1 - nx : 1;
+    const int sym = sy == 0 ? nxy - nx : -nx, syp = sy == ny - 1 ? nx - nxy : nx;
+    const int szm = z == 0 ? n - nxy : -nxy, szp = z == nz - 1 ? nxy - n : nxy;
+    T r0[RB::NVP];
+    RB::load(b0, bplane, ib, r0);
+#pragma unroll
+    for (int e = 0; e < E; ++e) out[e] = T(0);
+    sfor<0, 19, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
+        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+        const T wk = T(LD3Q19::w(k));
+        if constexpr (k == 0) {
+            const T s0k = wk * (-T(1.5) * r0[2 * N + 1]);
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const T geq = r0[e] * (T(1) + s0k) + (T(1) - wk) * m * r0[N + 2 + e];
+                const T gg = gin[size_t(e * 19) * n + s0];
+                const T post = gg + omg * (geq - gg);
+                gout[size_t(e * 19) * n + s0] = post;
+                out[e] += post;
+            }
+        } else {
+            constexpr int kb = opp(k);
+            if (CHECK && ((wall0 >> kb) & 1u)) {
+                // the source is beyond a wall: g_k(x, t+1) = g*_kbar(x)
+                const T eu = T(LD3Q19::ex(kb)) * r0[N - 1] + T(LD3Q19::ey(kb)) * r0[N] + T(LD3Q19::ez(kb)) * r0[N + 1];
+                const T skb = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * r0[2 * N + 1]);
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const T geq = r0[e] * skb - wk * m * r0[N + 2 + e];
+                    const T gg = gin[size_t(e * 19 + kb) * n + s0];
+                    const T post = gg + omg * (geq - gg);
+                    gout[size_t(e * 19 + k) * n + s0] = post;
+                    out[e] += post;
+                }
+            } else {
+                const T *pl = ez < 0 ? bp : (ez > 0 ? bm : b0);      // the source is x - e_k
+                T r[RB::NVP];
+                RB::load(pl, bplane, ib - ex - BX * ey, r);
+                const T eu = T(ex) * r[N - 1] + T(ey) * r[N] + T(ez) * r[N + 1];
+                const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * r[2 * N + 1]);
+                int src = s0;
+                if constexpr (ex != 0) src += ex > 0 ? sxm : sxp;
+                if constexpr (ey != 0) src += ey > 0 ? sym : syp;
+                if constexpr (ez != 0) src += ez > 0 ? szm : szp;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const T geq = r[e] * sk - wk * m * r[N + 2 + e];
+                    const T gg = gin[size_t(e * 19 + k) * n + src];
+                    const T post = gg + omg * (geq - gg);
+                    gout[size_t(e * 19 + k) * n + s0] = post;
+                    out[e] += post;
+                }
+            }
+        }
+    });
 }
 
 // The same update for two sites stacked in y (a at ib, b at ib + BX), sharing the loads of the
@@ -1077,9 +1150,11 @@ struct Gather3DShape {
 
 // SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
 // translation units apart: each sets the shared-memory attribute of the kernel it launches.
-template <int N, typename T, typename SF, int TX, int TYT>
+// TAUG: stored component populations (tau_g != 1), each of the thread's two sites on its own.
+template <int N, typename T, typename SF, int TX, int TYT, bool TAUG>
 __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 ? 512 / (TX * TYT) : 256 / (TX * TYT)))
-k_split3d_gather(Geom g, T m, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk) {
+k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk,
+                 const T *__restrict__ gin, T *__restrict__ gout) {
     using Sh = Gather3DShape<N, T, TX, TYT>;
     using RB = typename Sh::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1136,10 +1211,19 @@ k_split3d_gather(Geom g, T m, const T *__restrict__ vs, T *__restrict__ Cout, in
             const T *bm = sB + slot4(z - 1) * BSLOT, *b0 = sB + slot4(z) * BSLOT, *bp = sB + slot4(z + 1) * BSLOT;
             const int ib = (2 * tr + 1) * Sh::RX + (tx + 1);
             T outa[N - 1], outb[N - 1];
-            // the wall-free form carries no bounce-back code; the form is decided per thread
-            if (wa | wb) gather3d_pair<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wa, wb, m, outa, outb);
-            else         gather3d_pair<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, 0u, m, outa, outb);
             const int sa = sxa + nx * sya + t.nxy * z, sb = sxa + nx * syb + t.nxy * z;
+            if constexpr (TAUG) {
+                if (wa) gather3d_taug<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wa, m, omg, gin, gout, n, nx, ny, nz, sxa, sya, z, sa, outa);
+                else    gather3d_taug<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, m, omg, gin, gout, n, nx, ny, nz, sxa, sya, z, sa, outa);
+                if (own_b) {
+                    if (wb) gather3d_taug<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib + Sh::RX, wb, m, omg, gin, gout, n, nx, ny, nz, sxa, syb, z, sb, outb);
+                    else    gather3d_taug<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib + Sh::RX, 0u, m, omg, gin, gout, n, nx, ny, nz, sxa, syb, z, sb, outb);
+                }
+            } else {
+                // the wall-free form carries no bounce-back code; the form is decided per thread
+                if (wa | wb) gather3d_pair<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wa, wb, m, outa, outb);
+                else         gather3d_pair<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, 0u, m, outa, outb);
+            }
             bool bad = false;
 #pragma unroll
             for (int e = 0; e < N - 1; ++e) {
@@ -1187,20 +1271,21 @@ cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers 
     return cudaGetLastError();
 }
 
-template <int N, typename T, typename SF, int TX, int TYT>
+template <int N, typename T, typename SF, int TX, int TYT, bool TAUG>
 cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Gather3DShape<N, T, TX, TYT>;
     static int slots = 0;
     if (!slots) {
-        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT>,
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT, TAUG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
-        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT>, TX * TYT, Sh::BYTES);
+        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT, TAUG>, TX * TYT, Sh::BYTES);
     }
     int zchunk = 0;
     const dim3 grid = split3d_grid(g, TX, Sh::TY, slots, zchunk);
-    k_split3d_gather<N, T, SF, TX, TYT><<<grid, TX * TYT, Sh::BYTES, st>>>(
-        g, cf.m, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk);
+    k_split3d_gather<N, T, SF, TX, TYT, TAUG><<<grid, TX * TYT, Sh::BYTES, st>>>(
+        g, cf.m, cf.gomega, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk,
+        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]));
     return cudaGetLastError();
 }
 
@@ -1209,6 +1294,9 @@ cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffer
 // two kernels per step (kern[0]: physics and streaming, kern[1]: the Cahn-Hilliard gather).
 template <int N, typename T, typename SF>
 struct Fused3DLaunch {
+    // the fused form is built for N <= 4 only (the split form is faster at every measured size and
+    // its instantiations for N = 5..8 would double the build); there variants 0 and 1 alias 3 and 2
+    static constexpr bool kFused = N <= 4;
     static constexpr bool kWideFits = Fused3DShape<N, T, 32, 8>::BYTES <= 220 * 1024;
     template <int TYT> static constexpr bool gather_fits = Gather3DShape<N, T, 32, TYT>::BYTES <= 220 * 1024;
     static constexpr int kGatherLarge = gather_fits<8> ? 8 : (gather_fits<4> ? 4 : 2);
@@ -1216,52 +1304,58 @@ struct Fused3DLaunch {
     static_assert(gather_fits<2>, "the smallest gather tile fits");
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        // the no-phi ablation (flux potential of Eq. 12 without phi_j) and the stored component
+        // populations (tau_g != 1) run in the split form only: every variant launches its physics
+        // kernel
+        if (cf.no_phi || b.g[0]) {
+            if (!cf.no_phi) {
+                if (variant == 3 || variant == 0) return launch_split3d_phys<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
+                return launch_split3d_phys<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
+            }
+            if (variant == 3 || variant == 0) return launch_split3d_phys<N, T, SF, 32, 4, Q4_NOPHI>(g, cf, b, cur, st);
+            return launch_split3d_phys<N, T, SF, 32, 8, Q4_NOPHI>(g, cf, b, cur, st);
+        }
+        if constexpr (!kFused) {
+            if (variant < 2) variant = variant == 0 ? 3 : 2;
+        }
         if (variant == 2) return launch_split3d_phys<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
         if (variant == 3) return launch_split3d_phys<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
-        if constexpr (kWideFits) {
-            if (variant == 1) return launch_fused3d<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
+        if constexpr (kFused) {
+            if constexpr (kWideFits) {
+                if (variant == 1) return launch_fused3d<N, T, SF, 32, 8, Q4_PARAM>(g, cf, b, cur, st);
+            }
+            return launch_fused3d<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
         }
-        return launch_fused3d<N, T, SF, 32, 4, Q4_PARAM>(g, cf, b, cur, st);
+        return cudaErrorInvalidValue;
     }
     static cudaError_t gather(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        if (cf.no_phi || b.g[0] || !kFused) variant = (variant == 3 || variant == 0) ? 3 : 2;
+        // stored component populations (tau_g != 1): one tile shape
+        if (b.g[0]) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, true>(g, cf, b, cur, st);
         // two sites per thread: 32 x 16 sites on 256 threads (variant 2), 32 x 8 on 128 (variant 3),
         // or the next smaller tile whose four record planes fit a CTA's shared memory
-        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, kGatherSmall>(g, cf, b, cur, st);
-        return launch_split3d_gather<N, T, SF, 32, kGatherLarge>(g, cf, b, cur, st);
+        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, false>(g, cf, b, cur, st);
+        return launch_split3d_gather<N, T, SF, 32, kGatherLarge, false>(g, cf, b, cur, st);
     }
     static const Ops *ops(int prec) {
         using B = Launch<LD3Q19, N, T, SF>;
         static const Ops o = {19, 3, N, prec, 1, {K_FUSED, K_FUSED}, {&step, &gather}, 4,
-                              {"fused3d 32x4", "fused3d 32x8", "split3d 32x8", "split3d 32x4"},
+                              {kFused ? "fused3d 32x4" : "split3d 32x4", kFused ? "fused3d 32x8" : "split3d 32x8",
+                               "split3d 32x8", "split3d 32x4"},
                               &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
                               int(sizeof(SF)), int(sizeof(T)), nullptr, nullptr, nullptr,
-                              {1, 1, 2, 2}, {{K_FUSED, K_FUSED}, {K_FUSED, K_FUSED}, {K_PHYS, K_GATHER}, {K_PHYS, K_GATHER}},
+                              {kFused ? 1 : 2, kFused ? 1 : 2, 2, 2},
+                              {{kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER},
+                               {kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER}, {K_PHYS, K_GATHER}, {K_PHYS, K_GATHER}},
                               TRec<T, 2 * N + 2>::NVP};
         return &o;
     }
 };
 
-// N = 2..4 and N = 5..8 are instantiated in separate translation units.
-template <typename T, typename SF>
-const Ops *ops_fused3d_lo(int N, int prec) {
-    switch (N) {
-        case 2: return Fused3DLaunch<2, T, SF>::ops(prec);
-        case 3: return Fused3DLaunch<3, T, SF>::ops(prec);
-        case 4: return Fused3DLaunch<4, T, SF>::ops(prec);
-        default: return nullptr;
-    }
-}
-
-template <typename T, typename SF>
-const Ops *ops_fused3d_hi(int N, int prec) {
-    switch (N) {
-        case 5: return Fused3DLaunch<5, T, SF>::ops(prec);
-        case 6: return Fused3DLaunch<6, T, SF>::ops(prec);
-        case 7: return Fused3DLaunch<7, T, SF>::ops(prec);
-        case 8: return Fused3DLaunch<8, T, SF>::ops(prec);
-        default: return nullptr;
-    }
-}
+// One component count per call; the translation units instantiate a few counts each, so that the
+// build compiles them in parallel.
+template <int NN, typename T, typename SF>
+const Ops *ops_fused3d_one(int prec) { return Fused3DLaunch<NN, T, SF>::ops(prec); }
 
 }  // namespace nfe

@@ -225,8 +225,18 @@ cudaEvent_t get_event(nfe_sim *s) {
 }
 
 // one time step from buffer `cur`, optionally with events around each kernel
-nfe_status launch_step(nfe_sim *s, int cur, bool timed, int variant) {
+// The variant a step really runs: the D3Q19 no-phi ablation and stored component populations
+// (tau_g != 1) exist in the split form only, so its fused variants (0: 32x4, 1: 32x8) run the split
+// form with the same physics tile.
+int effective_variant(const nfe_sim *s, int variant) {
     const int v = variant < 0 ? 0 : variant;
+    if ((s->no_phi || s->buf.g[0]) && s->ops->Q == 19 && v < 2) return v == 0 ? 3 : 2;
+    return v;
+}
+
+nfe_status launch_step(nfe_sim *s, int cur, bool timed, int variant) {
+    const int v = effective_variant(s, variant);
+    variant = v;
     const bool own_list = s->ops->vnk[v] > 0;            // a variant with its own kernel list
     const int nk = own_list ? s->ops->vnk[v] : s->ops->nk;
     const int *kinds = own_list ? s->ops->vkinds[v] : s->ops->kinds;
@@ -388,12 +398,9 @@ nfe_status nfe_create(const nfe_grid *grid, int N, const nfe_params *p, nfe_sim 
     if (p->implicit_component < 0 || p->implicit_component >= N) return fail(NFE_EINVAL, "implicit_component out of range");
     if (p->precision < NFE_FP64 || p->precision > NFE_FP32_BF16STORE) return fail(NFE_EINVAL, "unknown precision");
     if (p->flags & ~(NFE_NONCONSERVATIVE_FORCE | NFE_NO_PHI)) return fail(NFE_EINVAL, "unknown flags");
-    if ((p->flags & NFE_NO_PHI) && grid->lattice != NFE_D2Q9)
-        return fail(NFE_EUNSUPPORTED, "NFE_NO_PHI (the no-phi ablation) runs on D2Q9 only");
     const double tau_g = p->tau_g == 0.0 ? 1.0 : p->tau_g;
     if (!(tau_g > 0.5) || !std::isfinite(tau_g)) return fail(NFE_EINVAL, "tau_g must be > 1/2 (0 selects 1)");
     const bool stored_g = tau_g != 1.0;
-    if (stored_g && grid->lattice != NFE_D2Q9) return fail(NFE_EUNSUPPORTED, "tau_g != 1 runs on D2Q9 only");
     if (stored_g && (p->flags & NFE_NO_PHI)) return fail(NFE_EUNSUPPORTED, "tau_g != 1 together with NFE_NO_PHI");
     if (p->precision == NFE_FP32_F16STORE && (p->scale_exp < -20 || p->scale_exp > 20))
         return fail(NFE_EINVAL, "scale_exp outside -20..20");
@@ -634,7 +641,7 @@ nfe_status nfe_get_info(const nfe_sim *s, nfe_info *out) {
     out->sites = s->geom.n;
     out->omega_stab = s->tab.omega;
     out->factor_residual = s->tab.residual;
-    const int v = s->variant < 0 ? 0 : s->variant;
+    const int v = effective_variant(s, s->variant);
     out->kernels_per_step = (s->ops->vnk[v] > 0 ? s->ops->vnk[v] : s->ops->nk) + (s->buf.outflow ? 2 : 0);   // + the convective outflow
     out->variant = s->variant;
     out->nvariants = s->ops->nvariants;

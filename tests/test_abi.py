@@ -62,31 +62,13 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(bad, status):
     assert e.value.status == status
 
 
-def test_no_phi_ablation_is_d2q9_only():
-    # The no-phi ablation runs in the D2Q9 step; D3Q19 refuses it before touching the GPU.
-    lib()
-    sig = np.full((3, 3), 0.005)
-    np.fill_diagonal(sig, 0)
-    p = W.base_params(19, 8, 8, 8, 3, sig, 1.0)
-    with pytest.raises(nfe.NfeError) as e:
-        nfe.Sim(p, flags=nfe.NFE_NO_PHI)
-    assert e.value.status == 7          # NFE_EUNSUPPORTED
-
-
 def test_tau_g_validation():
-    # tau_g must exceed 1/2 (0 selects 1); tau_g != 1 runs on D2Q9 only and not with NO_PHI.
+    # tau_g must exceed 1/2 (0 selects 1); tau_g != 1 does not combine with NO_PHI.
     lib()
     p = _params(tau_g=0.5)
     with pytest.raises(nfe.NfeError) as e:
         nfe.Sim(p)
     assert e.value.status == 1          # NFE_EINVAL
-    sig = np.full((3, 3), 0.005)
-    np.fill_diagonal(sig, 0)
-    q = W.base_params(19, 8, 8, 8, 3, sig, 1.0)
-    q["tau_g"] = 1.3
-    with pytest.raises(nfe.NfeError) as e:
-        nfe.Sim(q)
-    assert e.value.status == 7          # NFE_EUNSUPPORTED
     with pytest.raises(nfe.NfeError) as e:
         nfe.Sim(_params(tau_g=1.3), flags=nfe.NFE_NO_PHI)
     assert e.value.status == 7

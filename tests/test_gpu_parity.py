@@ -188,6 +188,37 @@ def test_no_phi_ablation_matches_oracle_and_nucleates(precision, tol_c, tol_v):
         assert rel(g["C"][3], Co[3]) < 1e-9
 
 
+@pytest.mark.parametrize("precision,tol_c,tol_v", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)])
+def test_no_phi_ablation_d3q19_matches_oracle_and_nucleates(precision, tol_c, tol_v):
+    # The no-phi ablation on D3Q19 (split form of the step): a 3-D lens-like layout with an absent
+    # fourth component, against the oracle's literal Eq. 12 without phi_j; the absent component
+    # appears where three present ones meet.
+    n = 24
+    z, y, x = np.meshgrid(np.arange(n), np.arange(n), np.arange(n), indexing="ij")
+    below = W.tanh_step(n / 2 - 0.5 - z)
+    drop = W.tanh_step(6.0 - np.sqrt((x - n / 2 + 0.5) ** 2 + (y - n / 2 + 0.5) ** 2 + (z - n / 2 + 0.5) ** 2))
+    C = np.zeros((4, n, n, n))
+    C[0] = below * (1 - drop)
+    C[1] = (1 - below) * (1 - drop)
+    C[2] = drop
+    sig = np.full((4, 4), 0.005)
+    np.fill_diagonal(sig, 0)
+    sig[0, 1] = sig[1, 0] = 0.01
+    sig[0, 2] = sig[2, 0] = sig[1, 2] = sig[2, 1] = 0.008
+    p = W.base_params(19, n, n, n, 4, sig, 1.0, walls=(False, False, True), m=0.05, implicit=0)
+    p["C0"] = C
+    steps = 40
+    prm = lbm.Params(p)
+    st = lbm.run(prm, lbm.init_state(prm, p["C0"]), steps, with_phi=False)
+    Co, vo, Po, _ = lbm.fields(prm, st)
+    g = gpu_run(p, steps, precision, flags=nfe.NFE_NO_PHI)
+    assert rel(g["C"], Co) < tol_c
+    assert rel(g["v"], vo) < tol_v
+    assert np.abs(Co[3]).max() > 1e-7 and np.abs(g["C"][3]).max() > 1e-7
+    if precision == "fp64":
+        assert rel(g["C"][3], Co[3]) < 1e-9
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 @pytest.mark.parametrize("case,tau_g", [("lens_walls_N3", 0.8), ("spinodal_N4", 1.3)])
 def test_stored_g_tau_g_parity_with_oracle(precision, case, tau_g):
@@ -196,6 +227,16 @@ def test_stored_g_tau_g_parity_with_oracle(precision, case, tau_g):
     p = CASES[case]()
     p["tau_g"] = tau_g
     compare(p, 100, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("tau_g,walls", [(0.8, (False, True, True)), (1.3, (True, False, False))])
+def test_stored_g_tau_g_d3q19_parity_with_oracle(precision, tau_g, walls):
+    # tau_g != 1 on D3Q19 (split form of the step, the stored g pulled, relaxed and bounced back
+    # in the gather kernel) against the oracle's literal g populations
+    p = _mixture3d(21, 13, 14, 4, 60, walls)
+    p["tau_g"] = tau_g
+    compare(p, 60, precision)
 
 
 def test_stored_g_conservation_checkpoint_and_absent_component():
@@ -341,7 +382,8 @@ def test_d3q19_variants_are_bitwise_identical(precision, case):
             s.set_fields(p["C0"])
             s.set_variant(v)
             s.step(13)
-            assert s.info()["kernels_per_step"] == (2 if v >= 2 else 1)
+            # the fused form exists for N <= 4; above, variants 0 and 1 alias the split ones
+            assert s.info()["kernels_per_step"] == (2 if v >= 2 or p["N"] > 4 else 1)
             states.append(s.get_state())
     for st in states[1:]:
         assert np.array_equal(st, states[0])
