@@ -423,7 +423,7 @@ def run_nfe(args):
         fb = {"fp64": 8, "fp32": 4, "f16": 2, "bf16": 2}[prec]
         cb = 8 if prec == "fp64" else 4
         Q = 19
-        rec = 2 * N + 2
+        rec = 2 * N + 1           # the gather record: C, v and S of the site
         if kind == "step_physics":
             return 2 * (Q - 1) * fb + (N - 1) * cb + rec * cb
         if kind == "step_gather":

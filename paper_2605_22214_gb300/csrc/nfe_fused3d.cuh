@@ -347,44 +347,74 @@ __device__ __forceinline__ void push_store3d(const Coef<T> &cf, SF *__restrict__
     }
 }
 
-// Shared-memory / scratch record of NV values: full 16-byte chunks in separate planes and, when
-// NV is not a whole number of chunks (FP32 with NV = 2 mod 4), an 8-byte plane for the last two.
+// Shared-memory / scratch record of NV values over `count` sites: full 16-byte chunks in separate
+// planes, then, for the values left over, an 8-byte plane (two FP32 values) and a plane of single
+// values (one FP32 or FP64 value).  Every plane keeps consecutive sites consecutive.
 template <typename T, int NV>
 struct TRec {
     static constexpr int PER = 16 / sizeof(T);
     static constexpr int NC = NV / PER;            // full chunks
-    static constexpr int TAIL = NV - NC * PER;     // 0, or 2 values (FP32)
-    static constexpr int NVP = NC * PER + TAIL;
-    static_assert(TAIL == 0 || (TAIL == 2 && sizeof(T) == 4), "records of an even number of values");
+    static constexpr int TAIL = NV - NC * PER;     // 0..3 (FP32), 0..1 (FP64)
+    static constexpr int TAIL2 = (sizeof(T) == 4 && TAIL >= 2) ? 2 : 0;   // values in the 8-byte plane
+    static constexpr int TAIL1 = TAIL - TAIL2;                            // values in the single plane
+    static constexpr int NVP = NV;
+    // offsets (in values) of the planes for `count` sites
+    __host__ __device__ static constexpr size_t chunk_at(int c, size_t count) { return size_t(c) * count * PER; }
+    __host__ __device__ static constexpr size_t tail2_at(size_t count) { return size_t(NC) * count * PER; }
+    __host__ __device__ static constexpr size_t tail1_at(size_t count) { return size_t(NC) * count * PER + TAIL2 * count; }
 };
 
-template <typename T, int NV>
-__device__ __forceinline__ void trec_load(const T *base, int count, int i, T (&out)[TRec<T, NV>::NVP]) {
+template <typename T, int NV, int NOUT>
+__device__ __forceinline__ void trec_load(const T *base, int count, int i, T (&out)[NOUT]) {
     using R = TRec<T, NV>;
     using V = typename Vec16<T>::type;
 #pragma unroll
     for (int c = 0; c < R::NC; ++c) {
-        const V v = reinterpret_cast<const V *>(base + size_t(c) * count * R::PER)[i];
+        const V v = reinterpret_cast<const V *>(base + R::chunk_at(c, count))[i];
         if constexpr (sizeof(T) == 4) {
             out[4 * c + 0] = v.x; out[4 * c + 1] = v.y; out[4 * c + 2] = v.z; out[4 * c + 3] = v.w;
         } else {
             out[2 * c + 0] = v.x; out[2 * c + 1] = v.y;
         }
     }
-    if constexpr (R::TAIL == 2) {
-        const float2 v = reinterpret_cast<const float2 *>(base + size_t(R::NC) * count * R::PER)[i];
-        out[R::NC * 4] = v.x; out[R::NC * 4 + 1] = v.y;
+    if constexpr (R::TAIL2 == 2) {
+        const float2 v = reinterpret_cast<const float2 *>(base + R::tail2_at(count))[i];
+        out[R::NC * R::PER] = v.x; out[R::NC * R::PER + 1] = v.y;
     }
+    if constexpr (R::TAIL1 == 1) out[R::NC * R::PER + R::TAIL2] = (base + R::tail1_at(count))[i];
 }
 
-// The B record (C, v, S, |v|^2) of one site in its layout: SRec planes (fused step, TAILREC false)
-// or TRec planes (split step, TAILREC true).
-template <typename T, int NV, bool TAILREC>
+template <typename T, int NV, int NIN>
+__device__ __forceinline__ void trec_store(T *base, size_t count, size_t i, const T (&in)[NIN]) {
+    using R = TRec<T, NV>;
+    using V = typename Vec16<T>::type;
+#pragma unroll
+    for (int c = 0; c < R::NC; ++c) {
+        V w;
+        if constexpr (sizeof(T) == 4) { w.x = in[4 * c]; w.y = in[4 * c + 1]; w.z = in[4 * c + 2]; w.w = in[4 * c + 3]; }
+        else { w.x = in[2 * c]; w.y = in[2 * c + 1]; }
+        reinterpret_cast<V *>(base + R::chunk_at(c, count))[i] = w;
+    }
+    if constexpr (R::TAIL2 == 2)
+        reinterpret_cast<float2 *>(base + R::tail2_at(count))[i] = make_float2(in[R::NC * R::PER], in[R::NC * R::PER + 1]);
+    if constexpr (R::TAIL1 == 1) (base + R::tail1_at(count))[i] = in[R::NC * R::PER + R::TAIL2];
+}
+
+// The B record (C, v, S, |v|^2) of one site, loaded into NV = 2N + 2 values: from SRec planes
+// holding all of them (fused step, SLIM false), or from TRec planes without |v|^2 (split step,
+// SLIM true: the gather record in HBM and shared memory is one value shorter and |v|^2 is formed
+// after the load, with the same operations as where the fused step forms it).
+template <typename T, int NV, bool SLIM>
 struct BRec {
-    static constexpr int NVP = TAILREC ? TRec<T, NV>::NVP : SRec<T, NV>::NVP;
+    static constexpr int NVP = SLIM ? NV : SRec<T, NV>::NVP;
     __device__ __forceinline__ static void load(const T *base, int count, int i, T (&out)[NVP]) {
-        if constexpr (TAILREC) trec_load<T, NV>(base, count, i, out);
-        else srec_load<T, NV>(base, count, i, out);
+        if constexpr (SLIM) {
+            trec_load<T, NV - 1>(base, count, i, out);
+            constexpr int N = (NV - 2) / 2;
+            out[NV - 1] = vsq3<T>(out[N - 1], out[N], out[N + 1]);
+        } else {
+            srec_load<T, NV>(base, count, i, out);
+        }
     }
 };
 
@@ -466,10 +496,10 @@ __device__ __forceinline__ void gather_final(const T (&r0)[NVP], const T (&acc)[
 // the increments gathered before C(x) is added and the S Laplacian as link differences, so
 // that every link's two contributions cancel exactly.  A source beyond a wall bounces back
 // (wall0 bit kbar set for the source x - e_k = x + e_kbar).
-template <int N, typename T, int BX, bool CHECK, bool TAILREC = false>
+template <int N, typename T, int BX, bool CHECK, bool SLIM = false>
 __device__ __forceinline__ void gather3d(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned wall0,
                                          T m, T (&out)[N - 1]) {
-    using RB = BRec<T, 2 * N + 2, TAILREC>;
+    using RB = BRec<T, 2 * N + 2, SLIM>;
     T r0[RB::NVP];
     RB::load(b0, bplane, ib, r0);
     T acc[N - 1], lapS[N - 1];
@@ -495,11 +525,11 @@ __device__ __forceinline__ void gather3d(const T *bm, const T *b0, const T *bp, 
 // for k = 0) from the source's record in shared memory and g from gin; a source beyond a wall gives
 // g*_{i,kbar}(x) (Eqs. 44-45).  Writes all 19 populations of every evolved component to gout and
 // returns C_i(x, t+1) = sum_k g_{i,k}(x, t+1) (Eq. 41).  Layout of g: plane (i 19 + k).
-template <int N, typename T, int BX, bool CHECK, bool TAILREC>
+template <int N, typename T, int BX, bool CHECK, bool SLIM>
 __device__ __forceinline__ void gather3d_taug(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned wall0,
                                               T m, T omg, const T *__restrict__ gin, T *__restrict__ gout, int n,
                                               int nx, int ny, int nz, int sx, int sy, int z, int s0, T (&out)[N - 1]) {
-    using RB = BRec<T, 2 * N + 2, TAILREC>;
+    using RB = BRec<T, 2 * N + 2, SLIM>;
     constexpr int E = N - 1;
     const int nxy = nx * ny;
     // offsets to the sources x - e_k, periodic wrap folded in
@@ -564,10 +594,10 @@ __device__ __forceinline__ void gather3d_taug(const T *bm, const T *b0, const T 
 // The same update for two sites stacked in y (a at ib, b at ib + BX), sharing the loads of the
 // records both need: 28 record loads for the two instead of 38.  Each site sums its terms in the
 // order of kGatherOrder, as the one-site form does, so both give the same bits.
-template <int N, typename T, int BX, bool CHECK, bool TAILREC>
+template <int N, typename T, int BX, bool CHECK, bool SLIM>
 __device__ __forceinline__ void gather3d_pair(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned walla,
                                               unsigned wallb, T m, T (&outa)[N - 1], T (&outb)[N - 1]) {
-    using RB = BRec<T, 2 * N + 2, TAILREC>;
+    using RB = BRec<T, 2 * N + 2, SLIM>;
     T ra[RB::NVP], rb[RB::NVP];
     RB::load(b0, bplane, ib, ra);
     RB::load(b0, bplane, ib + BX, rb);
@@ -969,7 +999,7 @@ struct Split3DShape {
     static constexpr int NT = TX * TY;
     static constexpr int ITER = (PLANE + NT - 1) / NT;
     using RA = SRec<T, N>;               // evolved C (N-1), E_B
-    using RB = TRec<T, 2 * N + 2>;       // the gather record written to the scratch array
+    using RB = TRec<T, 2 * N + 1>;       // the gather record written to the scratch array
     static constexpr size_t BYTES_A = sizeof(T) * size_t(SLOTS * RA::NVP * PLANE);
 };
 
@@ -1109,23 +1139,12 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
             site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, fo, S, F, v, P, sp, dm);
             const int s0 = t.sxy + t.nxy * z;
             {
-                // the gather record (C, v, S, |v|^2) of this site, TRec planes over the grid
-                using RB = typename Sh::RB;
-                T rec[RB::NVP];
+                // the gather record (C, v, S) of this site, TRec planes over the grid
+                T rec[2 * N + 1];
 #pragma unroll
                 for (int a = 0; a < N - 1; ++a) { rec[a] = c[a]; rec[N + 2 + a] = S[a]; }
                 rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
-                rec[2 * N + 1] = vsq3<T>(v[0], v[1], v[2]);
-                using V = typename Vec16<T>::type;
-#pragma unroll
-                for (int ch = 0; ch < RB::NC; ++ch) {
-                    V w;
-                    if constexpr (sizeof(T) == 4) { w.x = rec[4 * ch]; w.y = rec[4 * ch + 1]; w.z = rec[4 * ch + 2]; w.w = rec[4 * ch + 3]; }
-                    else { w.x = rec[2 * ch]; w.y = rec[2 * ch + 1]; }
-                    reinterpret_cast<V *>(vs + size_t(ch) * n * RB::PER)[s0] = w;
-                }
-                if constexpr (RB::TAIL == 2)
-                    reinterpret_cast<float2 *>(vs + size_t(RB::NC) * n * RB::PER)[s0] = make_float2(rec[4 * RB::NC], rec[4 * RB::NC + 1]);
+                trec_store<T, 2 * N + 1>(vs, size_t(n), size_t(s0), rec);
             }
             collide3d<N, T>(cf, c, v, F, P, sp, dm, fo);
             push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, fo);
@@ -1144,7 +1163,7 @@ struct Gather3DShape {
     static constexpr int SLOTS = 4;
     static constexpr int NT = TX * TYT;
     static constexpr int ITER = (PLANE + NT - 1) / NT;
-    using RB = TRec<T, 2 * N + 2>;
+    using RB = TRec<T, 2 * N + 1>;       // the gather record without |v|^2
     static constexpr size_t BYTES = sizeof(T) * size_t(SLOTS * RB::NVP * PLANE);
 };
 
@@ -1181,14 +1200,17 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
                     const int s = t.roff[it] + zo;
 #pragma unroll
                     for (int ch = 0; ch < RB::NC; ++ch) {
-                        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(base + size_t(ch) * Sh::PLANE * RB::PER + size_t(i) * RB::PER));
-                        const T *src = vs + size_t(ch) * n * RB::PER + size_t(s) * RB::PER;
+                        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(base + RB::chunk_at(ch, Sh::PLANE) + size_t(i) * RB::PER));
+                        const T *src = vs + RB::chunk_at(ch, size_t(n)) + size_t(s) * RB::PER;
                         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
                     }
-                    if constexpr (RB::TAIL == 2) {
-                        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(base + size_t(RB::NC) * Sh::PLANE * RB::PER + size_t(i) * 2));
-                        const T *src = vs + size_t(RB::NC) * n * RB::PER + size_t(s) * 2;
+                    if constexpr (RB::TAIL2 == 2) {
+                        const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(base + RB::tail2_at(Sh::PLANE) + size_t(i) * 2));
+                        const T *src = vs + RB::tail2_at(size_t(n)) + size_t(s) * 2;
                         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+                    }
+                    if constexpr (RB::TAIL1 == 1) {
+                        cp_async_value<T>(base + RB::tail1_at(Sh::PLANE) + i, vs + RB::tail1_at(size_t(n)) + s);
                     }
                 }
             }
@@ -1348,7 +1370,7 @@ struct Fused3DLaunch {
                               {kFused ? 1 : 2, kFused ? 1 : 2, 2, 2},
                               {{kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER},
                                {kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER}, {K_PHYS, K_GATHER}, {K_PHYS, K_GATHER}},
-                              TRec<T, 2 * N + 2>::NVP};
+                              TRec<T, 2 * N + 1>::NVP};
         return &o;
     }
 };
