@@ -1120,13 +1120,13 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
     finish_A(t.z_lo - 1);
     finish_A(t.z_lo);
     copy_A(t.z_lo + 1);
-#pragma unroll 1
-    for (int z = t.z_lo; z < t.z_hi; ++z) {
+    // one plane: its site updates with the populations in cur, the next plane's loaded into nxt
+    auto plane = [&](int z, T (&cur)[19], T (&nxt)[19]) {
         cp_async_wait_all();
         finish_A(z + 1);
         __syncthreads();                  // A(z-1..z+1) complete; every thread is past plane z-1
         copy_A(z + 2);
-        load_F(z + 1, fn);
+        load_F(z + 1, nxt);
         if (t.own_xy) {
             const bool check = t.wallt || (g.wz && (z == 0 || z == nz - 1));
             const unsigned wall0 = check ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
@@ -1136,7 +1136,7 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
             if (check) stencil3d<N, T, Sh::RX, true>(pm, p0, pp, Sh::PLANE, ia, wall0, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::RX, false>(pm, p0, pp, Sh::PLANE, ia, 0u, c, lap, gr, gE);
             T S[N - 1], F[3], v[3], P, sp[9], dm[9];
-            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, fo, S, F, v, P, sp, dm);
+            site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, cur, S, F, v, P, sp, dm);
             const int s0 = t.sxy + t.nxy * z;
             {
                 // the gather record (C, v, S) of this site, TRec planes over the grid
@@ -1146,9 +1146,15 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
                 rec[N - 1] = v[0]; rec[N] = v[1]; rec[N + 1] = v[2];
                 trec_store<T, 2 * N + 1>(vs, size_t(n), size_t(s0), rec);
             }
-            collide3d<N, T>(cf, c, v, F, P, sp, dm, fo);
-            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, fo);
+            collide3d<N, T>(cf, c, v, F, P, sp, dm, cur);
+            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, cur);
         }
+    };
+    // one plane per iteration (two per iteration with the population registers swapping roles
+    // doubles the loop body and measured slower)
+#pragma unroll 1
+    for (int z = t.z_lo; z < t.z_hi; ++z) {
+        plane(z, fo, fn);
 #pragma unroll
         for (int k = 0; k < 19; ++k) fo[k] = fn[k];
     }

@@ -143,6 +143,9 @@ void fill_coef(const nfe_sim &s, const nfe_params &p, Coef<T> &c) {
         c.omm[a] = p.lambda_trt < 0.0 ? T(1.0 / tau) : T(1.0 / (p.lambda_trt / (tau - 0.5) + 0.5));
         c.uidx[a] = s.uidx[a];
     }
+    c.uniform_tau = 1;
+    for (int a = 1; a < N; ++a)
+        if (c.omp[a] != c.omp[0] || c.omm[a] != c.omm[0]) c.uniform_tau = 0;
     c.m = T(p.m);
     c.d34 = T(0.75 * p.D);
     for (int d = 0; d < 3; ++d) c.fb[d] = T(p.body_force[d]);

@@ -56,6 +56,7 @@ struct Coef {
     int no_phi;                   // the no-phi ablation (flux potential without phi_j)
     T gomega;                     // 1 / tau_g (stored-g path, tau_g != 1)
     int has_fc;                   // body force on one component present
+    int uniform_tau;              // every component has the same omega+ and omega- (Eq. 42 has no choice)
     T fc[3];                      // that force per unit volume fraction, F += C_c F_c
     T fcsel[kMaxN];               // 1 for the internal slot of component c, 0 elsewhere
     T q4c[kQ4Inline];             // the same coefficients in the parameter block (N <= 6); last member

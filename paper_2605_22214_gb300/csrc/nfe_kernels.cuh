@@ -301,9 +301,10 @@ __device__ __forceinline__ void force_and_potential(const Coef<T> &cf, const Ste
 // lowest user index.
 template <int N, typename T>
 __device__ __forceinline__ void relaxation(const Coef<T> &cf, const T (&c)[N], T &op, T &om) {
+    op = cf.omp[0]; om = cf.omm[0];
+    if (cf.uniform_tau) return;           // one relaxation time for every component: nothing to choose
     T best = c[0];
     int bu = cf.uidx[0];
-    op = cf.omp[0]; om = cf.omm[0];
 #pragma unroll
     for (int a = 1; a < N; ++a) {
         if (c[a] > best || (c[a] == best && cf.uidx[a] < bu)) {
