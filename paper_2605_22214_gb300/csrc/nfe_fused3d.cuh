@@ -169,20 +169,22 @@ __device__ __forceinline__ void stencil3d(const T *pm, const T *p0, const T *pp,
 
 // Sums and differences of the direction pairs (k, k+1), k odd: sp[j] = f_k + f_k+1 and
 // dm[j] = f_k - f_k+1 for pair j = (k - 1) / 2.  The moments and the TRT collision use only these.
+// In FP32 the pairs are formed two at a time in the grouping the collision uses ((0, 1), (3, 4),
+// (5, 6), (7, 8), and 2 alone), so that its packed operands need no regrouping.
 template <typename T>
 __device__ __forceinline__ void pair_sums(const T (&f)[19], T (&sp)[9], T (&dm)[9]) {
     if constexpr (sizeof(T) == 4) {
-#pragma unroll
-        for (int j = 0; j < 9; j += 2) {
-            if (j + 1 < 9) {
-                const float2 a = make_float2(f[2 * j + 1], f[2 * j + 3]), b = make_float2(f[2 * j + 2], f[2 * j + 4]);
-                const float2 s = add2(a, b), d = sub2(a, b);
-                sp[j] = s.x; sp[j + 1] = s.y; dm[j] = d.x; dm[j + 1] = d.y;
-            } else {
-                sp[j] = f[2 * j + 1] + f[2 * j + 2];
-                dm[j] = f[2 * j + 1] - f[2 * j + 2];
-            }
-        }
+        auto two = [&](int j0, int j1) {
+            const float2 a = make_float2(f[2 * j0 + 1], f[2 * j1 + 1]), b = make_float2(f[2 * j0 + 2], f[2 * j1 + 2]);
+            const float2 s2 = add2(a, b), d2 = sub2(a, b);
+            sp[j0] = s2.x; sp[j1] = s2.y; dm[j0] = d2.x; dm[j1] = d2.y;
+        };
+        two(0, 1);
+        sp[2] = f[5] + f[6];
+        dm[2] = f[5] - f[6];
+        two(3, 4);
+        two(5, 6);
+        two(7, 8);
     } else {
 #pragma unroll
         for (int j = 0; j < 9; ++j) { sp[j] = f[2 * j + 1] + f[2 * j + 2]; dm[j] = f[2 * j + 1] - f[2 * j + 2]; }
@@ -264,15 +266,18 @@ __device__ __forceinline__ void collide3d(const Coef<T> &cf, const T (&c)[N], co
     const T X = op * (T(3) * P - T(1.5) * vv) - T(3) * ap * vF, Y = T(4.5) * op, Z = T(9) * ap, U = T(3) * om,
             V = T(3) * am;
     const T hop = T(0.5) * op, hom = T(0.5) * om;
-    // e.v and e.F of the first direction of every pair
-    const T eu[9] = {v[0], v[1], v[2], v[0] + v[1], v[0] - v[1], v[0] + v[2], v[0] - v[2], v[1] + v[2], v[1] - v[2]};
-    const T eF[9] = {F[0], F[1], F[2], F[0] + F[1], F[0] - F[1], F[0] + F[2], F[0] - F[2], F[1] + F[2], F[1] - F[2]};
     if constexpr (sizeof(T) == 4) {
         // two pairs of one weight class per instruction: (1,2)+(3,4), then (5,6) alone, then
-        // the six diagonal pairs two by two
+        // the six diagonal pairs two by two; e.v and e.F of the first direction of each pair
+        // formed two at a time (a + b and a - b as one packed FMA, exact)
         const float2 mhop = dup2(-hop), mhom = dup2(-hom);
-        auto two_pairs = [&](float wk, int j0, int j1) {
-            const float2 e_u = make_float2(eu[j0], eu[j1]), e_F = make_float2(eF[j0], eF[j1]);
+        const float2 pm = make_float2(1.0f, -1.0f);
+        const float2 eu2[5] = {make_float2(v[0], v[1]), make_float2(v[2], 0.0f), fma2(dup2(v[1]), pm, dup2(v[0])),
+                               fma2(dup2(v[2]), pm, dup2(v[0])), fma2(dup2(v[2]), pm, dup2(v[1]))};
+        const float2 eF2[5] = {make_float2(F[0], F[1]), make_float2(F[2], 0.0f), fma2(dup2(F[1]), pm, dup2(F[0])),
+                               fma2(dup2(F[2]), pm, dup2(F[0])), fma2(dup2(F[2]), pm, dup2(F[1]))};
+        auto two_pairs = [&](float wk, int j0, int j1, int q) {
+            const float2 e_u = eu2[q], e_F = eF2[q];
             const float2 s = make_float2(sp[j0], sp[j1]), d = make_float2(dm[j0], dm[j1]);
             const float2 sym = fma2(mhop, s, fma2(e_u, fma2(dup2(wk * Y), e_u, mul2(dup2(wk * Z), e_F)), dup2(wk * X)));
             const float2 anti = fma2(mhom, d, fma2(dup2(wk * U), e_u, mul2(dup2(wk * V), e_F)));
@@ -281,17 +286,21 @@ __device__ __forceinline__ void collide3d(const Coef<T> &cf, const T (&c)[N], co
             f[2 * j0 + 1] = pk.x; f[2 * j1 + 1] = pk.y; f[2 * j0 + 2] = pkb.x; f[2 * j1 + 2] = pkb.y;
         };
         const float wa = float(LD3Q19::w(1)), wd = float(LD3Q19::w(7));
-        two_pairs(wa, 0, 1);
+        two_pairs(wa, 0, 1, 0);
         {
-            const float sym = (wa * X + eu[2] * ((wa * Y) * eu[2] + (wa * Z) * eF[2])) - hop * sp[2];
-            const float anti = ((wa * U) * eu[2] + (wa * V) * eF[2]) - hom * dm[2];
+            const float eu = v[2], eF = F[2];
+            const float sym = (wa * X + eu * ((wa * Y) * eu + (wa * Z) * eF)) - hop * sp[2];
+            const float anti = ((wa * U) * eu + (wa * V) * eF) - hom * dm[2];
             f[5] = f[5] + (sym + anti);
             f[6] = f[6] + (sym - anti);
         }
-        two_pairs(wd, 3, 4);
-        two_pairs(wd, 5, 6);
-        two_pairs(wd, 7, 8);
+        two_pairs(wd, 3, 4, 2);
+        two_pairs(wd, 5, 6, 3);
+        two_pairs(wd, 7, 8, 4);
     } else {
+        // e.v and e.F of the first direction of every pair
+        const T eu[9] = {v[0], v[1], v[2], v[0] + v[1], v[0] - v[1], v[0] + v[2], v[0] - v[2], v[1] + v[2], v[1] - v[2]};
+        const T eF[9] = {F[0], F[1], F[2], F[0] + F[1], F[0] - F[1], F[0] + F[2], F[0] - F[2], F[1] + F[2], F[1] - F[2]};
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const T wk = j < 3 ? T(LD3Q19::w(1)) : T(LD3Q19::w(7));
