@@ -439,6 +439,27 @@ __host__ __device__ constexpr int d3q19_dir(int x, int y, int z) {
     return -1;
 }
 
+// FMA and product with the rounding fixed: a gather's terms are summed by different code in the
+// one-site and the stacked forms, and an expression left to the compiler may be contracted
+// differently in each; these keep every form on the same bits.
+template <typename T>
+__device__ __forceinline__ T fma_x(T a, T b, T c) {
+    if constexpr (sizeof(T) == 4) return __fmaf_rn(a, b, c);
+    else return __fma_rn(a, b, c);
+}
+template <typename T>
+__device__ __forceinline__ T mul_x(T a, T b) {
+    if constexpr (sizeof(T) == 4) return __fmul_rn(a, b);
+    else return __dmul_rn(a, b);
+}
+
+// s_k(v) = w_k (3 eu + 4.5 eu^2 - 1.5 |v|^2) = eu (3 w_k + 4.5 w_k eu) - 1.5 w_k |v|^2, eu = e_k . v
+// (the velocity part of g^eq_k, Eq. 40), with a fixed rounding sequence.
+template <typename T, int k>
+__device__ __forceinline__ T s_of(T eu, T vsq) {
+    return fma_x(eu, fma_x(T(4.5 * LD3Q19::w(k)), eu, T(3.0 * LD3Q19::w(k))), mul_x(T(-1.5 * LD3Q19::w(k)), vsq));
+}
+
 // One source term of the Cahn-Hilliard gather: record r of the source y = x - e_k adds
 // C_i(y) s_k(v(y)) to acc and w_k (S_i(y) - S_i(x)) to lapS (r0: the record of x).
 template <int N, typename T, int k, int NVP>
@@ -451,8 +472,7 @@ __device__ __forceinline__ void gather_term(const T (&r)[NVP], const T (&r0)[NVP
     if constexpr (ex != 0) eu = ex > 0 ? r[N - 1] : -r[N - 1];
     if constexpr (ey != 0) eu = ey > 0 ? eu + r[N] : eu - r[N];
     if constexpr (ez != 0) eu = ez > 0 ? eu + r[N + 1] : eu - r[N + 1];
-    // s_k = w_k (3 eu + 4.5 eu^2 - 1.5 |v|^2) = eu (3 w_k + 4.5 w_k eu) - 1.5 w_k |v|^2
-    const T sk = eu * (T(3.0 * LD3Q19::w(k)) + T(4.5 * LD3Q19::w(k)) * eu) - T(1.5 * LD3Q19::w(k)) * r[2 * N + 1];
+    const T sk = s_of<T, k>(eu, r[2 * N + 1]);
     if constexpr (sizeof(T) == 4) {
 #pragma unroll
         for (int e = 0; e + 1 < E; e += 2) {
@@ -463,12 +483,15 @@ __device__ __forceinline__ void gather_term(const T (&r)[NVP], const T (&r0)[NVP
             acc[e] = a.x; acc[e + 1] = a.y; lapS[e] = l.x; lapS[e + 1] = l.y;
         }
         if constexpr (E % 2 == 1) {
-            acc[E - 1] += r[E - 1] * sk;
-            lapS[E - 1] += wk * (r[N + 1 + E] - r0[N + 1 + E]);
+            acc[E - 1] = fma_x(r[E - 1], sk, acc[E - 1]);
+            lapS[E - 1] = fma_x(wk, r[N + 1 + E] - r0[N + 1 + E], lapS[E - 1]);
         }
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) { acc[e] += r[e] * sk; lapS[e] += wk * (r[N + 2 + e] - r0[N + 2 + e]); }
+        for (int e = 0; e < E; ++e) {
+            acc[e] = fma_x(r[e], sk, acc[e]);
+            lapS[e] = fma_x(wk, r[N + 2 + e] - r0[N + 2 + e], lapS[e]);
+        }
     }
 }
 
@@ -476,19 +499,23 @@ __device__ __forceinline__ void gather_term(const T (&r)[NVP], const T (&r0)[NVP
 // C_i(x) s_kbar(v(x)), and no S difference.
 template <int N, typename T, int k, int NVP>
 __device__ __forceinline__ void bounce_term(const T (&r0)[NVP], T (&acc)[N - 1]) {
-    const T wk = T(LD3Q19::w(k));
-    const T eu = -(T(LD3Q19::ex(k)) * r0[N - 1] + T(LD3Q19::ey(k)) * r0[N] + T(LD3Q19::ez(k)) * r0[N + 1]);
-    const T sk = wk * (T(3) * eu + T(4.5) * eu * eu - T(1.5) * r0[2 * N + 1]);
+    constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+    // e_kbar . v(x) = -e_k . v(x), the constant components folded
+    T eu = T(0);
+    if constexpr (ex != 0) eu = ex > 0 ? -r0[N - 1] : r0[N - 1];
+    if constexpr (ey != 0) eu = ey > 0 ? eu - r0[N] : eu + r0[N];
+    if constexpr (ez != 0) eu = ez > 0 ? eu - r0[N + 1] : eu + r0[N + 1];
+    const T sk = s_of<T, k>(eu, r0[2 * N + 1]);
 #pragma unroll
-    for (int e = 0; e < N - 1; ++e) acc[e] += r0[e] * sk;
+    for (int e = 0; e < N - 1; ++e) acc[e] = fma_x(r0[e], sk, acc[e]);
 }
 
 // Start of a gather: the rest population's increment C_i(x) s_0(v(x)).
 template <int N, typename T, int NVP>
 __device__ __forceinline__ void gather_init(const T (&r0)[NVP], T (&acc)[N - 1], T (&lapS)[N - 1]) {
-    const T w0 = T(1) / T(3);
+    const T s0 = mul_x(T(-0.5), r0[2 * N + 1]);      // -1.5 w_0 |v|^2, w_0 = 1/3
 #pragma unroll
-    for (int e = 0; e < N - 1; ++e) { acc[e] = r0[e] * (-T(1.5) * w0 * r0[2 * N + 1]); lapS[e] = T(0); }
+    for (int e = 0; e < N - 1; ++e) { acc[e] = mul_x(r0[e], s0); lapS[e] = T(0); }
 }
 
 // End of a gather: C(x) + increments, the S Laplacian as link differences (mass-exact).
@@ -496,7 +523,7 @@ template <int N, typename T, int NVP>
 __device__ __forceinline__ void gather_final(const T (&r0)[NVP], const T (&acc)[N - 1], const T (&lapS)[N - 1], T m,
                                              T (&out)[N - 1]) {
 #pragma unroll
-    for (int e = 0; e < N - 1; ++e) out[e] = r0[e] + (acc[e] - m * lapS[e]);
+    for (int e = 0; e < N - 1; ++e) out[e] = r0[e] + fma_x(-m, lapS[e], acc[e]);
 }
 
 // Cahn-Hilliard update (Eqs. 39-41, tau_g = 1) of one site from the (C, v, S, |v|^2) records of
@@ -600,59 +627,69 @@ __device__ __forceinline__ void gather3d_taug(const T *bm, const T *b0, const T 
     });
 }
 
-// The same update for two sites stacked in y (a at ib, b at ib + BX), sharing the loads of the
-// records both need: 28 record loads for the two instead of 38.  Each site sums its terms in the
-// order of kGatherOrder, as the one-site form does, so both give the same bits.
-template <int N, typename T, int BX, bool CHECK, bool SLIM>
-__device__ __forceinline__ void gather3d_pair(const T *bm, const T *b0, const T *bp, int bplane, int ib, unsigned walla,
-                                              unsigned wallb, T m, T (&outa)[N - 1], T (&outb)[N - 1]) {
+// Is the position (dx, dy, dz) relative to site 0 of a stack of K sites a source of one of them?
+__host__ __device__ constexpr bool stack_source(int K, int dx, int dy, int dz) {
+    for (int j = 0; j < K; ++j)
+        if (d3q19_dir(-dx, j - dy, -dz) > 0) return true;
+    return false;
+}
+
+// The same update for K sites stacked in y (site j at ib + j BX), sharing the loads of the records
+// several of them need: 9 K + 10 record loads for the K sites instead of 19 K (28 for two sites,
+// 37 for three, 46 for four).  The union of the sources is visited in (z, y, x) order, so each site
+// still sums its terms in the order of kGatherOrder, as the one-site form does: all give the same
+// bits.
+template <int N, typename T, int BX, bool CHECK, bool SLIM, int K>
+__device__ __forceinline__ void gather3d_stack(const T *bm, const T *b0, const T *bp, int bplane, int ib,
+                                               const unsigned (&wall)[K], T m, T (&out)[K][N - 1]) {
     using RB = BRec<T, 2 * N + 2, SLIM>;
-    T ra[RB::NVP], rb[RB::NVP];
-    RB::load(b0, bplane, ib, ra);
-    RB::load(b0, bplane, ib + BX, rb);
-    T acca[N - 1], lapa[N - 1], accb[N - 1], lapb[N - 1];
-    gather_init<N, T>(ra, acca, lapa);
-    gather_init<N, T>(rb, accb, lapb);
-    // positions (dx, dy, dz) relative to site a, dz then dy in -1..2 then dx ascending
-    sfor<0, 36, 1>([&](auto pc_) {
+    T rs[K][RB::NVP];
+#pragma unroll
+    for (int j = 0; j < K; ++j) RB::load(b0, bplane, ib + j * BX, rs[j]);
+    T acc[K][N - 1], lap[K][N - 1];
+#pragma unroll
+    for (int j = 0; j < K; ++j) gather_init<N, T>(rs[j], acc[j], lap[j]);
+    // positions (dx, dy, dz) relative to site 0, dz then dy in -1..K then dx ascending
+    constexpr int NYP = K + 2;
+    sfor<0, 9 * NYP, 1>([&](auto pc_) {
         constexpr int pidx = decltype(pc_)::value;
-        constexpr int dz = pidx / 12 - 1, dy = (pidx / 3) % 4 - 1, dx = pidx % 3 - 1;
-        // a source of site a / of site b: a D3Q19 neighbour offset (not the site itself)
-        constexpr int ka = d3q19_dir(-dx, -dy, -dz);
-        constexpr int kb2 = d3q19_dir(-dx, 1 - dy, -dz);
-        if constexpr (ka > 0 || kb2 > 0) {
-            // source beyond a wall: bounce-back instead of the neighbour's record
-            const bool bba = CHECK && ka > 0 && ((walla >> (ka > 0 ? opp(ka) : 0)) & 1u);
-            const bool bbb = CHECK && kb2 > 0 && ((wallb >> (kb2 > 0 ? opp(kb2) : 0)) & 1u);
-            // the records of the two sites themselves are already in registers
-            constexpr bool is_a = dx == 0 && dy == 0 && dz == 0, is_b = dx == 0 && dy == 1 && dz == 0;
+        constexpr int dz = pidx / (3 * NYP) - 1, dy = (pidx / 3) % NYP - 1, dx = pidx % 3 - 1;
+        // is this position a source of any of the K sites (a D3Q19 neighbour offset, not the site)?
+        constexpr bool any = stack_source(K, dx, dy, dz);
+        if constexpr (any) {
+            // the records of the K sites themselves are already in registers
+            constexpr int own = (dx == 0 && dz == 0 && dy >= 0 && dy < K) ? dy : -1;
             T r[RB::NVP];
-            if constexpr (is_a) {
+            if constexpr (own >= 0) {
 #pragma unroll
-                for (int q = 0; q < RB::NVP; ++q) r[q] = ra[q];
-            } else if constexpr (is_b) {
-#pragma unroll
-                for (int q = 0; q < RB::NVP; ++q) r[q] = rb[q];
+                for (int q = 0; q < RB::NVP; ++q) r[q] = rs[own][q];
             } else {
 #pragma unroll
                 for (int q = 0; q < RB::NVP; ++q) r[q] = T(0);
-                if ((ka > 0 && !bba) || (kb2 > 0 && !bbb)) {
+                // load unless every site that takes this source bounces back instead
+                bool need = false;
+                sfor<0, K, 1>([&](auto jc_) {
+                    constexpr int j = decltype(jc_)::value;
+                    constexpr int kj = d3q19_dir(-dx, j - dy, -dz);
+                    if constexpr (kj > 0) need |= !(CHECK && ((wall[j] >> opp(kj)) & 1u));
+                });
+                if (need) {
                     const T *pl = dz > 0 ? bp : (dz < 0 ? bm : b0);
                     RB::load(pl, bplane, ib + dx + BX * dy, r);
                 }
             }
-            if constexpr (ka > 0) {
-                if (bba) bounce_term<N, T, ka>(ra, acca);
-                else gather_term<N, T, ka>(r, ra, acca, lapa);
-            }
-            if constexpr (kb2 > 0) {
-                if (bbb) bounce_term<N, T, kb2>(rb, accb);
-                else gather_term<N, T, kb2>(r, rb, accb, lapb);
-            }
+            sfor<0, K, 1>([&](auto jc_) {
+                constexpr int j = decltype(jc_)::value;
+                constexpr int kj = d3q19_dir(-dx, j - dy, -dz);
+                if constexpr (kj > 0) {
+                    if (CHECK && ((wall[j] >> opp(kj)) & 1u)) bounce_term<N, T, kj>(rs[j], acc[j]);
+                    else gather_term<N, T, kj>(r, rs[j], acc[j], lap[j]);
+                }
+            });
         }
     });
-    gather_final<N, T>(ra, acca, lapa, m, outa);
-    gather_final<N, T>(rb, accb, lapb, m, outb);
+#pragma unroll
+    for (int j = 0; j < K; ++j) gather_final<N, T>(rs[j], acc[j], lap[j], m, out[j]);
 }
 
 // Bit k set when x + e_k lies beyond a wall.
@@ -994,10 +1031,14 @@ cudaError_t launch_fused3d(const Geom &g, const Coef<T> &cf, const Buffers &b, i
 //     collision and push-streaming of f, and v and S written to a scratch array in HBM;
 //   k_split3d_gather: per own site, C(t+1) from a shared-memory ring of those records on the
 //     tile + 1-site ring (16-byte cp.async copies of the scratch array).
-// The scratch array holds per site the gather's whole record (C, v, S, |v|^2) in TRec planes, so
-// the gather stages it with 16- and 8-byte copies and reads every neighbour with two 16-byte
-// and one 8-byte shared load (N = 4).  No site is computed twice (the fused step recomputes S
-// and v on the tile's ring), at the cost of the record crossing HBM (write + read).  Every value
+// The scratch array holds per site the gather's record (C, v, S) in TRec planes, |v|^2 being
+// formed again after each load, so the gather stages it with 16- and 4-byte copies and reads
+// every neighbour with two 16-byte and one 4-byte shared load (N = 4).  The record carries C
+// although C(t) is in HBM already: staging C from its own planes takes 4-byte copies into the
+// middle of 16-byte records, which meet 4-way shared-memory bank conflicts (measured: the
+// gather kernel ran 0.358 instead of 0.27 ms at 256^3).  No site is computed twice (the fused
+// step recomputes S and v on the tile's ring), at the cost of the record crossing HBM (write +
+// read).  Every value
 // is computed by the same device functions in the same order as in the fused step, so both forms
 // give the same bits.
 // ----------------------------------------------------------------------------
@@ -1170,10 +1211,10 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
     cp_async_wait_all();                  // no copy outlives the CTA
 }
 
-// Shape of the gather kernel: TX x (2 TYT) sites, TX x TYT threads, two sites stacked in y each.
-template <int N, typename T, int TX, int TYT>
+// Shape of the gather kernel: TX x (SPT TYT) sites, TX x TYT threads, SPT sites stacked in y each.
+template <int N, typename T, int TX, int TYT, int SPT>
 struct Gather3DShape {
-    static constexpr int TY = 2 * TYT;
+    static constexpr int TY = SPT * TYT;
     static constexpr int RX = TX + 2, RY = TY + 2, PLANE = RX * RY;   // tile + 1-ring
     static constexpr int SLOTS = 4;
     static constexpr int NT = TX * TYT;
@@ -1184,25 +1225,29 @@ struct Gather3DShape {
 
 // SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
 // translation units apart: each sets the shared-memory attribute of the kernel it launches.
-// TAUG: stored component populations (tau_g != 1), each of the thread's two sites on its own.
-template <int N, typename T, typename SF, int TX, int TYT, bool TAUG>
+// TAUG: stored component populations (tau_g != 1), each of the thread's sites on its own.
+template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG>
 __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 ? 512 / (TX * TYT) : 256 / (TX * TYT)))
 k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk,
                  const T *__restrict__ gin, T *__restrict__ gout) {
-    using Sh = Gather3DShape<N, T, TX, TYT>;
+    using Sh = Gather3DShape<N, T, TX, TYT, SPT>;
     using RB = typename Sh::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sB = reinterpret_cast<T *>(smem_raw);
     constexpr int BSLOT = RB::NVP * Sh::PLANE;
     const SplitTile<TX, Sh::TY, Sh::NT, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
     const int n = t.n, nz = t.nz, nx = t.nx, ny = t.ny;
-    // this thread's two sites: column tx, rows 2 r and 2 r + 1 of the tile
+    // this thread's sites: column tx, rows SPT r .. SPT r + SPT - 1 of the tile
     const int tx = t.tid % TX, tr = t.tid / TX;
-    const int gx = t.x0 + tx, gya = t.y0 + 2 * tr, gyb = gya + 1;
-    const bool own_a = gx < nx && gya < ny, own_b = gx < nx && gyb < ny;
-    const int sxa = t.edge ? pwrap(gx, nx, t.tiny) : gx;
-    const int sya = t.edge ? pwrap(gya, ny, t.tiny) : gya, syb = t.edge ? pwrap(gyb, ny, t.tiny) : gyb;
-
+    const int gx = t.x0 + tx, gy0 = t.y0 + SPT * tr;
+    const int sx = t.edge ? pwrap(gx, nx, t.tiny) : gx;
+    int sy[SPT];
+    bool own[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        own[j] = gx < nx && gy0 + j < ny;
+        sy[j] = t.edge ? pwrap(gy0 + j, ny, t.tiny) : gy0 + j;
+    }
     // start the copies of the records of plane zb (tile + 1-ring), one group
     auto copy_B = [&](int zb) {
         if (!(g.wz && (zb < 0 || zb >= nz))) {
@@ -1241,37 +1286,40 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
         cp_async_wait_all();
         __syncthreads();                  // B(z-1..z+1) complete; every thread is past plane z-1
         copy_B(z + 2);
-        if (own_a) {
+        if (own[0]) {
             const bool check = t.wallt || (g.wz && (z == 0 || z == nz - 1));
-            const unsigned wa = check ? wall_mask3(g, gx, gya, z) : 0u;
-            const unsigned wb = check && own_b ? wall_mask3(g, gx, gyb, z) : 0u;
+            unsigned wall[SPT];
+            unsigned wany = 0u;
+#pragma unroll
+            for (int j = 0; j < SPT; ++j) {
+                wall[j] = check && own[j] ? wall_mask3(g, gx, gy0 + j, z) : 0u;
+                wany |= wall[j];
+            }
             const T *bm = sB + slot4(z - 1) * BSLOT, *b0 = sB + slot4(z) * BSLOT, *bp = sB + slot4(z + 1) * BSLOT;
-            const int ib = (2 * tr + 1) * Sh::RX + (tx + 1);
-            T outa[N - 1], outb[N - 1];
-            const int sa = sxa + nx * sya + t.nxy * z, sb = sxa + nx * syb + t.nxy * z;
+            const int ib = (SPT * tr + 1) * Sh::RX + (tx + 1);
+            T out[SPT][N - 1];
             if constexpr (TAUG) {
-                if (wa) gather3d_taug<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wa, m, omg, gin, gout, n, nx, ny, nz, sxa, sya, z, sa, outa);
-                else    gather3d_taug<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, m, omg, gin, gout, n, nx, ny, nz, sxa, sya, z, sa, outa);
-                if (own_b) {
-                    if (wb) gather3d_taug<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib + Sh::RX, wb, m, omg, gin, gout, n, nx, ny, nz, sxa, syb, z, sb, outb);
-                    else    gather3d_taug<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib + Sh::RX, 0u, m, omg, gin, gout, n, nx, ny, nz, sxa, syb, z, sb, outb);
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    if (!own[j]) continue;
+                    const int sj = sx + nx * sy[j] + t.nxy * z;
+                    if (wall[j]) gather3d_taug<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib + j * Sh::RX, wall[j], m, omg, gin, gout, n, nx, ny, nz, sx, sy[j], z, sj, out[j]);
+                    else         gather3d_taug<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib + j * Sh::RX, 0u, m, omg, gin, gout, n, nx, ny, nz, sx, sy[j], z, sj, out[j]);
                 }
             } else {
                 // the wall-free form carries no bounce-back code; the form is decided per thread
-                if (wa | wb) gather3d_pair<N, T, Sh::RX, true, true>(bm, b0, bp, Sh::PLANE, ib, wa, wb, m, outa, outb);
-                else         gather3d_pair<N, T, Sh::RX, false, true>(bm, b0, bp, Sh::PLANE, ib, 0u, 0u, m, outa, outb);
+                if (wany) gather3d_stack<N, T, Sh::RX, true, true, SPT>(bm, b0, bp, Sh::PLANE, ib, wall, m, out);
+                else      gather3d_stack<N, T, Sh::RX, false, true, SPT>(bm, b0, bp, Sh::PLANE, ib, wall, m, out);
             }
             bool bad = false;
 #pragma unroll
-            for (int e = 0; e < N - 1; ++e) {
-                Cout[size_t(e) * n + sa] = outa[e];
-                bad |= !isfinite(outa[e]);
-            }
-            if (own_b) {
+            for (int j = 0; j < SPT; ++j) {
+                if (!own[j]) continue;
+                const int sj = sx + nx * sy[j] + t.nxy * z;
 #pragma unroll
                 for (int e = 0; e < N - 1; ++e) {
-                    Cout[size_t(e) * n + sb] = outb[e];
-                    bad |= !isfinite(outb[e]);
+                    Cout[size_t(e) * n + sj] = out[j][e];
+                    bad |= !isfinite(out[j][e]);
                 }
             }
             if (bad) atomicOr(flag, 1);
@@ -1308,19 +1356,19 @@ cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers 
     return cudaGetLastError();
 }
 
-template <int N, typename T, typename SF, int TX, int TYT, bool TAUG>
+template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG>
 cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
-    using Sh = Gather3DShape<N, T, TX, TYT>;
+    using Sh = Gather3DShape<N, T, TX, TYT, SPT>;
     static int slots = 0;
     if (!slots) {
-        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT, TAUG>,
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
-        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT, TAUG>, TX * TYT, Sh::BYTES);
+        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG>, TX * TYT, Sh::BYTES);
     }
     int zchunk = 0;
     const dim3 grid = split3d_grid(g, TX, Sh::TY, slots, zchunk);
-    k_split3d_gather<N, T, SF, TX, TYT, TAUG><<<grid, TX * TYT, Sh::BYTES, st>>>(
+    k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG><<<grid, TX * TYT, Sh::BYTES, st>>>(
         g, cf.m, cf.gomega, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk,
         static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]));
     return cudaGetLastError();
@@ -1335,10 +1383,12 @@ struct Fused3DLaunch {
     // its instantiations for N = 5..8 would double the build); there variants 0 and 1 alias 3 and 2
     static constexpr bool kFused = N <= 4;
     static constexpr bool kWideFits = Fused3DShape<N, T, 32, 8>::BYTES <= 220 * 1024;
-    template <int TYT> static constexpr bool gather_fits = Gather3DShape<N, T, 32, TYT>::BYTES <= 220 * 1024;
-    static constexpr int kGatherLarge = gather_fits<8> ? 8 : (gather_fits<4> ? 4 : 2);
-    static constexpr int kGatherSmall = gather_fits<4> ? 4 : 2;
-    static_assert(gather_fits<2>, "the smallest gather tile fits");
+    template <int TYT, int SPT> static constexpr bool gather_fits = Gather3DShape<N, T, 32, TYT, SPT>::BYTES <= 220 * 1024;
+    // sites per gather thread: three where the three sites' records and sums stay in registers
+    static constexpr int kSpt = (sizeof(T) == 4 && N <= 4) ? 3 : 2;
+    static constexpr int kGatherSmall = gather_fits<4, 2> ? 4 : 2;
+    static constexpr int kGatherStack = gather_fits<4, kSpt> ? 4 : (gather_fits<2, kSpt> ? 2 : 1);
+    static_assert(gather_fits<2, 2> && gather_fits<1, kSpt>, "the smallest gather tiles fit");
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         // the no-phi ablation (flux potential of Eq. 12 without phi_j) and the stored component
@@ -1369,11 +1419,12 @@ struct Fused3DLaunch {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         if (cf.no_phi || b.g[0] || !kFused) variant = (variant == 3 || variant == 0) ? 3 : 2;
         // stored component populations (tau_g != 1): one tile shape
-        if (b.g[0]) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, true>(g, cf, b, cur, st);
-        // two sites per thread: 32 x 16 sites on 256 threads (variant 2), 32 x 8 on 128 (variant 3),
-        // or the next smaller tile whose four record planes fit a CTA's shared memory
-        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, false>(g, cf, b, cur, st);
-        return launch_split3d_gather<N, T, SF, 32, kGatherLarge, false>(g, cf, b, cur, st);
+        if (b.g[0]) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, true>(g, cf, b, cur, st);
+        // variant 3: kSpt sites per thread on 32 x 4 threads (32 x 12 sites for FP32, N <= 4);
+        // variant 2: two sites per thread, 32 x 8 sites on 128 threads; each with the next smaller
+        // tile where its four record planes do not fit a CTA's shared memory
+        if (variant == 3) return launch_split3d_gather<N, T, SF, 32, kGatherStack, kSpt, false>(g, cf, b, cur, st);
+        return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, false>(g, cf, b, cur, st);
     }
     static const Ops *ops(int prec) {
         using B = Launch<LD3Q19, N, T, SF>;
