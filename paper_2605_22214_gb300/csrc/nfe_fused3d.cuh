@@ -1386,6 +1386,7 @@ struct Fused3DLaunch {
     template <int TYT, int SPT> static constexpr bool gather_fits = Gather3DShape<N, T, 32, TYT, SPT>::BYTES <= 220 * 1024;
     // sites per gather thread: three where the three sites' records and sums stay in registers
     static constexpr int kSpt = (sizeof(T) == 4 && N <= 4) ? 3 : 2;
+    static constexpr int kGatherLarge = gather_fits<8, 2> ? 8 : (gather_fits<4, 2> ? 4 : 2);
     static constexpr int kGatherSmall = gather_fits<4, 2> ? 4 : 2;
     static constexpr int kGatherStack = gather_fits<4, kSpt> ? 4 : (gather_fits<2, kSpt> ? 2 : 1);
     static_assert(gather_fits<2, 2> && gather_fits<1, kSpt>, "the smallest gather tiles fit");
@@ -1420,11 +1421,11 @@ struct Fused3DLaunch {
         if (cf.no_phi || b.g[0] || !kFused) variant = (variant == 3 || variant == 0) ? 3 : 2;
         // stored component populations (tau_g != 1): one tile shape
         if (b.g[0]) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, true>(g, cf, b, cur, st);
-        // variant 3: kSpt sites per thread on 32 x 4 threads (32 x 12 sites for FP32, N <= 4);
-        // variant 2: two sites per thread, 32 x 8 sites on 128 threads; each with the next smaller
-        // tile where its four record planes do not fit a CTA's shared memory
+        // variant 3: kSpt sites per thread on 32 x 4 threads (32 x 12 sites for FP32, N <= 4, else
+        // 32 x 8); variant 2: two sites per thread, 32 x 16 sites on 256 threads; each with the next
+        // smaller tile where its four record planes do not fit a CTA's shared memory
         if (variant == 3) return launch_split3d_gather<N, T, SF, 32, kGatherStack, kSpt, false>(g, cf, b, cur, st);
-        return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, false>(g, cf, b, cur, st);
+        return launch_split3d_gather<N, T, SF, 32, kGatherLarge, 2, false>(g, cf, b, cur, st);
     }
     static const Ops *ops(int prec) {
         using B = Launch<LD3Q19, N, T, SF>;
