@@ -320,8 +320,42 @@ def collide_f(lat, f, P, v, F, omega_p, omega_m, feq0_sign=-1.0):
 # public entry points
 # ----------------------------------------------------------------------------
 
-def init_state(prm, C0, v0=None, flux_form="literal"):
-    """f = f^eq(P = 0, v0) and g = g^eq(C0, v0, S(C0)) at t = 0."""
+def round_to_storage(x, fmt):
+    """x (float64) rounded to a 16-bit storage format and read back as float64.
+
+    fmt "fp16": IEEE binary16, round to nearest even (numpy's conversion);
+    fmt "bf16": the upper half of the binary32 word, x first rounded to binary32 and then its
+    16 low bits dropped with round to nearest even (the format keeps 8 significand bits).
+    Finite inputs only."""
+    x = np.asarray(x, dtype=np.float64)
+    if fmt == "fp16":
+        return x.astype(np.float16).astype(np.float64)
+    if fmt == "bf16":
+        u = x.astype(np.float32).view(np.uint32).astype(np.uint64)
+        odd = (u >> np.uint64(16)) & np.uint64(1)
+        u = (u + np.uint64(0x7FFF) + odd) & np.uint64(0xFFFF0000)
+        return u.astype(np.uint32).view(np.float32).astype(np.float64)
+    raise ValueError(fmt)
+
+
+def store_populations(lat, f, fmt, scale_exp=0):
+    """f as a library keeps it between steps when f is stored in 16 bits (a reading of the
+    paper, which stores f in full precision: f_k of this pressure-based scheme vanish at rest,
+    so f_k / w_k is stored, times 2^scale_exp for FP16): every f_k with k != 0 is replaced by
+    round(f_k / w_k 2^s) w_k 2^-s.  f_0 is untouched (it enters no moment and is not stored).
+    fmt None returns f unchanged."""
+    if fmt is None:
+        return f
+    out = f.copy()
+    sc = 2.0 ** scale_exp if fmt == "fp16" else 1.0
+    for k in range(1, lat.Q):
+        out[k] = round_to_storage(f[k] / lat.w[k] * sc, fmt) * lat.w[k] / sc
+    return out
+
+
+def init_state(prm, C0, v0=None, flux_form="literal", f_storage=None, scale_exp=0):
+    """f = f^eq(P = 0, v0) and g = g^eq(C0, v0, S(C0)) at t = 0 (f in the storage format
+    f_storage, see `store_populations`)."""
     lat = prm.lat
     C0 = np.asarray(C0, dtype=np.float64).reshape((prm.N,) + prm.shape)
     C = C0.copy()
@@ -337,11 +371,13 @@ def init_state(prm, C0, v0=None, flux_form="literal"):
     else:
         S = prm.tables.flux_potential(C, lapC)
     g = np.stack([g_equilibrium(lat, C[c], v, S[c], prm.m) for c in prm.evolved])
-    return State(f, g, 0)
+    return State(store_populations(lat, f, f_storage, scale_exp), g, 0)
 
 
-def step(prm, st, flux_form="literal", force_form="conservative", with_phi=True, feq0_sign=-1.0):
-    """Advance one time step (steps 1-7 above).  Returns the new State."""
+def step(prm, st, flux_form="literal", force_form="conservative", with_phi=True, feq0_sign=-1.0,
+         f_storage=None, scale_exp=0):
+    """Advance one time step (steps 1-7 above).  Returns the new State; with f_storage the
+    streamed f is kept in that 16-bit format (`store_populations`)."""
     lat = prm.lat
     C = components(prm, st.g)
     mac = macroscopic(prm, C, st.f, flux_form, force_form, with_phi)
@@ -350,7 +386,7 @@ def step(prm, st, flux_form="literal", force_form="conservative", with_phi=True,
     for a, c in enumerate(prm.evolved):
         geq = g_equilibrium(lat, C[c], mac["v"], mac["S"][c], prm.m)
         gpost[a] = st.g[a] - (st.g[a] - geq) / prm.tau_g
-    f_new = stream(prm, fpost)
+    f_new = store_populations(lat, stream(prm, fpost), f_storage, scale_exp)
     g_new = np.stack([stream(prm, gpost[a]) for a in range(len(prm.evolved))])
     return State(f_new, g_new, st.t + 1)
 

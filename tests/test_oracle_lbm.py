@@ -302,3 +302,66 @@ def test_tau_g_sets_the_mobility():
     assert abs(r32 - 3.0) < 0.12
     assert abs(r64 - 3.0) < 0.3 * abs(r32 - 3.0)
     assert abs((4.0 * r64 - r32) / 3.0 - 3.0) < 0.01
+
+
+def test_storage_rounding_follows_the_formats():
+    # 16-bit storage of f (a reading of the paper's f: stored as f_k / w_k): the rounding is pinned
+    # by values the IEEE binary16 and bfloat16 definitions fix (round to nearest, ties to even).
+    r16 = lambda x: float(lbm.round_to_storage(np.array([x]), "fp16")[0])
+    rbf = lambda x: float(lbm.round_to_storage(np.array([x]), "bf16")[0])
+    # binary16: 11 significand bits, unit in the last place 2^-10 at 1
+    assert r16(1.0 + 2.0 ** -11) == 1.0                      # tie -> even
+    assert r16(1.0 + 3 * 2.0 ** -11) == 1.0 + 2.0 ** -9       # tie -> even (upwards)
+    assert r16(1.0 + 2.0 ** -11 + 2.0 ** -20) == 1.0 + 2.0 ** -10
+    assert r16(2049.0) == 2048.0 and r16(2051.0) == 2052.0
+    assert r16(-1.0 - 3 * 2.0 ** -11) == -(1.0 + 2.0 ** -9)
+    assert r16(65504.0) == 65504.0
+    # bfloat16: 8 significand bits, unit in the last place 2^-7 at 1
+    assert rbf(1.0 + 2.0 ** -8) == 1.0
+    assert rbf(1.0 + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6
+    assert rbf(1.0 + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert rbf(-3.0) == -3.0 and rbf(257.0) == 256.0 and rbf(259.0) == 260.0
+    assert rbf(1e30) / 1e30 - 1.0 < 2.0 ** -8
+    # half-unit error bounds on random values of both signs
+    x = np.random.default_rng(5).uniform(-50.0, 50.0, 100000)
+    assert (np.abs(lbm.round_to_storage(x, "fp16") - x) <= 2.0 ** -11 * np.abs(x)).all()
+    assert (np.abs(lbm.round_to_storage(x, "bf16") - x) <= 2.0 ** -8 * np.abs(x)).all()
+
+
+@pytest.mark.parametrize("q", [9, 19])
+def test_store_populations_scales_by_weight_and_power_of_two(q):
+    lat = lbm.Lattice(q)
+    f = np.zeros((q, 1, 2, 3))
+    for k in range(q):
+        f[k, 0, 0, :] = lat.w[k] * 2.0 ** -10 * (1.0 + 2.0 ** -12)          # rounds down in FP16 at 2^10
+        f[k, 0, 1, :] = lat.w[k] * 2.0 ** -10 * (1.0 + 3 * 2.0 ** -11)      # tie -> 1 + 2^-9
+    out = lbm.store_populations(lat, f, "fp16", scale_exp=10)
+    np.testing.assert_array_equal(out[0], f[0])                              # f_0 is not stored
+    for k in range(1, q):
+        assert (out[k, 0, 0] == lat.w[k] * 2.0 ** -10).all()
+        assert (out[k, 0, 1] == lat.w[k] * 2.0 ** -10 * (1.0 + 2.0 ** -9)).all()
+    # without the scale the same values sit near 2^-10 in FP16 (spacing 2^-20): barely moved
+    out0 = lbm.store_populations(lat, f, "fp16", scale_exp=0)
+    assert np.abs(out0[1:] - f[1:]).max() <= 2.0 ** -21 * lat.w.max()
+    # BF16 ignores the scale: f_k / w_k = 2^-10 (1 + 2^-12) rounds to 2^-10
+    outb = lbm.store_populations(lat, f, "bf16", scale_exp=10)
+    for k in range(1, q):
+        assert (outb[k, 0, 0] == lat.w[k] * 2.0 ** -10).all()
+    assert lbm.store_populations(lat, f, None) is f
+
+
+def test_stored_f_keeps_mass_exact_and_stays_near_full_precision():
+    # With f kept in 16 bits the component populations g (full precision) still conserve mass
+    # exactly, and the run stays close to the full-precision one (momentum need not be conserved).
+    p = W.spinodal_2d(nx=24, ny=20)
+    prm = lbm.Params(p)
+    ref = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), 40, flux_form="factored")
+    C_ref = lbm.components(prm, ref.g)
+    for fmt, tol in (("fp16", 1e-4), ("bf16", 2e-3)):
+        st = lbm.init_state(prm, p["C0"], flux_form="factored", f_storage=fmt, scale_exp=10)
+        st = lbm.run(prm, st, 40, flux_form="factored", f_storage=fmt, scale_exp=10)
+        C = lbm.components(prm, st.g)
+        m0 = p["C0"].reshape(prm.N, -1).sum(axis=1)
+        np.testing.assert_allclose(C.reshape(prm.N, -1).sum(axis=1), m0, rtol=1e-13)
+        err = np.abs(C - C_ref).max()
+        assert 0 < err < tol, (fmt, err)
