@@ -125,9 +125,15 @@ k_batch_step(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ item
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) BatchSim<T> d;
     const int4 w = items[blockIdx.x];
-    load_desc(sims[w.x], d);
-    __syncthreads();
-    batch_tile_n<T, SF, TX, TY, NN, false>(d, parity, w.y, w.z, smem_raw);
+    const BatchSim<T> &dg = sims[w.x];
+    // the coefficients go to shared memory while the tile's own loads are already in flight:
+    // geometry and pointers are read straight from the descriptor (one broadcast load each),
+    // and the tile waits for the copy only before its first use of the coefficients
+    load_desc(dg, d);
+    const Geom geom = dg.geom;
+    fused2d_tile<NN, T, SF, TX, TY, false, Q4_GLOBAL, false, false, true>(
+        geom, d.coef, static_cast<const SF *>(dg.f[parity]), static_cast<SF *>(dg.f[1 - parity]),
+        static_cast<const T *>(dg.C[parity]), static_cast<T *>(dg.C[1 - parity]), dg.flag, w.y, w.z, smem_raw);
 }
 
 template <typename T, int TX, int TY>

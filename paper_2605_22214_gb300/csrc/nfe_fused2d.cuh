@@ -287,7 +287,10 @@ __device__ __forceinline__ T fload(const SF *p, double w, T finv) {
 // TAUG: the stored-g path (tau_g != 1), with the component populations in gin / gout.
 // GEO: node classes (solid nodes, inlets, outflow ghost column) from `geo`; see the boundary
 // rules at the phases below.
-template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4, bool TAUG = false, bool GEO = false>
+// CSYNC: cf is being copied into shared memory by the caller while the tile starts; the tile
+// issues its f and C loads first and reads cf only after a block barrier.
+template <int N, typename T, typename SF, int TX, int TY, bool L2ONLY, int Q4, bool TAUG = false, bool GEO = false,
+          bool CSYNC = false>
 __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, const SF *__restrict__ fin,
                                              SF *__restrict__ fout, const T *__restrict__ Cin,
                                              T *__restrict__ Cout, int *__restrict__ flag,
@@ -391,6 +394,7 @@ __device__ __forceinline__ void fused2d_tile(const Geom &g, const Coef<T> &cf, c
             }
         }
     }
+    if constexpr (CSYNC) __syncthreads();      // the caller's copy of cf is complete
 #pragma unroll
     for (int it = 0; it < ITER; ++it) {
         const int i = tid + it * NT;
