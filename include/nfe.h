@@ -17,8 +17,8 @@
  *     fractions (Sec. III B, Eqs. 39-43) with tau_g = 1,
  *   - halfway bounce-back and the wall-gradient rule on walls, periodic
  *     wrap on every other edge (Sec. III C, Eqs. 44-45);
- *   - on D2Q9, solid nodes anywhere in the grid, velocity and volume-fraction
- *     inlets and the convective outflow (Sec. III C; nfe_set_geometry).
+ *   - solid nodes anywhere in the grid (D2Q9 and D3Q19), and on D2Q9 velocity and
+ *     volume-fraction inlets and the convective outflow (Sec. III C; nfe_set_geometry).
  *
  * Conventions shared by every call:
  *   - Site index s = x + nx * (y + ny * z), x fastest.  Field arrays are
@@ -216,8 +216,9 @@ nfe_status nfe_diagnostics(nfe_sim *sim, nfe_diag *out);
  * NULL Sk or a component outside 0..N-1.  Synchronises. */
 nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, double *Sk);
 
-/* Open and complex boundaries of the D2Q9 step (Sec. III C, the conditions that the
- * emulsion and patterned-surface applications of Sec. V use).
+/* Open and complex boundaries (Sec. III C, the conditions that the emulsion and
+ * patterned-surface applications of Sec. V use): solid nodes on D2Q9 and D3Q19, inlets and
+ * the convective outflow on D2Q9.
  * node: host, n bytes, one class per site (x fastest): 0 fluid, 1 solid, 2 + j inlet j;
  *   NULL removes the geometry (ninlets, inlets and outflow are then ignored).
  * inlets: host, ninlets x (2 + N) doubles, row j = v_b (x, y) then C_b of all N
@@ -236,10 +237,11 @@ nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, do
  *   ghost column of volume fractions (convected the same way, started from column nx - 1)
  *   for the directional differences of column nx - 1.  Non-fluid nodes keep their
  *   populations and volume fractions; C := C_b on the inlet nodes now and at every
- *   nfe_set_fields.  nfe_fields reports v = P = 0 on solid nodes and v = v_b, P = 0 on
+ *   nfe_set_fields.  nfe_fields reports v = P = F_s = 0 on solid nodes and v = v_b, P = 0 on
  *   inlet nodes.  With outflow the raw state (nfe_get_state) also holds the ghost column,
  *   so set the geometry before restoring a state.
- * Errors: NFE_EUNSUPPORTED for D3Q19, tau_g != 1 or NFE_NO_PHI; NFE_EINVAL for a class
+ * Errors: NFE_EUNSUPPORTED for inlets or the outflow on D3Q19, tau_g != 1 or NFE_NO_PHI;
+ *   NFE_EINVAL for a class
  *   outside 0 .. 1 + ninlets, a bad inlet row or a violated outflow condition (these leave
  *   the previous geometry in place); NFE_ENOMEM or NFE_ECUDA while the new geometry is being
  *   uploaded, after which the simulation has no geometry (fully periodic / edge walls only)

@@ -29,7 +29,7 @@ __all__ = [
     "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
     "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
     "batch_sweep", "random_sigma", "random_simplex_points", "phase_separation_2d", "CONFIGS",
-    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "pals_2d", "FLUID", "SOLID", "INLET0",
+    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "porous_3d", "pals_2d", "FLUID", "SOLID", "INLET0",
 ]
 
 # node classes of a geometry (one byte per site)
@@ -331,6 +331,42 @@ def porous_channel_2d(nx=4096, ny=1024, N=4, seed=1031, pitch=16, post=4, u=0.01
     p = base_params(D2Q9, nx, ny, 1, N, sig, tau, m=m, name=f"porous_{nx}x{ny}_N{N}")
     p["C0"] = C
     p["geometry"] = dict(node=node, inlets=inlets, outflow=True)
+    return p
+
+
+def porous_3d(nx=40, ny=30, nz=20, N=4, seed=1041, walls=(False, False, True), tau=0.8, m=1.0 / 50.0,
+              pitch=10, post=3, body_force=(1e-6, 0.0, 0.0)):
+    """A D3Q19 porous block: solid cubes of post^3 sites every pitch sites (one per pitch^3 cell)
+    plus one solid slab across the grid at x in [nx/2, nx/2 + 2) with a square window of side
+    ny/3 in its middle; the given edge walls; a seeded smooth mixture of N components (two
+    tanh spheres in a matrix) driven by a small body force along x.  Fluid and solid nodes only."""
+    rng = np.random.default_rng(seed)
+    sig = random_sigma(rng, N)
+    x, y, z = _coords(nx, ny, nz)
+    node = np.zeros((nz, ny, nx), dtype=np.uint8)
+    o = pitch // 2
+    node[((x % pitch) >= o) & ((x % pitch) < o + post) & ((y % pitch) >= o) & ((y % pitch) < o + post)
+         & ((z % pitch) >= o) & ((z % pitch) < o + post)] = SOLID
+    w = max(ny // 3, 2)
+    slab = (x >= nx // 2) & (x < nx // 2 + 2)
+    window = (np.abs(y - (ny - 1) / 2.0) < w / 2.0) & (np.abs(z - (nz - 1) / 2.0) < w / 2.0)
+    node[slab & ~window] = SOLID
+    C = np.zeros((N, nz, ny, nx))
+    centres = rng.uniform(0.2, 0.8, size=(2, 3)) * np.array([nx, ny, nz])
+    radius = min(nx, ny, nz) / 5.0
+    rest = np.ones((nz, ny, nx))
+    for i, c in enumerate(centres):
+        d = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+        ci = rest * tanh_step(radius - d)
+        C[1 + i % (N - 1)] += ci
+        rest = rest - ci
+    C[0] = rest
+    C = np.clip(C, 0.0, None)
+    C /= C.sum(axis=0, keepdims=True)
+    p = base_params(D3Q19, nx, ny, nz, N, sig, tau, walls=walls, m=m, omega_stab=1.0 / 90.0,
+                    body_force=body_force, name=f"porous3d_{nx}x{ny}x{nz}_N{N}")
+    p["C0"] = C
+    p["geometry"] = dict(node=node, inlets=np.zeros((0, 2 + N)), outflow=False)
     return p
 
 

@@ -1,6 +1,6 @@
 """Open and complex boundaries of Sec. III C, the conditions that the emulsion and PaLS
-applications of Sec. V use, on the D2Q9 lattice: solid nodes inside the grid, Dirichlet
-inlets of velocity and volume fraction, and the convective outflow.
+applications of Sec. V use: solid nodes inside the grid (D2Q9 and D3Q19), Dirichlet inlets of
+velocity and volume fraction, and the convective outflow (D2Q9).
 
 Oracle code (test infrastructure only): imported by tests, the smoke check and the
 benchmark's CPU baseline, never by the product path.
@@ -52,8 +52,8 @@ class Geometry:
     """Node classes (shape of the grid), inlet table rows (vx, vy, C_1..C_N) and the outflow flag."""
 
     def __init__(self, prm, node, inlets=(), outflow=False):
-        if prm.lat.Q != 9:
-            raise ValueError("open and complex boundaries are built for D2Q9")
+        if prm.lat.Q != 9 and (len(inlets) or outflow):
+            raise ValueError("inlets and the outflow are built for D2Q9; D3Q19 takes solid nodes")
         self.node = np.asarray(node, dtype=np.int64).reshape(prm.shape)
         tab = np.asarray(inlets, dtype=np.float64).reshape(-1, 2 + prm.N)
         self.inlets = []

@@ -320,6 +320,28 @@ __device__ __forceinline__ T vsq3(T a, T b, T c) {
     else return __fma_rn(c, c, __fma_rn(b, b, __dmul_rn(a, a)));
 }
 
+// Bit k set when x + e_k is a solid node (geometry of fluid and solid nodes): own site s0 at
+// in-plane wrapped coordinates (sx, sy), plane zw, periodic wrap folded in.  Beyond a wall the
+// wrapped index still names a real site; the wall mask covers those links anyway.
+__device__ __forceinline__ unsigned solid_mask3(const unsigned char *__restrict__ node, int n, int nx, int ny, int nz,
+                                                int sx, int sy, int zw, int s0) {
+    const int nxy = nx * ny;
+    const int dxp = sx == nx - 1 ? 1 - nx : 1, dxm = sx == 0 ? nx - 1 : -1;
+    const int dyp = sy == ny - 1 ? nx - nxy : nx, dym = sy == 0 ? nxy - nx : -nx;
+    const int dzp = zw == nz - 1 ? nxy - n : nxy, dzm = zw == 0 ? n - nxy : -nxy;
+    unsigned m = 0u;
+    sfor<1, 19, 1>([&](auto kc_) {
+        constexpr int k = decltype(kc_)::value;
+        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+        int t = s0;
+        if constexpr (ex != 0) t += ex > 0 ? dxp : dxm;
+        if constexpr (ey != 0) t += ey > 0 ? dyp : dym;
+        if constexpr (ez != 0) t += ez > 0 ? dzp : dzm;
+        if (node[t] == kNodeSolid) m |= 1u << k;
+    });
+    return m;
+}
+
 // Push-streaming of the post-collision populations of one own site s0 (in-plane wrapped
 // coordinates sx, sy, plane zw) with halfway bounce-back (Eqs. 44-45) where wall0 has bit k set.
 // The periodic wrap is folded into six per-site neighbour offsets, so every site of a warp runs
@@ -1105,10 +1127,13 @@ struct SplitTile {
     __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
 };
 
-template <int N, typename T, typename SF, int TX, int TY, int Q4>
+// GEO: node classes (fluid and solid nodes): links into a solid node take the wall rules (the
+// stencil's mirror rule, bounce-back), and a solid node keeps its f and C (its record carries C
+// with v = S = 0 for the gather to copy).
+template <int N, typename T, typename SF, int TX, int TY, int Q4, bool GEO = false>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 / (TX * TY) : 256 / (TX * TY)))
 k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk) {
+               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk, const unsigned char *__restrict__ node) {
     using Sh = Split3DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1178,16 +1203,32 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
         copy_A(z + 2);
         load_F(z + 1, nxt);
         if (t.own_xy) {
-            const bool check = t.wallt || (g.wz && (z == 0 || z == nz - 1));
-            const unsigned wall0 = check ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
+            const bool wchk = t.wallt || (g.wz && (z == 0 || z == nz - 1));
+            unsigned wall0 = wchk ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
+            const int s0 = t.sxy + t.nxy * z;
+            bool solid_site = false;
+            if constexpr (GEO) {
+                solid_site = node[s0] == kNodeSolid;
+                wall0 |= solid_mask3(node, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0);
+            }
+            const bool check = GEO ? wall0 != 0u : wchk;
             const T *pm = sA + slot4(z - 1) * ASLOT, *p0 = sA + slot4(z) * ASLOT, *pp = sA + slot4(z + 1) * ASLOT;
             const int ia = (t.ty + 1) * Sh::RX + (t.tx + 1);
             T c[N], lap[N], gr[N][3], gE[3];
             if (check) stencil3d<N, T, Sh::RX, true>(pm, p0, pp, Sh::PLANE, ia, wall0, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::RX, false>(pm, p0, pp, Sh::PLANE, ia, 0u, c, lap, gr, gE);
+            if (GEO && solid_site) {
+                // a solid node keeps its state: f copied as stored, C passed to the gather
+                T rec[2 * N + 1];
+#pragma unroll
+                for (int a = 0; a < 2 * N + 1; ++a) rec[a] = a < N - 1 ? c[a] : T(0);
+                trec_store<T, 2 * N + 1>(vs, size_t(n), size_t(s0), rec);
+#pragma unroll
+                for (int k = 1; k < 19; ++k) fout[size_t(k - 1) * n + s0] = fin[size_t(k - 1) * n + s0];
+                return;
+            }
             T S[N - 1], F[3], v[3], P, sp[9], dm[9];
             site_physics3d<N, T, Q4>(cf, c, lap, gr, gE, cur, S, F, v, P, sp, dm);
-            const int s0 = t.sxy + t.nxy * z;
             {
                 // the gather record (C, v, S) of this site, TRec planes over the grid
                 T rec[2 * N + 1];
@@ -1226,10 +1267,12 @@ struct Gather3DShape {
 // SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
 // translation units apart: each sets the shared-memory attribute of the kernel it launches.
 // TAUG: stored component populations (tau_g != 1), each of the thread's sites on its own.
-template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG>
+// GEO: node classes (fluid and solid nodes): a source inside a solid node bounces back, and a
+// solid node keeps its C.
+template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG, bool GEO = false>
 __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 ? 512 / (TX * TYT) : 256 / (TX * TYT)))
 k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk,
-                 const T *__restrict__ gin, T *__restrict__ gout) {
+                 const T *__restrict__ gin, T *__restrict__ gout, const unsigned char *__restrict__ node) {
     using Sh = Gather3DShape<N, T, TX, TYT, SPT>;
     using RB = typename Sh::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1293,6 +1336,8 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
 #pragma unroll
             for (int j = 0; j < SPT; ++j) {
                 wall[j] = check && own[j] ? wall_mask3(g, gx, gy0 + j, z) : 0u;
+                if constexpr (GEO)
+                    if (own[j]) wall[j] |= solid_mask3(node, n, nx, ny, nz, sx, sy[j], z, sx + nx * sy[j] + t.nxy * z);
                 wany |= wall[j];
             }
             const T *bm = sB + slot4(z - 1) * BSLOT, *b0 = sB + slot4(z) * BSLOT, *bp = sB + slot4(z + 1) * BSLOT;
@@ -1310,6 +1355,17 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
                 // the wall-free form carries no bounce-back code; the form is decided per thread
                 if (wany) gather3d_stack<N, T, Sh::RX, true, true, SPT>(bm, b0, bp, Sh::PLANE, ib, wall, m, out);
                 else      gather3d_stack<N, T, Sh::RX, false, true, SPT>(bm, b0, bp, Sh::PLANE, ib, wall, m, out);
+            }
+            if constexpr (GEO) {
+                // a solid node keeps its C (the first values of its record)
+#pragma unroll
+                for (int j = 0; j < SPT; ++j) {
+                    if (!own[j] || node[sx + nx * sy[j] + t.nxy * z] != kNodeSolid) continue;
+                    T r[RB::NVP + 1];
+                    BRec<T, 2 * N + 2, true>::load(b0, Sh::PLANE, ib + j * Sh::RX, r);
+#pragma unroll
+                    for (int e = 0; e < N - 1; ++e) out[j][e] = r[e];
+                }
             }
             bool bad = false;
 #pragma unroll
@@ -1338,39 +1394,39 @@ inline dim3 split3d_grid(const Geom &g, int TX, int TY, int slots, int &zchunk) 
     return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, chunks);
 }
 
-template <int N, typename T, typename SF, int TX, int TY, int Q4>
+template <int N, typename T, typename SF, int TX, int TY, int Q4, bool GEO = false>
 cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Split3DShape<N, T, TX, TY>;
     static int slots = 0;
     if (!slots) {
-        cudaError_t e = cudaFuncSetAttribute(k_split3d_phys<N, T, SF, TX, TY, Q4>,
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_phys<N, T, SF, TX, TY, Q4, GEO>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES_A));
         if (e != cudaSuccess) return e;
-        slots = resident_ctas(k_split3d_phys<N, T, SF, TX, TY, Q4>, TX * TY, Sh::BYTES_A);
+        slots = resident_ctas(k_split3d_phys<N, T, SF, TX, TY, Q4, GEO>, TX * TY, Sh::BYTES_A);
     }
     int zchunk = 0;
     const dim3 grid = split3d_grid(g, TX, TY, slots, zchunk);
-    k_split3d_phys<N, T, SF, TX, TY, Q4><<<grid, TX * TY, Sh::BYTES_A, st>>>(
+    k_split3d_phys<N, T, SF, TX, TY, Q4, GEO><<<grid, TX * TY, Sh::BYTES_A, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]), static_cast<const T *>(b.C[cur]),
-        static_cast<T *>(b.vs), zchunk);
+        static_cast<T *>(b.vs), zchunk, GEO ? b.node : nullptr);
     return cudaGetLastError();
 }
 
-template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG>
+template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG, bool GEO = false>
 cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
     using Sh = Gather3DShape<N, T, TX, TYT, SPT>;
     static int slots = 0;
     if (!slots) {
-        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG>,
+        cudaError_t e = cudaFuncSetAttribute(k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG, GEO>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(Sh::BYTES));
         if (e != cudaSuccess) return e;
-        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG>, TX * TYT, Sh::BYTES);
+        slots = resident_ctas(k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG, GEO>, TX * TYT, Sh::BYTES);
     }
     int zchunk = 0;
     const dim3 grid = split3d_grid(g, TX, Sh::TY, slots, zchunk);
-    k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG><<<grid, TX * TYT, Sh::BYTES, st>>>(
+    k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG, GEO><<<grid, TX * TYT, Sh::BYTES, st>>>(
         g, cf.m, cf.gomega, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk,
-        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]));
+        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]), GEO ? b.node : nullptr);
     return cudaGetLastError();
 }
 
@@ -1392,6 +1448,8 @@ struct Fused3DLaunch {
     static_assert(gather_fits<2, 2> && gather_fits<1, kSpt>, "the smallest gather tiles fit");
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        // a geometry of fluid and solid nodes: the split form's geometry kernels, one tile shape
+        if (b.node) return launch_split3d_phys<N, T, SF, 32, 4, Q4_PARAM, true>(g, cf, b, cur, st);
         // the no-phi ablation (flux potential of Eq. 12 without phi_j) and the stored component
         // populations (tau_g != 1) run in the split form only: every variant launches its physics
         // kernel
@@ -1419,6 +1477,7 @@ struct Fused3DLaunch {
     static cudaError_t gather(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         if (cf.no_phi || b.g[0] || !kFused) variant = (variant == 3 || variant == 0) ? 3 : 2;
+        if (b.node) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, false, true>(g, cf, b, cur, st);
         // stored component populations (tau_g != 1): one tile shape
         if (b.g[0]) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, true>(g, cf, b, cur, st);
         // variant 3: kSpt sites per thread on 32 x 4 threads (32 x 12 sites for FP32, N <= 4, else
@@ -1433,7 +1492,7 @@ struct Fused3DLaunch {
                               {kFused ? "fused3d 32x4" : "split3d 32x4", kFused ? "fused3d 32x8" : "split3d 32x8",
                                "split3d 32x8", "split3d 32x4"},
                               &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
-                              int(sizeof(SF)), int(sizeof(T)), nullptr, nullptr, nullptr,
+                              int(sizeof(SF)), int(sizeof(T)), nullptr, &B::prepare_solid, &B::moments_solid,
                               {kFused ? 1 : 2, kFused ? 1 : 2, 2, 2},
                               {{kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER},
                                {kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER}, {K_PHYS, K_GATHER}, {K_PHYS, K_GATHER}},

@@ -233,6 +233,7 @@ cudaEvent_t get_event(nfe_sim *s) {
 // form with the same physics tile.
 int effective_variant(const nfe_sim *s, int variant) {
     const int v = variant < 0 ? 0 : variant;
+    if (s->buf.node && s->ops->Q == 19) return 3;      // the D3Q19 geometry kernels: one split form
     if ((s->no_phi || s->buf.g[0]) && s->ops->Q == 19 && v < 2) return v == 0 ? 3 : 2;
     return v;
 }
@@ -708,8 +709,9 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         geo_free(s);
         return NFE_OK;
     }
-    if (s->grid.lattice != NFE_D2Q9 || !s->ops->geo_prepare)
-        return fail(NFE_EUNSUPPORTED, "open and complex boundaries run on D2Q9 only");
+    if (!s->ops->geo_prepare) return fail(NFE_EUNSUPPORTED, "no geometry form for this lattice");
+    if (s->grid.lattice != NFE_D2Q9 && (ninlets != 0 || outflow))
+        return fail(NFE_EUNSUPPORTED, "inlets and the convective outflow run on D2Q9 only (D3Q19: fluid and solid nodes)");
     if (s->buf.g[0]) return fail(NFE_EUNSUPPORTED, "open and complex boundaries need tau_g = 1");
     if (s->no_phi) return fail(NFE_EUNSUPPORTED, "open and complex boundaries together with NFE_NO_PHI");
     if (ninlets < 0 || ninlets > kMaxInlets) return fail(NFE_EINVAL, "ninlets must be 0..%d", kMaxInlets);

@@ -119,9 +119,10 @@ struct Ops {
     cudaError_t (*init_g)(const Geom &, const void *coef, const Buffers &, int cur, const double *v, cudaStream_t);
     int f_elem_bytes;     // bytes per stored population
     int c_elem_bytes;     // bytes per stored volume fraction (and per scratch value)
-    // D2Q9 geometry (null for D3Q19): the inlet table from FP64 rows (vx, vy, C_b of all N
-    // components in internal order) on the device; C := C_b on the inlet nodes and ghost :=
-    // column nx - 1 in buffer cur; the fields of the state in buffer cur with the node classes
+    // geometry: the inlet table from FP64 rows (vx, vy, C_b of all N components in internal
+    // order) on the device (D2Q9; null for D3Q19, which takes fluid and solid nodes only);
+    // C := C_b on the inlet nodes and ghost := column nx - 1 in buffer cur; the fields of the
+    // state in buffer cur with the node classes
     cudaError_t (*inlet_table)(const void *coef, const double *rows, int ninl, void *out, cudaStream_t);
     cudaError_t (*geo_prepare)(const Geom &, const Buffers &, int cur, int ninl, cudaStream_t);
     cudaError_t (*moments_geo)(const Geom &, const void *coef, const Buffers &, int cur, cudaStream_t);

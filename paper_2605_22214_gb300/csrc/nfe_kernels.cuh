@@ -218,7 +218,8 @@ struct Stencil {
 
 template <class L, int N, typename T>
 __device__ __forceinline__ void stencil(const Geom &g, const Coef<T> &cf, const T *__restrict__ C,
-                                        int s, int x, int y, int z, Stencil<L, N, T> &st) {
+                                        int s, int x, int y, int z, Stencil<L, N, T> &st,
+                                        const unsigned char *__restrict__ node = nullptr) {
     const size_t n = size_t(g.n);
     T rest = T(0);
 #pragma unroll
@@ -234,6 +235,7 @@ __device__ __forceinline__ void stencil(const Geom &g, const Coef<T> &cf, const 
         const int j = neighbour<L>(g, x, y, z, k);
         st.nb[k] = j;
         if (j < 0) continue;               // wall: psi(x + e_k) := psi(x), difference 0
+        if (node && node[j] == kNodeSolid) continue;   // solid node: the same rule
         T cn[N];
         T r2 = T(0);
 #pragma unroll
@@ -317,11 +319,13 @@ __device__ __forceinline__ void relaxation(const Coef<T> &cf, const T (&c)[N], T
 // Kernels
 // ----------------------------------------------------------------------------
 
-// Fields of the current state in FP64: C (N planes, user order), v (3), P, F_s (3).
+// Fields of the current state in FP64: C (N planes, user order), v (3), P, F_s (3).  With node
+// classes (fluid and solid nodes only): the solid rule in the stencil, v = P = F_s = 0 on solid
+// nodes.
 template <class L, int N, typename T, typename SF>
 __global__ void __launch_bounds__(256)
 k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ C,
-          double *__restrict__ out, int *__restrict__ flag) {
+          double *__restrict__ out, int *__restrict__ flag, const unsigned char *__restrict__ node) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     const int x = s % g.nx;
@@ -330,7 +334,7 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     const int z = r / g.ny;
     const size_t n = size_t(g.n);
     Stencil<L, N, T> st;
-    stencil<L, N, T>(g, cf, C, s, x, y, z, st);
+    stencil<L, N, T>(g, cf, C, s, x, y, z, st, node);
     T Fs[3], S[N - 1];
     force_and_potential<L, N, T>(cf, st, Fs, S);
     T sumf = T(0), j0 = T(0), j1 = T(0), j2 = T(0);
@@ -347,11 +351,12 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     T cc = T(0);                          // body force on one component, F += C_c F_c
 #pragma unroll
     for (int a = 0; a < N; ++a) cc += cf.fcsel[a] * st.c[a];
-    const T v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0] + cc * cf.fc[0]);
-    const T v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1] + cc * cf.fc[1]);
-    const T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2] + cc * cf.fc[2]);
+    T v0 = j0 + T(0.5) * (Fs[0] + cf.fb[0] + cc * cf.fc[0]);
+    T v1 = j1 + T(0.5) * (Fs[1] + cf.fb[1] + cc * cf.fc[1]);
+    T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2] + cc * cf.fc[2]);
     const T w0 = T(L::w(0));
-    const T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) * T(1.0 / (3.0 * (1.0 - L::w(0))));
+    T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) * T(1.0 / (3.0 * (1.0 - L::w(0))));
+    if (node && node[s] == kNodeSolid) v0 = v1 = v2 = P = Fs[0] = Fs[1] = Fs[2] = T(0);
 #pragma unroll
     for (int a = 0; a < N; ++a) {
         out[size_t(cf.uidx[a]) * n + s] = double(st.c[a]);
@@ -451,9 +456,18 @@ struct Launch {
     static cudaError_t moments(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
-            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag);
+            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, nullptr);
         return cudaGetLastError();
     }
+    // with the node classes of a geometry of fluid and solid nodes (D3Q19)
+    static cudaError_t moments_solid(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
+            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, b.node);
+        return cudaGetLastError();
+    }
+    // nothing to prepare for fluid and solid nodes alone
+    static cudaError_t prepare_solid(const Geom &, const Buffers &, int, int, cudaStream_t) { return cudaSuccess; }
     static cudaError_t reduce(const Geom &g, const Buffers &b, int, int nblocks, cudaStream_t st) {
         k_reduce_partial<<<nblocks, 256, 0, st>>>(g.n, N, b.fields, b.partials);
         k_reduce_final<<<1, 256, 0, st>>>(nblocks, N, b.partials, b.flag, b.diag);

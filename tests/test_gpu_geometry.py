@@ -184,11 +184,50 @@ def test_geometry_validation():
         s.set_geometry(open_left, g["inlets"], False)             # fine without the outflow
     q = W.janus_3d(n=16, radius=4.0)
     with nfe.Sim(q, "fp32") as s:
+        s.set_geometry(np.zeros(16 ** 3, np.uint8))              # D3Q19: fluid and solid nodes
         with pytest.raises(nfe.NfeError) as e:
-            s.set_geometry(np.zeros(16 ** 3, np.uint8))
+            s.set_geometry(np.zeros(16 ** 3, np.uint8), outflow=True)
+        assert e.value.status == 7
+        one = np.zeros((1, 2 + q["N"]))
+        one[0, 2] = 1.0
+        node = np.zeros(16 ** 3, np.uint8)
+        node[0] = W.INLET0
+        with pytest.raises(nfe.NfeError) as e:
+            s.set_geometry(node, one)
         assert e.value.status == 7
     r = dict(p, tau_g=1.3)
     with nfe.Sim(r, "fp64") as s:
         with pytest.raises(nfe.NfeError) as e:
             s.set_geometry(g["node"], g["inlets"], True)
         assert e.value.status == 7
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_porous_3d_matches_oracle(precision):
+    # D3Q19 with solid cubes, a slab with a window, walls in z and a body force along x, on a
+    # grid ragged against the tiles in x and y
+    p = W.porous_3d()
+    steps = 30
+    _check(oracle_run(p, steps), gpu_run(p, steps, precision), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "bf16"])
+def test_d3q19_solid_layers_equal_edge_walls_bitwise(precision):
+    # the same box bounded by edge walls in y and z, and by solid layers around it (periodic
+    # there): solid links take exactly the wall rules, so the interior states agree bit for bit
+    nx, ny, nz, N = 40, 18, 12, 4
+    a = W.porous_3d(nx, ny, nz, N, walls=(False, True, True))
+    b = W.porous_3d(nx, ny + 2, nz + 2, N, walls=(False, False, False))
+    node = np.zeros((nz + 2, ny + 2, nx), np.uint8)
+    node[0] = node[-1] = W.SOLID
+    node[:, 0] = node[:, -1] = W.SOLID
+    node[1:-1, 1:-1] = a["geometry"]["node"]
+    C = np.zeros((N, nz + 2, ny + 2, nx))
+    C[0] = 1.0
+    C[:, 1:-1, 1:-1] = a["C0"]
+    b = dict(b, sigma=a["sigma"], C0=C)
+    b["geometry"] = dict(node=node, inlets=np.zeros((0, 2 + N)), outflow=False)
+    ga, gb = gpu_run(a, 25, precision), gpu_run(b, 25, precision)
+    np.testing.assert_array_equal(gb["f"][:, 1:-1, 1:-1], ga["f"])
+    np.testing.assert_array_equal(gb["C"][:, 1:-1, 1:-1], ga["C"])
+    assert np.abs(gb["v"][:, node == W.SOLID]).max() == 0.0

@@ -163,3 +163,61 @@ def test_inlet_injects_its_composition_at_the_inflow_rate():
         m1 = B.fields(prm, geo, st)[0][1][geo.fluid].sum()
         rates.append((m1 - m0) / 150 / (u * ny * cb))
     assert all(0.9 < r < 1.05 for r in rates), rates
+
+
+def _mixture3d(nx, ny, nz, seed):
+    x, y, z = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float), np.arange(nz, dtype=float),
+                          indexing="xy")
+    x, y, z = (np.transpose(a, (2, 0, 1)) for a in (x, y, z))      # (nz, ny, nx)
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(2, [nx - 2, ny - 2, nz - 2], size=(2, 3))
+    a = W.tanh_step(2.5 - np.sqrt((x - c[0, 0]) ** 2 + (y - c[0, 1]) ** 2 + (z - c[0, 2]) ** 2))
+    b = (1 - a) * W.tanh_step(2.0 - np.sqrt((x - c[1, 0]) ** 2 + (y - c[1, 1]) ** 2 + (z - c[1, 2]) ** 2))
+    return np.stack([1 - a - b, a, b])
+
+
+def test_solid_layers_are_the_edge_walls_d3q19():
+    # D3Q19: a box bounded by edge walls in y and z (Eqs. 44-45, the gradient rule at the edge)
+    # and the same box with solid layers around it in y and z, periodic there
+    nx, ny, nz = 6, 5, 4
+    C = _mixture3d(nx, ny, nz, 7)
+    pa = W.base_params(W.D3Q19, nx, ny, nz, 3, _sigma3(), 0.8, walls=(False, True, True), omega_stab=1 / 90)
+    pb = W.base_params(W.D3Q19, nx, ny + 2, nz + 2, 3, _sigma3(), 0.8, omega_stab=1 / 90)
+    prm_a, prm_b = lbm.Params(pa), lbm.Params(pb)
+    node = np.zeros((nz + 2, ny + 2, nx), int)
+    node[0] = node[-1] = B.SOLID
+    node[:, 0] = node[:, -1] = B.SOLID
+    geo = B.Geometry(prm_b, node)
+    Cb = np.zeros((3, nz + 2, ny + 2, nx))
+    Cb[:, 1:-1, 1:-1] = C
+    Cb[0, node == B.SOLID] = 1.0
+    sa = lbm.run(prm_a, lbm.init_state(prm_a, C), 12)
+    sb = B.run(prm_b, geo, B.init_state(prm_b, geo, Cb), 12)
+    np.testing.assert_allclose(sb.f[:, 1:-1, 1:-1], sa.f, rtol=0, atol=1e-15)
+    np.testing.assert_allclose(sb.g[:, :, 1:-1, 1:-1], sa.g, rtol=0, atol=1e-15)
+
+
+def test_interior_block_conserves_every_component_d3q19():
+    nx, ny, nz = 10, 8, 7
+    p = W.base_params(W.D3Q19, nx, ny, nz, 3, _sigma3(), 0.7, omega_stab=1 / 90, body_force=(2e-5, 0, 0))
+    prm = lbm.Params(p)
+    node = np.zeros((nz, ny, nx), int)
+    node[2:5, 3:6, 4:7] = B.SOLID
+    geo = B.Geometry(prm, node)
+    st = B.init_state(prm, geo, _mixture3d(nx, ny, nz, 9))
+    C0, _, _, _ = B.fields(prm, geo, st)
+    st = B.run(prm, geo, st, 20)
+    C1, v, _, _ = B.fields(prm, geo, st)
+    m0, m1 = C0[:, geo.fluid].sum(axis=1), C1[:, geo.fluid].sum(axis=1)
+    np.testing.assert_allclose(m1, m0, rtol=0, atol=1e-12 * nx * ny * nz)
+    assert np.abs(v[:, ~geo.fluid]).max() == 0.0
+    np.testing.assert_array_equal(C1[:, ~geo.fluid], C0[:, ~geo.fluid])   # solid nodes keep C
+    assert np.abs(v[:, geo.fluid]).max() > 1e-6
+
+
+def test_d3q19_rejects_inlets_and_outflow():
+    p = W.base_params(W.D3Q19, 6, 5, 4, 3, _sigma3(), 0.8)
+    prm = lbm.Params(p)
+    node = np.zeros((4, 5, 6), int)
+    with pytest.raises(ValueError):
+        B.Geometry(prm, node, outflow=True)
