@@ -528,6 +528,8 @@ def extras_measure(nfe, torch, stream, args, hbm, peak_kind):
         ("lens 64x64 D2Q9 N=3 (c1)", lambda: W.lens_2d(), "fp64", 400, True),
         ("porous channel 4096x1024 D2Q9 N=4 (4x4 posts every 16 sites, inlet, outflow)",
          lambda: W.porous_channel_2d(), "fp32", 60, False),
+        ("porous block 256^3 D3Q19 N=4 (3^3 solid cubes every 10 sites, slab with a window, walls in z)",
+         lambda: W.porous_3d(256, 256, 256, 4, walls=(False, False, True)), "fp32", 20, False),
     ]
     out = []
     for name, make, prec, K, fl in cases:

@@ -342,7 +342,8 @@ def porous_3d(nx=40, ny=30, nz=20, N=4, seed=1041, walls=(False, False, True), t
     tanh spheres in a matrix) driven by a small body force along x.  Fluid and solid nodes only."""
     rng = np.random.default_rng(seed)
     sig = random_sigma(rng, N)
-    x, y, z = _coords(nx, ny, nz)
+    # broadcast coordinates (nz, ny, nx)
+    z, y, x = (a.astype(np.float64) for a in np.ogrid[0:nz, 0:ny, 0:nx])
     node = np.zeros((nz, ny, nx), dtype=np.uint8)
     o = pitch // 2
     node[((x % pitch) >= o) & ((x % pitch) < o + post) & ((y % pitch) >= o) & ((y % pitch) < o + post)
@@ -359,9 +360,9 @@ def porous_3d(nx=40, ny=30, nz=20, N=4, seed=1041, walls=(False, False, True), t
         d = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
         ci = rest * tanh_step(radius - d)
         C[1 + i % (N - 1)] += ci
-        rest = rest - ci
+        rest -= ci
     C[0] = rest
-    C = np.clip(C, 0.0, None)
+    np.clip(C, 0.0, None, out=C)
     C /= C.sum(axis=0, keepdims=True)
     p = base_params(D3Q19, nx, ny, nz, N, sig, tau, walls=walls, m=m, omega_stab=1.0 / 90.0,
                     body_force=body_force, name=f"porous3d_{nx}x{ny}x{nz}_N{N}")

@@ -320,35 +320,14 @@ __device__ __forceinline__ T vsq3(T a, T b, T c) {
     else return __fma_rn(c, c, __fma_rn(b, b, __dmul_rn(a, a)));
 }
 
-// Bit k set when x + e_k is a solid node (geometry of fluid and solid nodes): own site s0 at
-// in-plane wrapped coordinates (sx, sy), plane zw, periodic wrap folded in.  Beyond a wall the
-// wrapped index still names a real site; the wall mask covers those links anyway.
-__device__ __forceinline__ unsigned solid_mask3(const unsigned char *__restrict__ node, int n, int nx, int ny, int nz,
-                                                int sx, int sy, int zw, int s0) {
-    const int nxy = nx * ny;
-    const int dxp = sx == nx - 1 ? 1 - nx : 1, dxm = sx == 0 ? nx - 1 : -1;
-    const int dyp = sy == ny - 1 ? nx - nxy : nx, dym = sy == 0 ? nxy - nx : -nx;
-    const int dzp = zw == nz - 1 ? nxy - n : nxy, dzm = zw == 0 ? n - nxy : -nxy;
-    unsigned m = 0u;
-    sfor<1, 19, 1>([&](auto kc_) {
-        constexpr int k = decltype(kc_)::value;
-        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
-        int t = s0;
-        if constexpr (ex != 0) t += ex > 0 ? dxp : dxm;
-        if constexpr (ey != 0) t += ey > 0 ? dyp : dym;
-        if constexpr (ez != 0) t += ez > 0 ? dzp : dzm;
-        if (node[t] == kNodeSolid) m |= 1u << k;
-    });
-    return m;
-}
-
 // Push-streaming of the post-collision populations of one own site s0 (in-plane wrapped
 // coordinates sx, sy, plane zw) with halfway bounce-back (Eqs. 44-45) where wall0 has bit k set.
 // The periodic wrap is folded into six per-site neighbour offsets, so every site of a warp runs
 // the same store sequence; only sites next to a wall take the bounce-back form.
 template <typename T, typename SF>
 __device__ __forceinline__ void push_store3d(const Coef<T> &cf, SF *__restrict__ fout, int n, int nx, int ny, int nz,
-                                             int sx, int sy, int zw, int s0, unsigned wall0, const T (&f)[19]) {
+                                             int sx, int sy, int zw, int s0, unsigned wall0, const T (&f)[19],
+                                             bool checked = false) {
     const int nxy = nx * ny;
     const int dxp = sx == nx - 1 ? 1 - nx : 1, dxm = sx == 0 ? nx - 1 : -1;
     const int dyp = sy == ny - 1 ? nx - nxy : nx, dym = sy == 0 ? nxy - nx : -nx;
@@ -362,7 +341,8 @@ __device__ __forceinline__ void push_store3d(const Coef<T> &cf, SF *__restrict__
         if constexpr (ez != 0) t += ez > 0 ? dzp : dzm;
         return t;
     };
-    if (wall0 == 0u) {
+    // checked: the bounce-back form whatever wall0 (a warp-wide choice; same stores where wall0 = 0)
+    if (wall0 == 0u && !checked) {
         sfor<1, 19, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             FStore<SF, T>::store(fout + (k - 1) * n + target(kc_), f[k], LD3Q19::w(k), cf.fscale);
@@ -1127,13 +1107,14 @@ struct SplitTile {
     __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
 };
 
-// GEO: node classes (fluid and solid nodes): links into a solid node take the wall rules (the
-// stencil's mirror rule, bounce-back), and a solid node keeps its f and C (its record carries C
-// with v = S = 0 for the gather to copy).
+// GEO: a geometry of fluid and solid nodes, given as per-site solid-link masks (lmask: bit k when
+// x + e_k is solid, bit 31 when x is): links into a solid node take the wall rules (the stencil's
+// mirror rule, bounce-back), with the checked forms chosen per warp, and a solid node keeps its f
+// and C (its record carries C with v = S = 0 for the gather to copy).
 template <int N, typename T, typename SF, int TX, int TY, int Q4, bool GEO = false>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 / (TX * TY) : 256 / (TX * TY)))
 k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk, const unsigned char *__restrict__ node) {
+               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk, const unsigned *__restrict__ lmask) {
     using Sh = Split3DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1208,10 +1189,11 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
             const int s0 = t.sxy + t.nxy * z;
             bool solid_site = false;
             if constexpr (GEO) {
-                solid_site = node[s0] == kNodeSolid;
-                wall0 |= solid_mask3(node, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0);
+                const unsigned lm = lmask[s0];
+                solid_site = (lm >> 31) != 0u;
+                wall0 |= lm & 0x7FFFFFFFu;
             }
-            const bool check = GEO ? wall0 != 0u : wchk;
+            const bool check = GEO ? __any_sync(__activemask(), wall0 != 0u) : wchk;
             const T *pm = sA + slot4(z - 1) * ASLOT, *p0 = sA + slot4(z) * ASLOT, *pp = sA + slot4(z + 1) * ASLOT;
             const int ia = (t.ty + 1) * Sh::RX + (t.tx + 1);
             T c[N], lap[N], gr[N][3], gE[3];
@@ -1238,7 +1220,7 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
                 trec_store<T, 2 * N + 1>(vs, size_t(n), size_t(s0), rec);
             }
             collide3d<N, T>(cf, c, v, F, P, sp, dm, cur);
-            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, cur);
+            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, cur, GEO && check);
         }
     };
     // one plane per iteration (two per iteration with the population registers swapping roles
@@ -1267,12 +1249,13 @@ struct Gather3DShape {
 // SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
 // translation units apart: each sets the shared-memory attribute of the kernel it launches.
 // TAUG: stored component populations (tau_g != 1), each of the thread's sites on its own.
-// GEO: node classes (fluid and solid nodes): a source inside a solid node bounces back, and a
-// solid node keeps its C.
+// GEO: a geometry of fluid and solid nodes (per-site solid-link masks as for the physics
+// kernel): a source inside a solid node bounces back, with the checked form chosen per warp,
+// and a solid node keeps its C.
 template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG, bool GEO = false>
 __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 ? 512 / (TX * TYT) : 256 / (TX * TYT)))
 k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk,
-                 const T *__restrict__ gin, T *__restrict__ gout, const unsigned char *__restrict__ node) {
+                 const T *__restrict__ gin, T *__restrict__ gout, const unsigned *__restrict__ lmask) {
     using Sh = Gather3DShape<N, T, TX, TYT, SPT>;
     using RB = typename Sh::RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1337,9 +1320,10 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
             for (int j = 0; j < SPT; ++j) {
                 wall[j] = check && own[j] ? wall_mask3(g, gx, gy0 + j, z) : 0u;
                 if constexpr (GEO)
-                    if (own[j]) wall[j] |= solid_mask3(node, n, nx, ny, nz, sx, sy[j], z, sx + nx * sy[j] + t.nxy * z);
+                    if (own[j]) wall[j] |= lmask[sx + nx * sy[j] + t.nxy * z] & 0x7FFFFFFFu;
                 wany |= wall[j];
             }
+            if constexpr (GEO) wany = __any_sync(__activemask(), wany != 0u) ? 1u : 0u;
             const T *bm = sB + slot4(z - 1) * BSLOT, *b0 = sB + slot4(z) * BSLOT, *bp = sB + slot4(z + 1) * BSLOT;
             const int ib = (SPT * tr + 1) * Sh::RX + (tx + 1);
             T out[SPT][N - 1];
@@ -1360,7 +1344,7 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
                 // a solid node keeps its C (the first values of its record)
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
-                    if (!own[j] || node[sx + nx * sy[j] + t.nxy * z] != kNodeSolid) continue;
+                    if (!own[j] || (lmask[sx + nx * sy[j] + t.nxy * z] >> 31) == 0u) continue;
                     T r[RB::NVP + 1];
                     BRec<T, 2 * N + 2, true>::load(b0, Sh::PLANE, ib + j * Sh::RX, r);
 #pragma unroll
@@ -1408,7 +1392,7 @@ cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers 
     const dim3 grid = split3d_grid(g, TX, TY, slots, zchunk);
     k_split3d_phys<N, T, SF, TX, TY, Q4, GEO><<<grid, TX * TY, Sh::BYTES_A, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]), static_cast<const T *>(b.C[cur]),
-        static_cast<T *>(b.vs), zchunk, GEO ? b.node : nullptr);
+        static_cast<T *>(b.vs), zchunk, GEO ? b.lmask : nullptr);
     return cudaGetLastError();
 }
 
@@ -1426,7 +1410,7 @@ cudaError_t launch_split3d_gather(const Geom &g, const Coef<T> &cf, const Buffer
     const dim3 grid = split3d_grid(g, TX, Sh::TY, slots, zchunk);
     k_split3d_gather<N, T, SF, TX, TYT, SPT, TAUG, GEO><<<grid, TX * TYT, Sh::BYTES, st>>>(
         g, cf.m, cf.gomega, static_cast<const T *>(b.vs), static_cast<T *>(b.C[1 - cur]), b.flag, zchunk,
-        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]), GEO ? b.node : nullptr);
+        static_cast<const T *>(b.g[cur]), static_cast<T *>(b.g[1 - cur]), GEO ? b.lmask : nullptr);
     return cudaGetLastError();
 }
 

@@ -180,7 +180,7 @@ nfe_status free_all(nfe_sim *s) {
     void *ptrs[] = {s->buf.f[0], s->buf.f[1], s->buf.C[0], s->buf.C[1],
                     s->buf.fields, s->buf.partials, s->buf.diag, s->buf.flag, s->q4dev, s->r3dev,
                     s->buf.g[0], s->buf.g[1], s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1],
-                    s->buf.opart, s->buf.vs};
+                    s->buf.opart, s->buf.lmask, s->buf.vs};
     for (void *p : ptrs) dev_free(s, p);
     std::memset(&s->buf, 0, sizeof s->buf);
     s->q4dev = nullptr;
@@ -324,9 +324,10 @@ size_t state_size(const nfe_sim *s) {
 }
 
 void geo_free(nfe_sim *s) {
-    void *ptrs[] = {s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1], s->buf.opart};
+    void *ptrs[] = {s->node_dev, s->inl_dev, s->buf.ghost[0], s->buf.ghost[1], s->buf.opart, s->buf.lmask};
     for (void *p : ptrs) dev_free(s, p);
     s->buf.opart = nullptr;
+    s->buf.lmask = nullptr;
     s->device_bytes -= s->geo_bytes;
     s->geo_bytes = 0;
     s->node_dev = nullptr;
@@ -756,6 +757,11 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         const size_t pb = size_t(2 * ((ny + 31) / 32)) * sizeof(double);   // 2 per CTA of the outflow (32 rows)
         if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.opart), pb)) != NFE_OK) { geo_free(s); return st; }
         s->geo_bytes += pb;
+    }
+    if (s->ops->Q == 19) {
+        // the solid links of every site, formed once from the node classes
+        if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.lmask), n * sizeof(unsigned))) != NFE_OK) { geo_free(s); return st; }
+        s->geo_bytes += n * sizeof(unsigned);
     }
     s->geo_bytes += n + size_t(std::max(ninlets, 1)) * 2 * N * ce + 2 * s->ghost_bytes;
     s->buf.node = s->node_dev;

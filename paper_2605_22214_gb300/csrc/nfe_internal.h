@@ -82,13 +82,16 @@ struct Buffers {
     double *diag;         // reduction result
     int *flag;            // non-finite flag
     int cur;              // index of the buffer holding the current state
-    // D2Q9 geometry (null when the grid has none)
+    // geometry (null when the grid has none)
     const unsigned char *node;   // node class per site
     const void *inl;             // inlet table, compute type: per inlet vx, vy, C_b (N-1), S_b (N-1)
     void *ghost[2];              // outflow ghost column, (N-1) x ny, compute type, or null
     int outflow;                 // convective outflow on the x = nx - 1 edge
     double *opart;               // outflow partial sums (2 per 32 rows), or null
-    void *vs;                    // split D3Q19 step: per-site gather records (C, v, S, |v|^2), compute type, or null
+    unsigned *lmask;             // D3Q19 geometry: per site, bit k set when x + e_k is a solid node
+                                 // (k = 1..18) and bit 31 when x is; or null
+    void *vs;                    // split D3Q19 step: per-site gather records (C, v, S of the evolved
+                                 // components, 2N - 1 + 2 values), compute type, or null
 };
 
 // Launchers exported by the lattice translation units.  Each returns

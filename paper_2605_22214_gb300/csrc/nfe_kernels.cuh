@@ -372,6 +372,26 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     if (bad) atomicOr(flag, 1);
 }
 
+// Solid links of every site of a geometry of fluid and solid nodes: bit k (k = 1..Q-1) when
+// x + e_k is a solid node (periodic wrap; a neighbour beyond an edge wall sets no bit, the wall
+// mask covers it), bit 31 when x itself is solid.
+template <class L>
+__global__ void k_link_mask(Geom g, const unsigned char *__restrict__ node, unsigned *__restrict__ out) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const int x = s % g.nx;
+    const int r = s / g.nx;
+    const int y = r % g.ny;
+    const int z = r / g.ny;
+    unsigned m = node[s] == kNodeSolid ? (1u << 31) : 0u;
+#pragma unroll
+    for (int k = 1; k < L::Q; ++k) {
+        const int j = neighbour<L>(g, x, y, z, k);
+        if (j >= 0 && node[j] == kNodeSolid) m |= 1u << k;
+    }
+    out[s] = m;
+}
+
 // f = f^eq(P = 0, v): f_k = s_k(v) for k >= 1 (Eqs. 27-28).
 template <class L, typename T, typename SF>
 __global__ void k_init_f(Geom g, Coef<T> cf, const double *__restrict__ v, SF *__restrict__ f) {
@@ -466,8 +486,12 @@ struct Launch {
             g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, b.node);
         return cudaGetLastError();
     }
-    // nothing to prepare for fluid and solid nodes alone
-    static cudaError_t prepare_solid(const Geom &, const Buffers &, int, int, cudaStream_t) { return cudaSuccess; }
+    // fluid and solid nodes alone: the per-site solid-link masks
+    static cudaError_t prepare_solid(const Geom &g, const Buffers &b, int, int, cudaStream_t st) {
+        if (!b.lmask) return cudaErrorInvalidValue;
+        k_link_mask<L><<<blocks_for(g.n, 256), 256, 0, st>>>(g, b.node, b.lmask);
+        return cudaGetLastError();
+    }
     static cudaError_t reduce(const Geom &g, const Buffers &b, int, int nblocks, cudaStream_t st) {
         k_reduce_partial<<<nblocks, 256, 0, st>>>(g.n, N, b.fields, b.partials);
         k_reduce_final<<<1, 256, 0, st>>>(nblocks, N, b.partials, b.flag, b.diag);
