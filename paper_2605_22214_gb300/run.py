@@ -5,6 +5,7 @@
 WORKLOAD is one of: spinodal (D2Q9, N = 4, size^2), janus3d (D3Q19, N = 4, size^3),
 lens (D2Q9, N = 3, size^2, walls in y), poiseuille3d (D3Q19, N = 7, 32 x 32 x 192),
 porous (D2Q9, N = 4, (4 size) x size channel through solid posts, inlet and outflow),
+porous3d (D3Q19, N = 4, size^3 block of solid cubes and a slab with a window, walls in z),
 emulsion (D2Q9, N = 4, the 600 x 140 emulsion generator),
 pals (D2Q9, N = 4, the 400 x 140 patterned liquid surface),
 batch (--sims D2Q9 lens/Janus simulations of mixed size and N in one batch, FP32;
@@ -35,6 +36,8 @@ def make(name, size):
         return W.layered_poiseuille()
     if name == "porous":
         return W.porous_channel_2d(nx=4 * size, ny=size)
+    if name == "porous3d":
+        return W.porous_3d(size, size, size, 4, walls=(False, False, True))
     if name == "emulsion":
         return W.emulsion_2d()
     if name == "pals":
