@@ -97,6 +97,8 @@ k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict_
     // Work is handed out dynamically by one counter that only grows: step t owns the
     // indices [t * nitems, (t + 1) * nitems).  A CTA that draws an index of the next
     // step keeps it and starts the next step with it.
+    // The following index is drawn when a tile starts and read when it ends, so the atomic's
+    // round trip overlaps the tile instead of stalling the CTA between tiles.
     __shared__ long long next;
     if (threadIdx.x == 0) next = (long long)atomicAdd(&sync->ticket, 1ull);
     __syncthreads();
@@ -105,10 +107,12 @@ k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict_
         const long long end = (long long)(t + 1) * nitems;
         long long idx = next;
         while (idx < end) {
+            unsigned long long drawn = 0ull;
+            if (threadIdx.x == 0) drawn = atomicAdd(&sync->ticket, 1ull);
             const int4 w = items[idx - (long long)t * nitems];
             batch_tile<T, SF, TX, TY>(sims[w.x], cur, w.y, w.z, smem_raw);
             __syncthreads();      // shared memory is reused by the next tile
-            if (threadIdx.x == 0) next = (long long)atomicAdd(&sync->ticket, 1ull);
+            if (threadIdx.x == 0) next = (long long)drawn;
             __syncthreads();
             idx = next;
         }
