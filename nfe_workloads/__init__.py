@@ -29,7 +29,7 @@ __all__ = [
     "D2Q9", "D3Q19", "tanh_step", "base_params", "lens_2d", "spinodal_2d",
     "layered_poiseuille", "janus_3d", "janus_2d", "droplet_2d", "planar_2d",
     "batch_sweep", "random_sigma", "random_simplex_points", "phase_separation_2d", "CONFIGS",
-    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "porous_3d", "pals_2d", "FLUID", "SOLID", "INLET0",
+    "open_channel_2d", "emulsion_2d", "porous_channel_2d", "porous_3d", "inlet_channel_3d", "pals_2d", "FLUID", "SOLID", "INLET0",
 ]
 
 # node classes of a geometry (one byte per site)
@@ -368,6 +368,38 @@ def porous_3d(nx=40, ny=30, nz=20, N=4, seed=1041, walls=(False, False, True), t
                     body_force=body_force, name=f"porous3d_{nx}x{ny}x{nz}_N{N}")
     p["C0"] = C
     p["geometry"] = dict(node=node, inlets=np.zeros((0, 2 + N)), outflow=False)
+    return p
+
+
+def inlet_channel_3d(nx=40, ny=18, nz=14, N=3, seed=1051, tau=0.8, m=1.0 / 50.0):
+    """A D3Q19 channel, periodic in x, with solid planes at y = 0, ny - 1 and z = 0, nz - 1, a
+    solid post in the middle, and the plane x = 0 split into two inlets (lower and upper half in
+    y) of different compositions and velocities (every velocity component nonzero), plus a third
+    inlet patch in the upper y plane; the interior starts as a seeded smooth mixture.  The fluid
+    leaving at x = nx - 1 meets the inlet plane through the wrap."""
+    rng = np.random.default_rng(seed)
+    sig = random_sigma(rng, N)
+    node = np.zeros((nz, ny, nx), dtype=np.uint8)
+    node[0] = node[-1] = SOLID
+    node[:, 0] = node[:, -1] = SOLID
+    h = ny // 2
+    node[1:-1, 1:h, 0] = INLET0
+    node[1:-1, h:-1, 0] = INLET0 + 1
+    node[nz // 2 - 2:nz // 2 + 2, -1, nx // 3:nx // 3 + 5] = INLET0 + 2
+    node[nz // 2 - 2:nz // 2 + 1, ny // 2 - 2:ny // 2 + 2, nx // 2 - 1:nx // 2 + 2] = SOLID
+    pts = random_simplex_points(rng, N, 3)
+    inlets = np.zeros((3, 3 + N))
+    inlets[0, :3], inlets[1, :3], inlets[2, :3] = (0.01, 0.002, -0.001), (0.006, -0.002, 0.003), (0.001, -0.008, 0.0)
+    inlets[:, 3:] = pts
+    x, y, z = _coords(nx, ny, nz)
+    C = np.empty((N, nz, ny, nx))
+    for i in range(N):
+        kx, ky, kz, ph = rng.uniform(1, 3), rng.uniform(1, 3), rng.uniform(1, 2), rng.uniform(0, 2 * np.pi)
+        C[i] = 1.0 + 0.6 * np.sin(2 * np.pi * kx * x / nx + ph) * np.cos(2 * np.pi * ky * y / ny) * np.cos(2 * np.pi * kz * z / nz)
+    C /= C.sum(axis=0, keepdims=True)
+    p = base_params(D3Q19, nx, ny, nz, N, sig, tau, m=m, omega_stab=1.0 / 90.0, name=f"inlet_channel3d_{nx}x{ny}x{nz}_N{N}")
+    p["C0"] = C
+    p["geometry"] = dict(node=node, inlets=inlets, outflow=False)
     return p
 
 

@@ -1,6 +1,6 @@
 """Open and complex boundaries of Sec. III C, the conditions that the emulsion and PaLS
-applications of Sec. V use: solid nodes inside the grid (D2Q9 and D3Q19), Dirichlet inlets of
-velocity and volume fraction, and the convective outflow (D2Q9).
+applications of Sec. V use: solid nodes inside the grid and Dirichlet inlets of velocity and
+volume fraction (D2Q9 and D3Q19), and the convective outflow (D2Q9).
 
 Oracle code (test infrastructure only): imported by tests, the smoke check and the
 benchmark's CPU baseline, never by the product path.
@@ -49,17 +49,20 @@ FLUID, SOLID, INLET0 = 0, 1, 2
 
 
 class Geometry:
-    """Node classes (shape of the grid), inlet table rows (vx, vy, C_1..C_N) and the outflow flag."""
+    """Node classes (shape of the grid), inlet table rows (v_b with one component per lattice
+    dimension, then C_1..C_N) and the outflow flag."""
 
     def __init__(self, prm, node, inlets=(), outflow=False):
-        if prm.lat.Q != 9 and (len(inlets) or outflow):
-            raise ValueError("inlets and the outflow are built for D2Q9; D3Q19 takes solid nodes")
+        if prm.lat.Q != 9 and outflow:
+            raise ValueError("the outflow is built for D2Q9")
+        D = prm.lat.dim
         self.node = np.asarray(node, dtype=np.int64).reshape(prm.shape)
-        tab = np.asarray(inlets, dtype=np.float64).reshape(-1, 2 + prm.N)
+        tab = np.asarray(inlets, dtype=np.float64).reshape(-1, D + prm.N)
         self.inlets = []
         for row in tab:
-            vb = np.array([row[0], row[1], 0.0])
-            Cb = row[2:].copy()
+            vb = np.zeros(3)
+            vb[:D] = row[:D]
+            Cb = row[D:].copy()
             # S_b: flux potential of the uniform state C_b (no Laplacian term)
             Sb = prm.tables.bulk_flux_potential(Cb.reshape(prm.N, 1, 1, 1))[:, 0, 0, 0]
             self.inlets.append((vb, Cb, Sb))

@@ -1107,14 +1107,17 @@ struct SplitTile {
     __device__ __forceinline__ int zwrap(int z) const { return nz > 1 ? wrap(z, nz) : 0; }
 };
 
-// GEO: a geometry of fluid and solid nodes, given as per-site solid-link masks (lmask: bit k when
-// x + e_k is solid, bit 31 when x is): links into a solid node take the wall rules (the stencil's
-// mirror rule, bounce-back), with the checked forms chosen per warp, and a solid node keeps its f
-// and C (its record carries C with v = S = 0 for the gather to copy).
+// GEO: a geometry of solid and inlet nodes (Sec. III C), given as per-site link masks (k_link_mask)
+// with the node classes and the inlet table: links into a solid node take the wall rules (the
+// stencil's mirror rule, bounce-back), with the checked forms chosen per warp; links into an
+// inlet node take the moving-wall bounce-back of the velocity inlet, while the stencil sees the
+// inlet's C_b; a solid or inlet node keeps its f and C and writes the record the gather reads
+// from it.
 template <int N, typename T, typename SF, int TX, int TY, int Q4, bool GEO = false>
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 / (TX * TY) : 256 / (TX * TY)))
 k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
-               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk, const unsigned *__restrict__ lmask) {
+               const T *__restrict__ Cin, T *__restrict__ vs, int zchunk, const unsigned *__restrict__ lmask,
+               const unsigned char *__restrict__ node, const T *__restrict__ inl) {
     using Sh = Split3DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1187,23 +1190,33 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
             const bool wchk = t.wallt || (g.wz && (z == 0 || z == nz - 1));
             unsigned wall0 = wchk ? wall_mask3(g, t.gx0, t.gy0, z) : 0u;
             const int s0 = t.sxy + t.nxy * z;
-            bool solid_site = false;
+            unsigned lm = 0u;
             if constexpr (GEO) {
-                const unsigned lm = lmask[s0];
-                solid_site = (lm >> 31) != 0u;
-                wall0 |= lm & 0x7FFFFFFFu;
+                lm = lmask[s0];
+                wall0 |= lm & kLinkSolidBits;
             }
-            const bool check = GEO ? __any_sync(__activemask(), wall0 != 0u) : wchk;
+            const bool check = GEO ? __any_sync(__activemask(), wall0 != 0u || (lm & kLinkInletNear) != 0u) : wchk;
             const T *pm = sA + slot4(z - 1) * ASLOT, *p0 = sA + slot4(z) * ASLOT, *pp = sA + slot4(z + 1) * ASLOT;
             const int ia = (t.ty + 1) * Sh::RX + (t.tx + 1);
             T c[N], lap[N], gr[N][3], gE[3];
             if (check) stencil3d<N, T, Sh::RX, true>(pm, p0, pp, Sh::PLANE, ia, wall0, c, lap, gr, gE);
             else       stencil3d<N, T, Sh::RX, false>(pm, p0, pp, Sh::PLANE, ia, 0u, c, lap, gr, gE);
-            if (GEO && solid_site) {
-                // a solid node keeps its state: f copied as stored, C passed to the gather
+            if (GEO && (lm & kLinkNonFluid)) {
+                // a solid or inlet node keeps its state: f copied as stored; its record is (C, 0, 0)
+                // for a solid node (the gather copies C back out) and the prescribed state
+                // (C_b, v_b, S_b) for an inlet node (the gather's terms from it carry g^eq of that
+                // state, and its own C stays C_b)
                 T rec[2 * N + 1];
+                const unsigned cls = link_class(lm);
+                if (cls >= kNodeInlet0) {
+                    const T *row = inl + (cls - kNodeInlet0) * (2 * N + 1);
 #pragma unroll
-                for (int a = 0; a < 2 * N + 1; ++a) rec[a] = a < N - 1 ? c[a] : T(0);
+                    for (int a = 0; a < N - 1; ++a) { rec[a] = row[3 + a]; rec[N + 2 + a] = row[N + 2 + a]; }
+                    rec[N - 1] = row[0]; rec[N] = row[1]; rec[N + 1] = row[2];
+                } else {
+#pragma unroll
+                    for (int a = 0; a < 2 * N + 1; ++a) rec[a] = a < N - 1 ? c[a] : T(0);
+                }
                 trec_store<T, 2 * N + 1>(vs, size_t(n), size_t(s0), rec);
 #pragma unroll
                 for (int k = 1; k < 19; ++k) fout[size_t(k - 1) * n + s0] = fin[size_t(k - 1) * n + s0];
@@ -1220,6 +1233,29 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
                 trec_store<T, 2 * N + 1>(vs, size_t(n), size_t(s0), rec);
             }
             collide3d<N, T>(cf, c, v, F, P, sp, dm, cur);
+            if constexpr (GEO) {
+                if (lm & kLinkInletNear) {
+                    // links into an inlet node (Sec. III C, velocity inlet): the population that
+                    // would enter it comes back as f*_k(x) - 6 w_k e_k . v_b into direction kbar
+                    const int nxy = t.nx * t.ny;
+                    sfor<1, 19, 1>([&](auto kc_) {
+                        constexpr int k = decltype(kc_)::value;
+                        constexpr int ex = LD3Q19::ex(k), ey = LD3Q19::ey(k), ez = LD3Q19::ez(k);
+                        if ((wall0 >> k) & 1u) return;      // beyond a wall or solid: plain bounce-back
+                        const int xx = t.sx + ex, yy = t.sy + ey, zz = z + ez;
+                        const int xw = xx < 0 ? xx + t.nx : (xx >= t.nx ? xx - t.nx : xx);
+                        const int yw = yy < 0 ? yy + t.ny : (yy >= t.ny ? yy - t.ny : yy);
+                        const int zw = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+                        const unsigned char cls = node[xw + t.nx * yw + nxy * zw];
+                        if (cls >= kNodeInlet0) {
+                            const T *row = inl + (cls - kNodeInlet0) * (2 * N + 1);
+                            const T eu = T(ex) * row[0] + T(ey) * row[1] + T(ez) * row[2];
+                            cur[k] -= T(6.0 * LD3Q19::w(k)) * eu;
+                            wall0 |= 1u << k;
+                        }
+                    });
+                }
+            }
             push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, cur, GEO && check);
         }
     };
@@ -1249,9 +1285,10 @@ struct Gather3DShape {
 // SF (the storage type of f, unused here) keeps the instantiations of the FP32, FP16 and BF16
 // translation units apart: each sets the shared-memory attribute of the kernel it launches.
 // TAUG: stored component populations (tau_g != 1), each of the thread's sites on its own.
-// GEO: a geometry of fluid and solid nodes (per-site solid-link masks as for the physics
-// kernel): a source inside a solid node bounces back, with the checked form chosen per warp,
-// and a solid node keeps its C.
+// GEO: a geometry of solid and inlet nodes (link masks as for the physics kernel): a source
+// inside a solid node bounces back, with the checked form chosen per warp; a source at an inlet
+// node contributes g^eq of the inlet's prescribed state through its record; a solid or inlet
+// node keeps its C.
 template <int N, typename T, typename SF, int TX, int TYT, int SPT, bool TAUG, bool GEO = false>
 __global__ void __launch_bounds__(TX * TYT, (sizeof(T) == 4 ? 512 / (TX * TYT) : 256 / (TX * TYT)))
 k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ Cout, int *__restrict__ flag, int zchunk,
@@ -1320,7 +1357,7 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
             for (int j = 0; j < SPT; ++j) {
                 wall[j] = check && own[j] ? wall_mask3(g, gx, gy0 + j, z) : 0u;
                 if constexpr (GEO)
-                    if (own[j]) wall[j] |= lmask[sx + nx * sy[j] + t.nxy * z] & 0x7FFFFFFFu;
+                    if (own[j]) wall[j] |= lmask[sx + nx * sy[j] + t.nxy * z] & kLinkSolidBits;
                 wany |= wall[j];
             }
             if constexpr (GEO) wany = __any_sync(__activemask(), wany != 0u) ? 1u : 0u;
@@ -1341,10 +1378,10 @@ k_split3d_gather(Geom g, T m, T omg, const T *__restrict__ vs, T *__restrict__ C
                 else      gather3d_stack<N, T, Sh::RX, false, true, SPT>(bm, b0, bp, Sh::PLANE, ib, wall, m, out);
             }
             if constexpr (GEO) {
-                // a solid node keeps its C (the first values of its record)
+                // a solid or inlet node keeps its C (the first values of its record)
 #pragma unroll
                 for (int j = 0; j < SPT; ++j) {
-                    if (!own[j] || (lmask[sx + nx * sy[j] + t.nxy * z] >> 31) == 0u) continue;
+                    if (!own[j] || (lmask[sx + nx * sy[j] + t.nxy * z] & kLinkNonFluid) == 0u) continue;
                     T r[RB::NVP + 1];
                     BRec<T, 2 * N + 2, true>::load(b0, Sh::PLANE, ib + j * Sh::RX, r);
 #pragma unroll
@@ -1392,7 +1429,8 @@ cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers 
     const dim3 grid = split3d_grid(g, TX, TY, slots, zchunk);
     k_split3d_phys<N, T, SF, TX, TY, Q4, GEO><<<grid, TX * TY, Sh::BYTES_A, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]), static_cast<const T *>(b.C[cur]),
-        static_cast<T *>(b.vs), zchunk, GEO ? b.lmask : nullptr);
+        static_cast<T *>(b.vs), zchunk, GEO ? b.lmask : nullptr, GEO ? b.node : nullptr,
+        GEO ? static_cast<const T *>(b.inl) : nullptr);
     return cudaGetLastError();
 }
 
@@ -1432,7 +1470,7 @@ struct Fused3DLaunch {
     static_assert(gather_fits<2, 2> && gather_fits<1, kSpt>, "the smallest gather tiles fit");
     static cudaError_t step(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
-        // a geometry of fluid and solid nodes: the split form's geometry kernels, one tile shape
+        // a geometry of solid and inlet nodes: the split form's geometry kernels, one tile shape
         if (b.node) return launch_split3d_phys<N, T, SF, 32, 4, Q4_PARAM, true>(g, cf, b, cur, st);
         // the no-phi ablation (flux potential of Eq. 12 without phi_j) and the stored component
         // populations (tau_g != 1) run in the split form only: every variant launches its physics
@@ -1476,7 +1514,7 @@ struct Fused3DLaunch {
                               {kFused ? "fused3d 32x4" : "split3d 32x4", kFused ? "fused3d 32x8" : "split3d 32x8",
                                "split3d 32x8", "split3d 32x4"},
                               &B::moments, &B::reduce, &B::init_f, &B::unpack_f, &B::pack_C, &B::init_g,
-                              int(sizeof(SF)), int(sizeof(T)), nullptr, &B::prepare_solid, &B::moments_solid,
+                              int(sizeof(SF)), int(sizeof(T)), &B::inlet_table3, &B::prepare_solid, &B::moments_solid,
                               {kFused ? 1 : 2, kFused ? 1 : 2, 2, 2},
                               {{kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER},
                                {kFused ? K_FUSED : K_PHYS, kFused ? K_FUSED : K_GATHER}, {K_PHYS, K_GATHER}, {K_PHYS, K_GATHER}},

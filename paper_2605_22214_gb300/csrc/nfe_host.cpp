@@ -711,32 +711,32 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         return NFE_OK;
     }
     if (!s->ops->geo_prepare) return fail(NFE_EUNSUPPORTED, "no geometry form for this lattice");
-    if (s->grid.lattice != NFE_D2Q9 && (ninlets != 0 || outflow))
-        return fail(NFE_EUNSUPPORTED, "inlets and the convective outflow run on D2Q9 only (D3Q19: fluid and solid nodes)");
+    if (s->grid.lattice != NFE_D2Q9 && outflow)
+        return fail(NFE_EUNSUPPORTED, "the convective outflow runs on D2Q9 only");
     if (s->buf.g[0]) return fail(NFE_EUNSUPPORTED, "open and complex boundaries need tau_g = 1");
     if (s->no_phi) return fail(NFE_EUNSUPPORTED, "open and complex boundaries together with NFE_NO_PHI");
     if (ninlets < 0 || ninlets > kMaxInlets) return fail(NFE_EINVAL, "ninlets must be 0..%d", kMaxInlets);
     if (ninlets > 0 && !inlets) return fail(NFE_EINVAL, "inlets is NULL");
     const int N = s->N, nx = s->geom.nx, ny = s->geom.ny;
+    const int D = s->ops->Q == 19 ? 3 : 2;           // velocity components of an inlet row
     const size_t n = size_t(s->geom.n);
     for (size_t i = 0; i < n; ++i)
         if (node[i] >= kNodeInlet0 + ninlets) return fail(NFE_EINVAL, "node class %d at site %zu (ninlets = %d)", int(node[i]), i, ninlets);
     // inlet rows in internal component order
-    std::vector<double> rows(size_t(std::max(ninlets, 1)) * (2 + N), 0.0);
+    std::vector<double> rows(size_t(std::max(ninlets, 1)) * (D + N), 0.0);
     for (int j = 0; j < ninlets; ++j) {
-        const double *r = inlets + size_t(j) * (2 + N);
+        const double *r = inlets + size_t(j) * (D + N);
         double sum = 0.0;
-        for (int a = 0; a < 2 + N; ++a)
+        for (int a = 0; a < D + N; ++a)
             if (!std::isfinite(r[a])) return fail(NFE_EINVAL, "inlet %d: non-finite value", j);
         for (int a = 0; a < N; ++a) {
-            if (r[2 + a] < 0.0) return fail(NFE_EINVAL, "inlet %d: C_b[%d] < 0", j, a);
-            sum += r[2 + a];
+            if (r[D + a] < 0.0) return fail(NFE_EINVAL, "inlet %d: C_b[%d] < 0", j, a);
+            sum += r[D + a];
         }
         if (std::fabs(sum - 1.0) > 1e-9) return fail(NFE_EINVAL, "inlet %d: C_b sums to %.17g, not 1", j, sum);
-        double *o = rows.data() + size_t(j) * (2 + N);
-        o[0] = r[0];
-        o[1] = r[1];
-        for (int a = 0; a < N; ++a) o[2 + a] = r[2 + s->uidx[a]];
+        double *o = rows.data() + size_t(j) * (D + N);
+        for (int a = 0; a < D; ++a) o[a] = r[a];
+        for (int a = 0; a < N; ++a) o[D + a] = r[D + s->uidx[a]];
     }
     if (outflow) {
         if (s->geom.wx) return fail(NFE_EINVAL, "outflow needs a periodic x axis (no x walls)");
@@ -749,7 +749,8 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
     geo_free(s);
     const size_t ce = s->ops->c_elem_bytes;
     if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->node_dev), n)) != NFE_OK) return st;
-    if ((st = dev_alloc(s, &s->inl_dev, size_t(std::max(ninlets, 1)) * 2 * N * ce)) != NFE_OK) { geo_free(s); return st; }
+    const size_t inl_row = size_t(2 * N + (D - 2));    // v_b (D), C_b and S_b of the evolved components
+    if ((st = dev_alloc(s, &s->inl_dev, size_t(std::max(ninlets, 1)) * inl_row * ce)) != NFE_OK) { geo_free(s); return st; }
     if (outflow) {
         s->ghost_bytes = size_t(N - 1) * ny * ce;
         for (int b = 0; b < 2; ++b)
@@ -763,7 +764,7 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.lmask), n * sizeof(unsigned))) != NFE_OK) { geo_free(s); return st; }
         s->geo_bytes += n * sizeof(unsigned);
     }
-    s->geo_bytes += n + size_t(std::max(ninlets, 1)) * 2 * N * ce + 2 * s->ghost_bytes;
+    s->geo_bytes += n + size_t(std::max(ninlets, 1)) * inl_row * ce + 2 * s->ghost_bytes;
     s->buf.node = s->node_dev;
     s->buf.inl = s->inl_dev;
     s->buf.outflow = outflow ? 1 : 0;

@@ -325,7 +325,8 @@ __device__ __forceinline__ void relaxation(const Coef<T> &cf, const T (&c)[N], T
 template <class L, int N, typename T, typename SF>
 __global__ void __launch_bounds__(256)
 k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ C,
-          double *__restrict__ out, int *__restrict__ flag, const unsigned char *__restrict__ node) {
+          double *__restrict__ out, int *__restrict__ flag, const unsigned char *__restrict__ node,
+          const T *__restrict__ inl) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     const int x = s % g.nx;
@@ -356,7 +357,13 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     T v2 = j2 + T(0.5) * (Fs[2] + cf.fb[2] + cc * cf.fc[2]);
     const T w0 = T(L::w(0));
     T P = (sumf - T(1.5) * w0 * (v0 * v0 + v1 * v1 + v2 * v2)) * T(1.0 / (3.0 * (1.0 - L::w(0))));
-    if (node && node[s] == kNodeSolid) v0 = v1 = v2 = P = Fs[0] = Fs[1] = Fs[2] = T(0);
+    if (node && node[s] != kNodeFluid) {
+        v0 = v1 = v2 = P = Fs[0] = Fs[1] = Fs[2] = T(0);
+        if (node[s] >= kNodeInlet0) {       // D3Q19 inlet row: v_b first
+            const T *row = inl + (node[s] - kNodeInlet0) * (2 * N + 1);
+            v0 = row[0]; v1 = row[1]; v2 = row[2];
+        }
+    }
 #pragma unroll
     for (int a = 0; a < N; ++a) {
         out[size_t(cf.uidx[a]) * n + s] = double(st.c[a]);
@@ -372,9 +379,13 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     if (bad) atomicOr(flag, 1);
 }
 
-// Solid links of every site of a geometry of fluid and solid nodes: bit k (k = 1..Q-1) when
+// Link mask of every site of a D3Q19 geometry (solid and inlet nodes): bit k (k = 1..18) when
 // x + e_k is a solid node (periodic wrap; a neighbour beyond an edge wall sets no bit, the wall
-// mask covers it), bit 31 when x itself is solid.
+// mask covers it), bits 19..25 the class of x when x is not a fluid node, bit 30 when a
+// neighbour is an inlet node, bit 31 when x is not a fluid node.
+constexpr unsigned kLinkSolidBits = 0x7FFFEu, kLinkInletNear = 1u << 30, kLinkNonFluid = 1u << 31;
+__device__ __forceinline__ unsigned link_class(unsigned m) { return (m >> 19) & 0x7Fu; }
+
 template <class L>
 __global__ void k_link_mask(Geom g, const unsigned char *__restrict__ node, unsigned *__restrict__ out) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -383,13 +394,50 @@ __global__ void k_link_mask(Geom g, const unsigned char *__restrict__ node, unsi
     const int r = s / g.nx;
     const int y = r % g.ny;
     const int z = r / g.ny;
-    unsigned m = node[s] == kNodeSolid ? (1u << 31) : 0u;
+    const unsigned cls = node[s];
+    unsigned m = cls != kNodeFluid ? (kLinkNonFluid | (cls << 19)) : 0u;
 #pragma unroll
     for (int k = 1; k < L::Q; ++k) {
         const int j = neighbour<L>(g, x, y, z, k);
-        if (j >= 0 && node[j] == kNodeSolid) m |= 1u << k;
+        if (j < 0) continue;
+        if (node[j] == kNodeSolid) m |= 1u << k;
+        else if (node[j] >= kNodeInlet0) m |= kLinkInletNear;
     }
     out[s] = m;
+}
+
+// D3Q19 inlet table: rows K x (3 + N) FP64 (v_b, C_b in internal order); out: K x (2N + 1) in the
+// compute type: v_b (3), C_b of the evolved components, S_b (Eq. 12 at the uniform C_b).
+template <int N, typename T>
+__global__ void k_inlet_table3(Coef<T> cf, const double *__restrict__ rows, int K, T *__restrict__ out) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K) return;
+    const double *r = rows + size_t(j) * (3 + N);
+    T c[N];
+#pragma unroll
+    for (int a = 0; a < N; ++a) c[a] = T(r[3 + a]);
+    T q[N - 1], S[N - 1];
+    flux_poly<N, T, Q4_GLOBAL>(c, cf, q);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) S[e] = c[e] * q[e];
+    flux_rest<N, T, Q4_GLOBAL>(c, cf, S);
+    T *o = out + size_t(j) * (2 * N + 1);
+    o[0] = T(r[0]); o[1] = T(r[1]); o[2] = T(r[2]);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) { o[3 + e] = c[e]; o[N + 2 + e] = S[e]; }
+}
+
+// C := C_b on the inlet nodes of a D3Q19 geometry.
+template <int N, typename T>
+__global__ void k_inlet_fill3(Geom g, const unsigned char *__restrict__ node, const T *__restrict__ inl,
+                              T *__restrict__ C) {
+    const long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (s >= g.n) return;
+    const unsigned char cls = node[s];
+    if (cls < kNodeInlet0) return;
+    const T *row = inl + (cls - kNodeInlet0) * (2 * N + 1);
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) C[size_t(e) * size_t(g.n) + s] = row[3 + e];
 }
 
 // f = f^eq(P = 0, v): f_k = s_k(v) for k >= 1 (Eqs. 27-28).
@@ -476,20 +524,30 @@ struct Launch {
     static cudaError_t moments(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
-            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, nullptr);
+            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, nullptr,
+            nullptr);
         return cudaGetLastError();
     }
-    // with the node classes of a geometry of fluid and solid nodes (D3Q19)
+    // with the node classes of a D3Q19 geometry (solid and inlet nodes)
     static cudaError_t moments_solid(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
-            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, b.node);
+            g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, b.node,
+            static_cast<const T *>(b.inl));
         return cudaGetLastError();
     }
-    // fluid and solid nodes alone: the per-site solid-link masks
-    static cudaError_t prepare_solid(const Geom &g, const Buffers &b, int, int, cudaStream_t st) {
+    // D3Q19 geometry: the per-site link masks, and C := C_b on the inlet nodes of buffer cur
+    static cudaError_t prepare_solid(const Geom &g, const Buffers &b, int cur, int ninl, cudaStream_t st) {
         if (!b.lmask) return cudaErrorInvalidValue;
         k_link_mask<L><<<blocks_for(g.n, 256), 256, 0, st>>>(g, b.node, b.lmask);
+        if (ninl > 0)
+            k_inlet_fill3<N, T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, b.node, static_cast<const T *>(b.inl),
+                                                                      static_cast<T *>(b.C[cur]));
+        return cudaGetLastError();
+    }
+    static cudaError_t inlet_table3(const void *coef, const double *rows, int K, void *out, cudaStream_t st) {
+        const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
+        k_inlet_table3<N, T><<<1, kMaxInlets, 0, st>>>(cf, rows, K, static_cast<T *>(out));
         return cudaGetLastError();
     }
     static cudaError_t reduce(const Geom &g, const Buffers &b, int, int nblocks, cudaStream_t st) {

@@ -184,17 +184,19 @@ def test_geometry_validation():
         s.set_geometry(open_left, g["inlets"], False)             # fine without the outflow
     q = W.janus_3d(n=16, radius=4.0)
     with nfe.Sim(q, "fp32") as s:
-        s.set_geometry(np.zeros(16 ** 3, np.uint8))              # D3Q19: fluid and solid nodes
+        s.set_geometry(np.zeros(16 ** 3, np.uint8))              # D3Q19: solid and inlet nodes
         with pytest.raises(nfe.NfeError) as e:
             s.set_geometry(np.zeros(16 ** 3, np.uint8), outflow=True)
         assert e.value.status == 7
-        one = np.zeros((1, 2 + q["N"]))
-        one[0, 2] = 1.0
+        one = np.zeros((1, 3 + q["N"]))                          # D3Q19 rows: v_b (3), C_b (N)
+        one[0, 3] = 1.0
         node = np.zeros(16 ** 3, np.uint8)
         node[0] = W.INLET0
+        s.set_geometry(node, one)
+        one[0, 4] = 0.5                                           # C_b no longer sums to 1
         with pytest.raises(nfe.NfeError) as e:
             s.set_geometry(node, one)
-        assert e.value.status == 7
+        assert e.value.status == 1
     r = dict(p, tau_g=1.3)
     with nfe.Sim(r, "fp64") as s:
         with pytest.raises(nfe.NfeError) as e:
@@ -231,3 +233,37 @@ def test_d3q19_solid_layers_equal_edge_walls_bitwise(precision):
     np.testing.assert_array_equal(gb["f"][:, 1:-1, 1:-1], ga["f"])
     np.testing.assert_array_equal(gb["C"][:, 1:-1, 1:-1], ga["C"])
     assert np.abs(gb["v"][:, node == W.SOLID]).max() == 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_inlet_channel_3d_matches_oracle(precision):
+    # D3Q19 inlets (two in the x = 0 plane, one in a wall plane), solid planes and a post
+    p = W.inlet_channel_3d()
+    steps = 30
+    _check(oracle_run(p, steps), gpu_run(p, steps, precision), precision)
+
+
+def test_uniform_inflow_is_a_fixed_point_d3q19_gpu():
+    # the oracle's pin on the GPU: a uniform mixture moving at v_b, fed by an inlet plane holding
+    # the same state, periodic in x, stays as it is
+    N, nx, ny, nz = 3, 40, 10, 8
+    sig = np.array([[0.0, 0.006, 0.007], [0.006, 0.0, 0.005], [0.007, 0.005, 0.0]])
+    p = W.base_params(W.D3Q19, nx, ny, nz, N, sig, 0.8, omega_stab=1 / 90)
+    node = np.zeros((nz, ny, nx), np.uint8)
+    node[..., 0] = W.INLET0
+    Cb, vb = np.array([0.2, 0.5, 0.3]), (0.01, 0.003, -0.004)
+    C0 = np.broadcast_to(Cb[:, None, None, None], (N, nz, ny, nx)).copy()
+    v0 = np.zeros((3, nz, ny, nx))
+    v0[0], v0[1], v0[2] = vb
+    with nfe.Sim(p, "fp64") as s:
+        s.set_fields(C0, v0)
+        s.set_geometry(node, np.array([[*vb, *Cb]]))
+        f0 = s.populations()
+        s.step(15)
+        s.sync()
+        C, v, _ = s.fields()
+        f1 = s.populations()
+    fl = node == W.FLUID
+    assert np.abs(f1 - f0)[:, fl].max() < 1e-15
+    assert np.abs(C - C0).max() < 1e-14
+    np.testing.assert_allclose(v[:, fl], np.array(vb)[:, None] * np.ones((1, int(fl.sum()))), rtol=0, atol=1e-15)

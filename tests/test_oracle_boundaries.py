@@ -215,9 +215,62 @@ def test_interior_block_conserves_every_component_d3q19():
     assert np.abs(v[:, geo.fluid]).max() > 1e-6
 
 
-def test_d3q19_rejects_inlets_and_outflow():
+def test_d3q19_rejects_the_outflow():
     p = W.base_params(W.D3Q19, 6, 5, 4, 3, _sigma3(), 0.8)
     prm = lbm.Params(p)
     node = np.zeros((4, 5, 6), int)
     with pytest.raises(ValueError):
         B.Geometry(prm, node, outflow=True)
+
+
+def test_uniform_inflow_is_a_fixed_point_d3q19():
+    # D3Q19, periodic in x: a uniform mixture moving at v_b (all three components nonzero) fed by
+    # an inlet plane at x = 0 holding the same state stays as it is; the fluid leaving at
+    # x = nx - 1 meets the inlet plane through the wrap, so the moving-wall rule acts on both
+    # faces of the plane
+    N, nx, ny, nz = 3, 8, 5, 4
+    p = W.base_params(W.D3Q19, nx, ny, nz, N, _sigma3(), 0.8, omega_stab=1 / 90)
+    prm = lbm.Params(p)
+    node = np.zeros((nz, ny, nx), int)
+    node[..., 0] = B.INLET0
+    Cb, vb = np.array([0.2, 0.5, 0.3]), (0.01, 0.003, -0.004)
+    geo = B.Geometry(prm, node, [[*vb, *Cb]])
+    C0 = np.broadcast_to(Cb[:, None, None, None], (N, nz, ny, nx)).copy()
+    v0 = np.zeros((3, nz, ny, nx))
+    v0[0], v0[1], v0[2] = vb
+    st = B.init_state(prm, geo, C0, v0)
+    f0, g0 = st.f.copy(), st.g.copy()
+    st = B.run(prm, geo, st, 15)
+    assert np.abs(st.f - f0)[:, geo.fluid].max() < 1e-15
+    assert np.abs(st.g - g0)[:, :, geo.fluid].max() < 1e-14
+    C, v, _, _ = B.fields(prm, geo, st)
+    np.testing.assert_allclose(v[:, node == B.INLET0], np.array(vb)[:, None] * np.ones((1, ny * nz)), atol=0)
+
+
+def test_inlet_feeds_a_closed_box_d3q19():
+    # an inlet in one face of a box with solid walls elsewhere: the composition C_b enters; and
+    # with v_b = 0 and the box's own composition the inlet face acts as a wall (a state at rest
+    # stays at rest)
+    N, nx, ny, nz = 3, 8, 6, 5
+    p = W.base_params(W.D3Q19, nx, ny, nz, N, _sigma3(), 0.8, omega_stab=1 / 90)
+    prm = lbm.Params(p)
+    node = np.full((nz, ny, nx), B.SOLID, int)
+    node[1:-1, 1:-1, 1:-1] = B.FLUID
+    node[2:4, 2:4, 0] = B.INLET0                             # a 2 x 2 inlet in the x = 0 face
+    Cb, vb = np.array([0.0, 1.0, 0.0]), (0.01, 0.0, 0.0)
+    geo = B.Geometry(prm, node, [[*vb, *Cb]])
+    C0 = np.zeros((N, nz, ny, nx))
+    C0[0] = 1.0
+    st = B.init_state(prm, geo, C0)
+    C_a, _, _, _ = B.fields(prm, geo, st)
+    st = B.run(prm, geo, st, 30)
+    C_b, _, _, _ = B.fields(prm, geo, st)
+    fl = geo.fluid
+    assert C_b[1][fl].sum() > C_a[1][fl].sum() + 0.01          # component 1 came in
+    assert np.isfinite(st.f).all() and np.isfinite(st.g).all()
+    Cr = np.array([0.3, 0.3, 0.4])
+    geo0 = B.Geometry(prm, node, [[0.0, 0.0, 0.0, *Cr]])
+    st = B.init_state(prm, geo0, np.broadcast_to(Cr[:, None, None, None], (N, nz, ny, nx)).copy())
+    f0, g0 = st.f.copy(), st.g.copy()
+    st = B.run(prm, geo0, st, 10)
+    assert np.abs(st.f - f0)[:, fl].max() < 1e-15 and np.abs(st.g - g0)[:, :, fl].max() < 1e-14
