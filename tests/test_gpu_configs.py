@@ -281,6 +281,55 @@ def _janus_drift(force_form, steps, every):
     return out
 
 
+def test_janus_c4_full_size_one_step_at_sampled_sites():
+    # c4 at its stated size (256^3, four drops of radius 32) in the launch configuration the
+    # benchmark times (FP32, the split step of variant 3): after 40 steps the GPU state is read
+    # back, one more step is taken, and at sampled sites (drop interfaces and random sites) the
+    # oracle takes that step on a 9^3 periodic window of the GPU state centred on the site.  A
+    # site's update reaches two sites out, so the window's centre is exact; the oracle's g
+    # enters the tau_g = 1 step only through C = sum_k g_k, so g_0 = C, g_k = 0 stands in.
+    p = W.janus_3d()
+    n = p["nx"]
+    with nfe.Sim(p, "fp32") as s:
+        s.set_fields(p["C0"])
+        s.set_variant(3)
+        s.step(40)
+        s.sync()
+        CA = s.fields()[0]
+        fA = s.populations()
+        s.step(1)
+        s.sync()
+        CB = s.fields()[0]
+        fB = s.populations()
+    rng = np.random.default_rng(44)
+    mid = np.argwhere(((CA > 0.2) & (CA < 0.8)).any(axis=0))
+    sites = [tuple(mid[i]) for i in rng.choice(len(mid), 12, replace=False)]
+    sites += [tuple(rng.integers(0, n, 3)) for _ in range(4)]
+    pw = dict(p, nx=9, ny=9, nz=9)
+    prm = lbm.Params(pw)
+    worst_c, worst_f = 0.0, 0.0
+    for (z0, y0, x0) in sites:
+        iz, iy, ix = ((np.arange(9) - 4 + c) % n for c in (z0, y0, x0))
+        win = np.ix_(iz, iy, ix)
+        Cw = np.stack([CA[a][win] for a in range(p["N"])])
+        fw = np.zeros((19, 9, 9, 9))
+        for k in range(1, 19):
+            fw[k] = fA[k - 1][win]
+        g = np.zeros((len(prm.evolved), 19, 9, 9, 9))
+        for a, c in enumerate(prm.evolved):
+            g[a, 0] = Cw[c]
+        st = lbm.step(prm, lbm.State(fw, g, 0), flux_form="factored")
+        Co = lbm.components(prm, st.g)[:, 4, 4, 4]
+        fo = st.f[1:, 4, 4, 4]
+        worst_c = max(worst_c, float(np.abs(CB[:, z0, y0, x0] - Co).max()))
+        worst_f = max(worst_f, float(np.abs(fB[:, z0, y0, x0] - fo).max() / np.abs(fw[1:]).max()))
+    print(f"c4 256^3, step 41 at {len(sites)} sites: max |C - oracle| {worst_c:.2e}, f {worst_f:.2e} (relative)")
+    # one FP32 step from the same state: C is rounded once (2^-24 relative) after increments of
+    # at most ~1e-2 formed with FP32 relative error; measured 4.3e-8 and 2.2e-7
+    assert worst_c < 1e-6, worst_c
+    assert worst_f < 1e-5, worst_f
+
+
 def test_janus_drift_nonconservative_vs_conservative():
     # Sec. IV A (Fig. of the Janus droplet): with the non-conservative force of Eq. 31 the
     # asymmetric Janus drop drifts; with the conservative force of Eq. 34 the mean velocity stays
