@@ -17,8 +17,8 @@
  *     fractions (Sec. III B, Eqs. 39-43) with tau_g = 1,
  *   - halfway bounce-back and the wall-gradient rule on walls, periodic
  *     wrap on every other edge (Sec. III C, Eqs. 44-45);
- *   - solid nodes anywhere in the grid and velocity and volume-fraction inlets (D2Q9 and
- *     D3Q19), and on D2Q9 the convective outflow (Sec. III C; nfe_set_geometry).
+ *   - solid nodes anywhere in the grid, velocity and volume-fraction inlets and the
+ *     convective outflow, on D2Q9 and D3Q19 (Sec. III C; nfe_set_geometry).
  *
  * Conventions shared by every call:
  *   - Site index s = x + nx * (y + ny * z), x fastest.  Field arrays are
@@ -217,16 +217,17 @@ nfe_status nfe_diagnostics(nfe_sim *sim, nfe_diag *out);
 nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, double *Sk);
 
 /* Open and complex boundaries (Sec. III C, the conditions that the emulsion and
- * patterned-surface applications of Sec. V use): solid nodes and inlets on D2Q9 and D3Q19, the
- * convective outflow on D2Q9.
+ * patterned-surface applications of Sec. V use), on D2Q9 and D3Q19: solid nodes, inlets and the
+ * convective outflow.
  * node: host, n bytes, one class per site (x fastest): 0 fluid, 1 solid, 2 + j inlet j;
  *   NULL removes the geometry (ninlets, inlets and outflow are then ignored).
  * inlets: host, ninlets x (D + N) doubles (D = 2 on D2Q9, 3 on D3Q19), row j = v_b (x, y,
  *   and z on D3Q19) then C_b of all N components in the user's order (finite, >= 0, summing
  *   to 1 within 1e-9);
  *   0 <= ninlets <= 64, NULL when ninlets = 0.
- * outflow: nonzero = convective outflow on the x = nx - 1 edge; then column 0 must
- *   hold no fluid node, column nx - 1 no inlet node, nx >= 3 and the x axis no wall.
+ * outflow: nonzero = convective outflow on the x = nx - 1 edge (a column on D2Q9, a plane on
+ *   D3Q19); then column (plane) 0 must hold no fluid node, column nx - 1 no inlet node,
+ *   nx >= 3 and the x axis no wall.  Column below means every (y, z) line's site x.
  * Rules: a solid node takes halfway bounce-back for f and for the component
  *   populations, and a neighbour inside it takes the value at x in every directional
  *   difference; links from inlet j carry f_k(x, t+1) = f*_kbar(x) + 2 w_k (e_k . v_b) /
@@ -241,7 +242,7 @@ nfe_status nfe_domain_size(nfe_sim *sim, double *L, int component, int nbins, do
  *   nfe_set_fields.  nfe_fields reports v = P = F_s = 0 on solid nodes and v = v_b, P = 0 on
  *   inlet nodes.  With outflow the raw state (nfe_get_state) also holds the ghost column,
  *   so set the geometry before restoring a state.
- * Errors: NFE_EUNSUPPORTED for the outflow on D3Q19, tau_g != 1 or NFE_NO_PHI;
+ * Errors: NFE_EUNSUPPORTED for tau_g != 1 or NFE_NO_PHI;
  *   NFE_EINVAL for a class
  *   outside 0 .. 1 + ninlets, a bad inlet row or a violated outflow condition (these leave
  *   the previous geometry in place); NFE_ENOMEM or NFE_ECUDA while the new geometry is being

@@ -371,12 +371,13 @@ def porous_3d(nx=40, ny=30, nz=20, N=4, seed=1041, walls=(False, False, True), t
     return p
 
 
-def inlet_channel_3d(nx=40, ny=18, nz=14, N=3, seed=1051, tau=0.8, m=1.0 / 50.0):
+def inlet_channel_3d(nx=40, ny=18, nz=14, N=3, seed=1051, tau=0.8, m=1.0 / 50.0, outflow=False):
     """A D3Q19 channel, periodic in x, with solid planes at y = 0, ny - 1 and z = 0, nz - 1, a
     solid post in the middle, and the plane x = 0 split into two inlets (lower and upper half in
     y) of different compositions and velocities (every velocity component nonzero), plus a third
-    inlet patch in the upper y plane; the interior starts as a seeded smooth mixture.  The fluid
-    leaving at x = nx - 1 meets the inlet plane through the wrap."""
+    inlet patch in the upper y plane; the interior starts as a seeded smooth mixture.  Without the
+    outflow the fluid leaving at x = nx - 1 meets the inlet plane through the wrap; with it the
+    plane x = nx - 1 takes the convective outflow."""
     rng = np.random.default_rng(seed)
     sig = random_sigma(rng, N)
     node = np.zeros((nz, ny, nx), dtype=np.uint8)
@@ -399,7 +400,7 @@ def inlet_channel_3d(nx=40, ny=18, nz=14, N=3, seed=1051, tau=0.8, m=1.0 / 50.0)
     C /= C.sum(axis=0, keepdims=True)
     p = base_params(D3Q19, nx, ny, nz, N, sig, tau, m=m, omega_stab=1.0 / 90.0, name=f"inlet_channel3d_{nx}x{ny}x{nz}_N{N}")
     p["C0"] = C
-    p["geometry"] = dict(node=node, inlets=inlets, outflow=False)
+    p["geometry"] = dict(node=node, inlets=inlets, outflow=bool(outflow))
     return p
 
 

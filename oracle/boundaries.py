@@ -1,6 +1,6 @@
 """Open and complex boundaries of Sec. III C, the conditions that the emulsion and PaLS
-applications of Sec. V use: solid nodes inside the grid and Dirichlet inlets of velocity and
-volume fraction (D2Q9 and D3Q19), and the convective outflow (D2Q9).
+applications of Sec. V use, on D2Q9 and D3Q19: solid nodes inside the grid, Dirichlet inlets of
+velocity and volume fraction, and the convective outflow.
 
 Oracle code (test infrastructure only): imported by tests, the smoke check and the
 benchmark's CPU baseline, never by the product path.
@@ -25,7 +25,7 @@ inlet   Velocity Dirichlet (the moving-wall bounce-back cited in Sec. III C), rh
         moving populations carry only C_i s_k(v) and the m S_i terms, so the net flux through
         the link is set by C_i(x), not by C_b.  Directional differences see C_b and E_B(C_b) at
         the inlet node, as Sec. III C asks.
-outflow Convective condition on the last column x = nx - 1 (the convective boundary
+outflow Convective condition on the last column (plane) x = nx - 1 (the convective boundary
         equations of Sec. III C): every population there becomes
         (f(N, t) + U f(N-1, t+1)) / (1 + U), U the mean of sum_k e_kx f_k(t+1) over the fluid
         nodes of column nx - 2 (the F/2 term of Eq. 37 is left out: F at t+1 is not known
@@ -53,8 +53,6 @@ class Geometry:
     dimension, then C_1..C_N) and the outflow flag."""
 
     def __init__(self, prm, node, inlets=(), outflow=False):
-        if prm.lat.Q != 9 and outflow:
-            raise ValueError("the outflow is built for D2Q9")
         D = prm.lat.dim
         self.node = np.asarray(node, dtype=np.int64).reshape(prm.shape)
         tab = np.asarray(inlets, dtype=np.float64).reshape(-1, D + prm.N)

@@ -239,7 +239,7 @@ def nfe_domain_size(h, N, component=0, nbins=0):
 def nfe_set_geometry(h, node, inlets=None, outflow=False):
     """Node classes (uint8 per site, x fastest; None removes the geometry), inlet rows
     (vx, vy, C_1..C_N on D2Q9; vx, vy, vz, C_1..C_N on D3Q19) and the convective outflow on the
-    x = nx - 1 edge (D2Q9)."""
+    x = nx - 1 edge."""
     if node is None:
         _check(load().nfe_set_geometry(h, None, 0, None, 0))
         return

@@ -320,6 +320,14 @@ __device__ __forceinline__ T vsq3(T a, T b, T c) {
     else return __fma_rn(c, c, __fma_rn(b, b, __dmul_rn(a, a)));
 }
 
+// Directions with e_kx > 0 (the links of a site of column nx - 1 into the outflow's ghost column).
+__host__ __device__ constexpr unsigned d3q19_xplus_mask() {
+    unsigned m = 0u;
+    for (int k = 1; k < 19; ++k)
+        if (LD3Q19::ex(k) > 0) m |= 1u << k;
+    return m;
+}
+
 // Push-streaming of the post-collision populations of one own site s0 (in-plane wrapped
 // coordinates sx, sy, plane zw) with halfway bounce-back (Eqs. 44-45) where wall0 has bit k set.
 // The periodic wrap is folded into six per-site neighbour offsets, so every site of a warp runs
@@ -327,7 +335,7 @@ __device__ __forceinline__ T vsq3(T a, T b, T c) {
 template <typename T, typename SF>
 __device__ __forceinline__ void push_store3d(const Coef<T> &cf, SF *__restrict__ fout, int n, int nx, int ny, int nz,
                                              int sx, int sy, int zw, int s0, unsigned wall0, const T (&f)[19],
-                                             bool checked = false) {
+                                             bool checked = false, unsigned drop = 0u) {
     const int nxy = nx * ny;
     const int dxp = sx == nx - 1 ? 1 - nx : 1, dxm = sx == 0 ? nx - 1 : -1;
     const int dyp = sy == ny - 1 ? nx - nxy : nx, dym = sy == 0 ? nxy - nx : -nx;
@@ -351,9 +359,10 @@ __device__ __forceinline__ void push_store3d(const Coef<T> &cf, SF *__restrict__
         sfor<1, 19, 1>([&](auto kc_) {
             constexpr int k = decltype(kc_)::value;
             constexpr int kb = opp(k);
-            // halfway bounce-back: f_kbar(x, t+1) = post_k(x)
+            // halfway bounce-back: f_kbar(x, t+1) = post_k(x); a dropped link (into the outflow's
+            // ghost column) stores nothing
             if ((wall0 >> k) & 1u) FStore<SF, T>::store(fout + (kb - 1) * n + s0, f[k], LD3Q19::w(kb), cf.fscale);
-            else FStore<SF, T>::store(fout + (k - 1) * n + target(kc_), f[k], LD3Q19::w(k), cf.fscale);
+            else if (!((drop >> k) & 1u)) FStore<SF, T>::store(fout + (k - 1) * n + target(kc_), f[k], LD3Q19::w(k), cf.fscale);
         });
     }
 }
@@ -1117,7 +1126,7 @@ template <int N, typename T, typename SF, int TX, int TY, int Q4, bool GEO = fal
 __global__ void __launch_bounds__(TX * TY, (sizeof(T) == 4 ? 512 / (TX * TY) : 256 / (TX * TY)))
 k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ fout,
                const T *__restrict__ Cin, T *__restrict__ vs, int zchunk, const unsigned *__restrict__ lmask,
-               const unsigned char *__restrict__ node, const T *__restrict__ inl) {
+               const unsigned char *__restrict__ node, const T *__restrict__ inl, const T *__restrict__ ghost) {
     using Sh = Split3DShape<N, T, TX, TY>;
     using RA = typename Sh::RA;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1126,19 +1135,40 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
     const SplitTile<TX, TY, Sh::NT, Sh::ITER, Sh::PLANE, Sh::RX> t(g, zchunk);
     const int n = t.n, nz = t.nz;
 
+    // with an outflow, the ring sites beyond x = nx - 1 come from the ghost column: their line
+    // (y) index, or -1 for every other ring site
+    int grow[Sh::ITER];
+#pragma unroll
+    for (int it = 0; it < Sh::ITER; ++it) {
+        grow[it] = -1;
+        if constexpr (GEO) {
+            const int i = t.tid + it * Sh::NT;
+            if (ghost && i < Sh::PLANE) {
+                const int ly = i / Sh::RX, lx = i - ly * Sh::RX;
+                if (t.x0 + lx - 1 == t.nx) {
+                    const int gy = t.y0 + ly - 1;
+                    grow[it] = g.wy ? min(max(gy, 0), t.ny - 1) : pwrap(gy, t.ny, t.tiny);
+                }
+            }
+        }
+    }
     // start the copies of the evolved C of plane za (tile + 1-ring), one group
     auto copy_A = [&](int za) {
         if (!(g.wz && (za < 0 || za >= nz))) {
-            const int zo = t.nxy * t.zwrap(za);
+            const int zw = t.zwrap(za);
+            const int zo = t.nxy * zw;
             T *base = sA + slot4(za) * ASLOT;
 #pragma unroll
             for (int it = 0; it < Sh::ITER; ++it) {
                 const int i = t.tid + it * Sh::NT;
                 if (t.roff[it] >= 0) {
+                    const int rows = t.ny * nz;
 #pragma unroll
-                    for (int a = 0; a < N - 1; ++a)
-                        cp_async_value<T>(base + (a / RA::PER) * Sh::PLANE * RA::PER + i * RA::PER + (a % RA::PER),
-                                          Cin + size_t(a) * n + (t.roff[it] + zo));
+                    for (int a = 0; a < N - 1; ++a) {
+                        const T *src = (GEO && grow[it] >= 0) ? ghost + size_t(a) * rows + (grow[it] + t.ny * zw)
+                                                              : Cin + size_t(a) * n + (t.roff[it] + zo);
+                        cp_async_value<T>(base + (a / RA::PER) * Sh::PLANE * RA::PER + i * RA::PER + (a % RA::PER), src);
+                    }
                 }
             }
         }
@@ -1195,7 +1225,8 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
                 lm = lmask[s0];
                 wall0 |= lm & kLinkSolidBits;
             }
-            const bool check = GEO ? __any_sync(__activemask(), wall0 != 0u || (lm & kLinkInletNear) != 0u) : wchk;
+            const bool check = GEO ? __any_sync(__activemask(), wall0 != 0u || (lm & (kLinkInletNear | kLinkOutflowCol)) != 0u)
+                                   : wchk;
             const T *pm = sA + slot4(z - 1) * ASLOT, *p0 = sA + slot4(z) * ASLOT, *pp = sA + slot4(z + 1) * ASLOT;
             const int ia = (t.ty + 1) * Sh::RX + (t.tx + 1);
             T c[N], lap[N], gr[N][3], gE[3];
@@ -1256,7 +1287,10 @@ k_split3d_phys(Geom g, Coef<T> cf, const SF *__restrict__ fin, SF *__restrict__ 
                     });
                 }
             }
-            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, cur, GEO && check);
+            // with an outflow, the links of column nx - 1 into the ghost column are dropped (the
+            // convective condition then replaces that column's populations)
+            const unsigned drop = (GEO && (lm & kLinkOutflowCol)) ? d3q19_xplus_mask() : 0u;
+            push_store3d<T, SF>(cf, fout, n, t.nx, t.ny, nz, t.sx, t.sy, z, s0, wall0, cur, GEO && check, drop);
         }
     };
     // one plane per iteration (two per iteration with the population registers swapping roles
@@ -1430,7 +1464,8 @@ cudaError_t launch_split3d_phys(const Geom &g, const Coef<T> &cf, const Buffers 
     k_split3d_phys<N, T, SF, TX, TY, Q4, GEO><<<grid, TX * TY, Sh::BYTES_A, st>>>(
         g, cf, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]), static_cast<const T *>(b.C[cur]),
         static_cast<T *>(b.vs), zchunk, GEO ? b.lmask : nullptr, GEO ? b.node : nullptr,
-        GEO ? static_cast<const T *>(b.inl) : nullptr);
+        GEO ? static_cast<const T *>(b.inl) : nullptr,
+        (GEO && b.outflow) ? static_cast<const T *>(b.ghost[cur]) : nullptr);
     return cudaGetLastError();
 }
 
@@ -1499,7 +1534,11 @@ struct Fused3DLaunch {
     static cudaError_t gather(const Geom &g, const void *coef, const Buffers &b, int cur, cudaStream_t st, int variant) {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         if (cf.no_phi || b.g[0] || !kFused) variant = (variant == 3 || variant == 0) ? 3 : 2;
-        if (b.node) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, false, true>(g, cf, b, cur, st);
+        if (b.node) {
+            cudaError_t e = launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, false, true>(g, cf, b, cur, st);
+            if (e == cudaSuccess && b.outflow) e = launch_outflow<LD3Q19, N, T, SF>(g, cf, b, cur, st);
+            return e;
+        }
         // stored component populations (tau_g != 1): one tile shape
         if (b.g[0]) return launch_split3d_gather<N, T, SF, 32, kGatherSmall, 2, true>(g, cf, b, cur, st);
         // variant 3: kSpt sites per thread on 32 x 4 threads (32 x 12 sites for FP32, N <= 4, else

@@ -1,5 +1,6 @@
-// Open and complex boundaries of the D2Q9 step (Sec. III C; the conditions of the microfluidic
-// and patterned-surface applications): the kernels besides the fused tile's geometry form.
+// Open and complex boundaries (Sec. III C; the conditions of the microfluidic and
+// patterned-surface applications): the kernels besides the fused tile's geometry form (the
+// outflow kernels also serve the D3Q19 split step).
 //
 //   k_outflow_sum / k_outflow_apply
 //                   the convective outflow on the x = nx - 1 edge, after the fused step:
@@ -7,8 +8,9 @@
 //                   every population and volume fraction of a fluid node in column nx - 1
 //                   becomes (old + U new(upstream)) / (1 + U); the ghost column follows
 //                   with C(nx - 1, t+1).  The F/2 term of the velocity is left out (F at
-//                   t+1 is not known at this point).  One thread per row; the partial sums
-//                   of U are added in a fixed order, so U is the same on every run.
+//                   t+1 is not known at this point).  One thread per row (a (y, z) line;
+//                   D2Q9 and D3Q19); the partial sums of U are added in a fixed order, so
+//                   U is the same on every run.
 //   k_inlet_table   per inlet: v_b, C_b and the flux potential S_b of the uniform state C_b
 //                   (Eq. 12 without the Laplacian term), in the compute type.
 //   k_geo_prepare   C := C_b on the inlet nodes; ghost := column nx - 1.
@@ -23,27 +25,28 @@ namespace nfe {
 constexpr int kOutflowRows = 32;
 
 // Part 1: per CTA, the sum of sum_k e_kx f_k(t+1) over the fluid nodes of column nx - 2 in its
-// rows, and their count (FP64, fixed order).
-template <typename T, typename SF>
+// rows, and their count (FP64, fixed order).  A row is one (y, z) line of the grid (rows =
+// ny nz; site x + nx r), so the same kernels serve D2Q9 and D3Q19.
+template <class L, typename T, typename SF>
 __global__ void __launch_bounds__(kOutflowRows)
 k_outflow_sum(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, const SF *__restrict__ fnew,
-              double *__restrict__ part) {
+              double *__restrict__ part, int rows) {
     __shared__ double red[kOutflowRows];
     __shared__ int cnt[kOutflowRows];
-    const int nx = g.nx, ny = g.ny;
+    const int nx = g.nx;
     const size_t n = size_t(g.n);
-    const int tid = threadIdx.x, y = blockIdx.x * kOutflowRows + tid;
+    const int tid = threadIdx.x, r = blockIdx.x * kOutflowRows + tid;
     double jx = 0.0;
     int c = 0;
-    if (y < ny) {
-        const int s = (nx - 2) + nx * y;
+    if (r < rows) {
+        const size_t s = size_t(nx - 2) + size_t(nx) * r;
         if (node[s] == kNodeFluid) {
             T j = T(0);
 #pragma unroll
-            for (int k = 1; k < 9; ++k)
-                if (LD2Q9::ex(k) != 0) {
-                    const T fk = FStore<SF, T>::load(fnew + (k - 1) * n + s, LD2Q9::w(k), cf.finv);
-                    j += LD2Q9::ex(k) > 0 ? fk : -fk;
+            for (int k = 1; k < L::Q; ++k)
+                if (L::ex(k) != 0) {
+                    const T fk = FStore<SF, T>::load(fnew + (k - 1) * n + s, L::w(k), cf.finv);
+                    j += L::ex(k) > 0 ? fk : -fk;
                 }
             jx = double(j);
             c = 1;
@@ -60,14 +63,15 @@ k_outflow_sum(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, const 
 }
 
 // Part 2: U from the partial sums (every CTA adds them in the same order), then the update of
-// its rows of column nx - 1 and of the ghost column.
-template <int N, typename T, typename SF>
+// its rows of column nx - 1 and of the ghost column (ghost value e of row r at e rows + r).
+template <class L, int N, typename T, typename SF>
 __global__ void __launch_bounds__(kOutflowRows)
 k_outflow_apply(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, const SF *__restrict__ fold,
                 SF *__restrict__ fnew, const T *__restrict__ Cold, T *__restrict__ Cnew,
-                const T *__restrict__ gh_in, T *__restrict__ gh_out, const double *__restrict__ part, int nparts) {
+                const T *__restrict__ gh_in, T *__restrict__ gh_out, const double *__restrict__ part, int nparts,
+                int rows) {
     __shared__ double Us;
-    const int nx = g.nx, ny = g.ny;
+    const int nx = g.nx;
     const size_t n = size_t(g.n);
     if (threadIdx.x == 0) {
         double sum = 0.0, c = 0.0;
@@ -77,32 +81,39 @@ k_outflow_apply(Geom g, Coef<T> cf, const unsigned char *__restrict__ node, cons
     __syncthreads();
     const double U = Us;
     const T u = T(U), inv = T(1.0 / (1.0 + U));
-    const int y = blockIdx.x * kOutflowRows + threadIdx.x;
-    if (y >= ny) return;
-    const int sN = (nx - 1) + nx * y, sM = (nx - 2) + nx * y;
+    const int r = blockIdx.x * kOutflowRows + threadIdx.x;
+    if (r >= rows) return;
+    const size_t sN = size_t(nx - 1) + size_t(nx) * r, sM = size_t(nx - 2) + size_t(nx) * r;
     if (node[sN] == kNodeFluid) {
 #pragma unroll
-        for (int k = 1; k < 9; ++k) {
-            const T a = FStore<SF, T>::load(fold + (k - 1) * n + sN, LD2Q9::w(k), cf.finv);
-            const T b = FStore<SF, T>::load(fnew + (k - 1) * n + sM, LD2Q9::w(k), cf.finv);
-            FStore<SF, T>::store(fnew + (k - 1) * n + sN, (a + u * b) * inv, LD2Q9::w(k), cf.fscale);
+        for (int k = 1; k < L::Q; ++k) {
+            const T a = FStore<SF, T>::load(fold + (k - 1) * n + sN, L::w(k), cf.finv);
+            const T b = FStore<SF, T>::load(fnew + (k - 1) * n + sM, L::w(k), cf.finv);
+            FStore<SF, T>::store(fnew + (k - 1) * n + sN, (a + u * b) * inv, L::w(k), cf.fscale);
         }
 #pragma unroll
         for (int e = 0; e < N - 1; ++e) Cnew[e * n + sN] = (Cold[e * n + sN] + u * Cnew[e * n + sM]) * inv;
     }
 #pragma unroll
-    for (int e = 0; e < N - 1; ++e) gh_out[e * ny + y] = (gh_in[e * ny + y] + u * Cnew[e * n + sN]) * inv;
+    for (int e = 0; e < N - 1; ++e) gh_out[size_t(e) * rows + r] = (gh_in[size_t(e) * rows + r] + u * Cnew[e * n + sN]) * inv;
+}
+
+template <class L, int N, typename T, typename SF>
+cudaError_t launch_outflow(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
+    const int rows = g.ny * g.nz;
+    const int blocks = (rows + kOutflowRows - 1) / kOutflowRows;
+    k_outflow_sum<L, T, SF><<<blocks, kOutflowRows, 0, st>>>(g, cf, b.node, static_cast<const SF *>(b.f[1 - cur]), b.opart,
+                                                             rows);
+    k_outflow_apply<L, N, T, SF><<<blocks, kOutflowRows, 0, st>>>(
+        g, cf, b.node, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
+        static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]),
+        static_cast<const T *>(b.ghost[cur]), static_cast<T *>(b.ghost[1 - cur]), b.opart, blocks, rows);
+    return cudaGetLastError();
 }
 
 template <int N, typename T, typename SF>
 cudaError_t launch_outflow2d(const Geom &g, const Coef<T> &cf, const Buffers &b, int cur, cudaStream_t st) {
-    const int blocks = (g.ny + kOutflowRows - 1) / kOutflowRows;
-    k_outflow_sum<T, SF><<<blocks, kOutflowRows, 0, st>>>(g, cf, b.node, static_cast<const SF *>(b.f[1 - cur]), b.opart);
-    k_outflow_apply<N, T, SF><<<blocks, kOutflowRows, 0, st>>>(
-        g, cf, b.node, static_cast<const SF *>(b.f[cur]), static_cast<SF *>(b.f[1 - cur]),
-        static_cast<const T *>(b.C[cur]), static_cast<T *>(b.C[1 - cur]),
-        static_cast<const T *>(b.ghost[cur]), static_cast<T *>(b.ghost[1 - cur]), b.opart, blocks);
-    return cudaGetLastError();
+    return launch_outflow<LD2Q9, N, T, SF>(g, cf, b, cur, st);
 }
 
 // rows: K x (2 + N) FP64 (vx, vy, C_b in internal order); out: K x 2N in the compute type.

@@ -107,7 +107,7 @@ struct nfe_sim {
     unsigned char *node_dev = nullptr;
     void *inl_dev = nullptr;
     int ninlets = 0;
-    size_t ghost_bytes = 0;           // one ghost buffer ((N-1) x ny), 0 without an outflow
+    size_t ghost_bytes = 0;           // one ghost buffer ((N-1) x ny nz), 0 without an outflow
     size_t geo_bytes = 0;             // device bytes held by the geometry
     nfe_alloc_fn ualloc = nullptr;    // caller's device allocator (null: cudaMalloc)
     nfe_free_fn ufree = nullptr;
@@ -711,8 +711,6 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         return NFE_OK;
     }
     if (!s->ops->geo_prepare) return fail(NFE_EUNSUPPORTED, "no geometry form for this lattice");
-    if (s->grid.lattice != NFE_D2Q9 && outflow)
-        return fail(NFE_EUNSUPPORTED, "the convective outflow runs on D2Q9 only");
     if (s->buf.g[0]) return fail(NFE_EUNSUPPORTED, "open and complex boundaries need tau_g = 1");
     if (s->no_phi) return fail(NFE_EUNSUPPORTED, "open and complex boundaries together with NFE_NO_PHI");
     if (ninlets < 0 || ninlets > kMaxInlets) return fail(NFE_EINVAL, "ninlets must be 0..%d", kMaxInlets);
@@ -738,12 +736,14 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
         for (int a = 0; a < D; ++a) o[a] = r[a];
         for (int a = 0; a < N; ++a) o[D + a] = r[D + s->uidx[a]];
     }
+    const int nrows = ny * s->geom.nz;                // (y, z) lines of the grid
     if (outflow) {
         if (s->geom.wx) return fail(NFE_EINVAL, "outflow needs a periodic x axis (no x walls)");
         if (nx < 3) return fail(NFE_EINVAL, "outflow needs nx >= 3");
-        for (int y = 0; y < ny; ++y) {
-            if (node[size_t(nx) * y] == kNodeFluid) return fail(NFE_EINVAL, "outflow: fluid node at (0, %d)", y);
-            if (node[size_t(nx) * y + nx - 1] >= kNodeInlet0) return fail(NFE_EINVAL, "outflow: inlet node at (%d, %d)", nx - 1, y);
+        for (int r = 0; r < nrows; ++r) {
+            if (node[size_t(nx) * r] == kNodeFluid) return fail(NFE_EINVAL, "outflow: fluid node at (0, %d, %d)", r % ny, r / ny);
+            if (node[size_t(nx) * r + nx - 1] >= kNodeInlet0)
+                return fail(NFE_EINVAL, "outflow: inlet node at (%d, %d, %d)", nx - 1, r % ny, r / ny);
         }
     }
     geo_free(s);
@@ -752,10 +752,10 @@ nfe_status nfe_set_geometry(nfe_sim *s, const uint8_t *node, int ninlets, const 
     const size_t inl_row = size_t(2 * N + (D - 2));    // v_b (D), C_b and S_b of the evolved components
     if ((st = dev_alloc(s, &s->inl_dev, size_t(std::max(ninlets, 1)) * inl_row * ce)) != NFE_OK) { geo_free(s); return st; }
     if (outflow) {
-        s->ghost_bytes = size_t(N - 1) * ny * ce;
+        s->ghost_bytes = size_t(N - 1) * nrows * ce;
         for (int b = 0; b < 2; ++b)
             if ((st = dev_alloc(s, &s->buf.ghost[b], s->ghost_bytes)) != NFE_OK) { geo_free(s); return st; }
-        const size_t pb = size_t(2 * ((ny + 31) / 32)) * sizeof(double);   // 2 per CTA of the outflow (32 rows)
+        const size_t pb = size_t(2 * ((nrows + 31) / 32)) * sizeof(double);   // 2 per CTA of the outflow (32 rows)
         if ((st = dev_alloc(s, reinterpret_cast<void **>(&s->buf.opart), pb)) != NFE_OK) { geo_free(s); return st; }
         s->geo_bytes += pb;
     }

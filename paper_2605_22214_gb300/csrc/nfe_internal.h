@@ -85,7 +85,7 @@ struct Buffers {
     // geometry (null when the grid has none)
     const unsigned char *node;   // node class per site
     const void *inl;             // inlet table, compute type: per inlet vx, vy, C_b (N-1), S_b (N-1)
-    void *ghost[2];              // outflow ghost column, (N-1) x ny, compute type, or null
+    void *ghost[2];              // outflow ghost column, (N-1) x (ny nz), compute type, or null
     int outflow;                 // convective outflow on the x = nx - 1 edge
     double *opart;               // outflow partial sums (2 per 32 rows), or null
     unsigned *lmask;             // D3Q19 geometry: per site, bit k set when x + e_k is a solid node

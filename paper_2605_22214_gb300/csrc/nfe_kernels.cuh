@@ -219,7 +219,8 @@ struct Stencil {
 template <class L, int N, typename T>
 __device__ __forceinline__ void stencil(const Geom &g, const Coef<T> &cf, const T *__restrict__ C,
                                         int s, int x, int y, int z, Stencil<L, N, T> &st,
-                                        const unsigned char *__restrict__ node = nullptr) {
+                                        const unsigned char *__restrict__ node = nullptr,
+                                        const T *__restrict__ ghost = nullptr) {
     const size_t n = size_t(g.n);
     T rest = T(0);
 #pragma unroll
@@ -235,11 +236,18 @@ __device__ __forceinline__ void stencil(const Geom &g, const Coef<T> &cf, const 
         const int j = neighbour<L>(g, x, y, z, k);
         st.nb[k] = j;
         if (j < 0) continue;               // wall: psi(x + e_k) := psi(x), difference 0
-        if (node && node[j] == kNodeSolid) continue;   // solid node: the same rule
+        // with an outflow, column nx - 1 sees the ghost column beyond it (solid where column
+        // nx - 1 of that line is)
+        const bool gcol = ghost && x == g.nx - 1 && L::ex(k) > 0;
+        const int jrow = j / g.nx;
+        if (node && node[gcol ? (g.nx - 1) + g.nx * jrow : j] == kNodeSolid) continue;   // solid node: the same rule
         T cn[N];
         T r2 = T(0);
 #pragma unroll
-        for (int a = 0; a < N - 1; ++a) { cn[a] = C[a * n + j]; r2 += cn[a]; }
+        for (int a = 0; a < N - 1; ++a) {
+            cn[a] = gcol ? ghost[size_t(a) * (g.ny * g.nz) + jrow] : C[a * n + j];
+            r2 += cn[a];
+        }
         cn[N - 1] = T(1) - r2;
         const T wk = T(L::w(k));
 #pragma unroll
@@ -326,7 +334,7 @@ template <class L, int N, typename T, typename SF>
 __global__ void __launch_bounds__(256)
 k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ C,
           double *__restrict__ out, int *__restrict__ flag, const unsigned char *__restrict__ node,
-          const T *__restrict__ inl) {
+          const T *__restrict__ inl, const T *__restrict__ ghost) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     const int x = s % g.nx;
@@ -335,7 +343,7 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     const int z = r / g.ny;
     const size_t n = size_t(g.n);
     Stencil<L, N, T> st;
-    stencil<L, N, T>(g, cf, C, s, x, y, z, st, node);
+    stencil<L, N, T>(g, cf, C, s, x, y, z, st, node, ghost);
     T Fs[3], S[N - 1];
     force_and_potential<L, N, T>(cf, st, Fs, S);
     T sumf = T(0), j0 = T(0), j1 = T(0), j2 = T(0);
@@ -379,15 +387,18 @@ k_moments(Geom g, Coef<T> cf, const SF *__restrict__ fin, const T *__restrict__ 
     if (bad) atomicOr(flag, 1);
 }
 
-// Link mask of every site of a D3Q19 geometry (solid and inlet nodes): bit k (k = 1..18) when
-// x + e_k is a solid node (periodic wrap; a neighbour beyond an edge wall sets no bit, the wall
-// mask covers it), bits 19..25 the class of x when x is not a fluid node, bit 30 when a
-// neighbour is an inlet node, bit 31 when x is not a fluid node.
-constexpr unsigned kLinkSolidBits = 0x7FFFEu, kLinkInletNear = 1u << 30, kLinkNonFluid = 1u << 31;
+// Link mask of every site of a D3Q19 geometry (solid and inlet nodes, convective outflow): bit k
+// (k = 1..18) when x + e_k is a solid node (periodic wrap; a neighbour beyond an edge wall sets no
+// bit, the wall mask covers it), bits 19..25 the class of x when x is not a fluid node, bit 29
+// when x lies in the outflow column nx - 1 (its links with e_kx > 0 end in the ghost column, solid
+// where column nx - 1 is), bit 30 when a neighbour is an inlet node, bit 31 when x is not a fluid
+// node.
+constexpr unsigned kLinkSolidBits = 0x7FFFEu, kLinkOutflowCol = 1u << 29, kLinkInletNear = 1u << 30,
+                   kLinkNonFluid = 1u << 31;
 __device__ __forceinline__ unsigned link_class(unsigned m) { return (m >> 19) & 0x7Fu; }
 
 template <class L>
-__global__ void k_link_mask(Geom g, const unsigned char *__restrict__ node, unsigned *__restrict__ out) {
+__global__ void k_link_mask(Geom g, const unsigned char *__restrict__ node, unsigned *__restrict__ out, int outflow) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= g.n) return;
     const int x = s % g.nx;
@@ -396,14 +407,31 @@ __global__ void k_link_mask(Geom g, const unsigned char *__restrict__ node, unsi
     const int z = r / g.ny;
     const unsigned cls = node[s];
     unsigned m = cls != kNodeFluid ? (kLinkNonFluid | (cls << 19)) : 0u;
+    const bool ocol = outflow && x == g.nx - 1;
+    if (ocol) m |= kLinkOutflowCol;
 #pragma unroll
     for (int k = 1; k < L::Q; ++k) {
         const int j = neighbour<L>(g, x, y, z, k);
         if (j < 0) continue;
+        if (ocol && L::ex(k) > 0) {
+            // the ghost column: solid where column nx - 1 of that line is
+            if (node[(g.nx - 1) + g.nx * (j / g.nx)] == kNodeSolid) m |= 1u << k;
+            continue;
+        }
         if (node[j] == kNodeSolid) m |= 1u << k;
         else if (node[j] >= kNodeInlet0) m |= kLinkInletNear;
     }
     out[s] = m;
+}
+
+// Ghost column of the convective outflow from column nx - 1 of buffer cur (rows = ny nz lines).
+template <int N, typename T>
+__global__ void k_ghost_init(Geom g, const T *__restrict__ C, T *__restrict__ ghost) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int rows = g.ny * g.nz;
+    if (r >= rows) return;
+#pragma unroll
+    for (int e = 0; e < N - 1; ++e) ghost[size_t(e) * rows + r] = C[size_t(e) * size_t(g.n) + size_t(g.nx - 1) + size_t(g.nx) * r];
 }
 
 // D3Q19 inlet table: rows K x (3 + N) FP64 (v_b, C_b in internal order); out: K x (2N + 1) in the
@@ -525,7 +553,7 @@ struct Launch {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
             g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, nullptr,
-            nullptr);
+            nullptr, nullptr);
         return cudaGetLastError();
     }
     // with the node classes of a D3Q19 geometry (solid and inlet nodes)
@@ -533,16 +561,21 @@ struct Launch {
         const Coef<T> &cf = *static_cast<const Coef<T> *>(coef);
         k_moments<L, N, T, SF><<<blocks_for(g.n, 256), 256, 0, st>>>(
             g, cf, static_cast<const SF *>(b.f[cur]), static_cast<const T *>(b.C[cur]), b.fields, b.flag, b.node,
-            static_cast<const T *>(b.inl));
+            static_cast<const T *>(b.inl), b.outflow ? static_cast<const T *>(b.ghost[cur]) : nullptr);
         return cudaGetLastError();
     }
-    // D3Q19 geometry: the per-site link masks, and C := C_b on the inlet nodes of buffer cur
+    // D3Q19 geometry: the per-site link masks, C := C_b on the inlet nodes of buffer cur and, with
+    // an outflow, the ghost column
     static cudaError_t prepare_solid(const Geom &g, const Buffers &b, int cur, int ninl, cudaStream_t st) {
         if (!b.lmask) return cudaErrorInvalidValue;
-        k_link_mask<L><<<blocks_for(g.n, 256), 256, 0, st>>>(g, b.node, b.lmask);
+        k_link_mask<L><<<blocks_for(g.n, 256), 256, 0, st>>>(g, b.node, b.lmask, b.outflow);
         if (ninl > 0)
             k_inlet_fill3<N, T><<<blocks_for(g.n, 256), 256, 0, st>>>(g, b.node, static_cast<const T *>(b.inl),
                                                                       static_cast<T *>(b.C[cur]));
+        // column nx - 1 holds no inlet node, so the ghost copy does not race with the fill
+        if (b.outflow)
+            k_ghost_init<N, T><<<blocks_for((long long)g.ny * g.nz, 256), 256, 0, st>>>(
+                g, static_cast<const T *>(b.C[cur]), static_cast<T *>(b.ghost[cur]));
         return cudaGetLastError();
     }
     static cudaError_t inlet_table3(const void *coef, const double *rows, int K, void *out, cudaStream_t st) {

@@ -215,12 +215,25 @@ def test_interior_block_conserves_every_component_d3q19():
     assert np.abs(v[:, geo.fluid]).max() > 1e-6
 
 
-def test_d3q19_rejects_the_outflow():
-    p = W.base_params(W.D3Q19, 6, 5, 4, 3, _sigma3(), 0.8)
+def test_uniform_inflow_through_to_the_outflow_is_a_fixed_point_d3q19():
+    # D3Q19 version of the pin above: inlet plane at x = 0, convective outflow at x = nx - 1
+    N, nx, ny, nz = 3, 10, 5, 4
+    p = W.base_params(W.D3Q19, nx, ny, nz, N, _sigma3(), 0.8, omega_stab=1 / 90)
     prm = lbm.Params(p)
-    node = np.zeros((4, 5, 6), int)
-    with pytest.raises(ValueError):
-        B.Geometry(prm, node, outflow=True)
+    node = np.zeros((nz, ny, nx), int)
+    node[..., 0] = B.INLET0
+    Cb, vb = np.array([0.2, 0.5, 0.3]), (0.01, 0.003, -0.002)
+    geo = B.Geometry(prm, node, [[*vb, *Cb]], outflow=True)
+    C0 = np.broadcast_to(Cb[:, None, None, None], (N, nz, ny, nx)).copy()
+    v0 = np.zeros((3, nz, ny, nx))
+    v0[0], v0[1], v0[2] = vb
+    st = B.init_state(prm, geo, C0, v0)
+    f0, g0, gh0 = st.f.copy(), st.g.copy(), st.ghost.copy()
+    assert gh0.shape == (N - 1, nz, ny)
+    st = B.run(prm, geo, st, 15)
+    assert np.abs(st.f - f0)[:, geo.fluid].max() < 1e-15
+    assert np.abs(st.g - g0)[:, :, geo.fluid].max() < 1e-14
+    assert np.abs(st.ghost - gh0).max() < 1e-15
 
 
 def test_uniform_inflow_is_a_fixed_point_d3q19():
