@@ -74,8 +74,8 @@ enum {
     NFE_NONCONSERVATIVE_FORCE = 1,  /* F_s = sum_i mu_i grad C_i (Eq. 31) instead of Eq. 34 */
     NFE_NO_PHI = 2                  /* drop phi_j from the flux potential (Eq. 12): the ablation in
                                        which an absent component nucleates at interfaces (Sec. IV).
-                                       Single simulations only (D3Q19: the split form of the step);
-                                       nfe_batch_create returns NFE_EUNSUPPORTED for batches */
+                                       D3Q19: the split form of the step; batches: per-step
+                                       launches on 32 x 8 tiles (nfe_batch_set_mode) */
 };
 
 #define NFE_MAX_N 8
@@ -116,9 +116,9 @@ typedef struct {
     double tau_g;             /* relaxation time of the component populations g (Sec. III B); 0 or 1
                                  selects tau_g = 1, where g* = g^eq and g needs no storage.  Other
                                  values (> 1/2) store the N-1 evolved components' g populations
-                                 ((N-1) x Q planes, two buffers, compute type); single simulations
-                                 only (D3Q19: the split form of the step): NFE_EUNSUPPORTED for
-                                 batches, with a geometry and together with NFE_NO_PHI */
+                                 ((N-1) x Q planes, two buffers, compute type).  D3Q19: the split
+                                 form of the step; batches: per-step launches on 32 x 8 tiles.
+                                 NFE_EUNSUPPORTED with a geometry and together with NFE_NO_PHI */
     double component_force[3];    /* a body force acting on one component in proportion to its
                                      volume fraction, F += C_c F_c (the PaLS study of Sec. V drives
                                      only the droplet of fluid 2); all zero = none */
@@ -299,7 +299,10 @@ const char *nfe_last_error(void);
  * runs out (NFE_ETIMEOUT from nfe_batch_sync) the kernel returns early and the
  * states are undefined, but the GPU context stays usable.
  * Constraints: D2Q9 grids, N = 2..5, one precision for the whole batch
- * (NFE_FP32 or NFE_FP64), params[i].cuda_stream ignored (params[0]'s is used). */
+ * (NFE_FP32 or NFE_FP64), params[i].cuda_stream ignored (params[0]'s is used).  Members with
+ * NFE_NO_PHI or tau_g != 1 run in the per-step form on 32 x 8 tiles: with such a member,
+ * nfe_batch_set_mode(NFE_BATCH_PERSISTENT) and nfe_batch_set_barrier_test return
+ * NFE_EUNSUPPORTED. */
 typedef struct nfe_batch nfe_batch;
 
 typedef struct {

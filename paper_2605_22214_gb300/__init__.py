@@ -428,14 +428,16 @@ class Sim:
 
 
 class Batch:
-    """Many independent D2Q9 simulations advanced by one persistent kernel launch."""
+    """Many independent D2Q9 simulations advanced together (per-step launches or one persistent
+    launch); a member's dict may carry "flags" and "tau_g"."""
 
     def __init__(self, plist, precision="fp32", stream=None):
         self.plist = list(plist)
         n = len(self.plist)
         grids = (nfe_grid * n)(*[make_grid(p) for p in self.plist])
         Ns = (C.c_int * n)(*[int(p["N"]) for p in self.plist])
-        self._params = [make_params(p, precision, stream) for p in self.plist]
+        # per-member flags (NFE_NO_PHI, NFE_NONCONSERVATIVE_FORCE) and tau_g come with its dict
+        self._params = [make_params(p, precision, stream, flags=int(p.get("flags", 0))) for p in self.plist]
         params = (nfe_params * n)(*self._params)
         h = C.c_void_p()
         _check(load().nfe_batch_create(n, grids, Ns, params, C.byref(h)))

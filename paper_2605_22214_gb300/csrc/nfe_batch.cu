@@ -120,10 +120,12 @@ k_batch_persistent(const BatchSim<T> *__restrict__ sims, const int4 *__restrict_
     }
 }
 
-// One launch per step and per component count, one CTA per work item (the non-persistent
-// batched form).  The work list is grouped by N, so each launch covers one contiguous range and
-// carries a single inlined tile body (smaller code, its own register allocation, no switch).
-template <typename T, typename SF, int TX, int TY, int NN>
+// One launch per step and per (component count, form), one CTA per work item (the
+// non-persistent batched form).  The work list is grouped that way, so each launch covers one
+// contiguous range and carries a single inlined tile body (smaller code, its own register
+// allocation, no switch).  FORM 1: the no-phi flux potential; FORM 2: stored component
+// populations (tau_g != 1; 32 x 8 tiles only).
+template <typename T, typename SF, int TX, int TY, int NN, int FORM>
 __global__ void __launch_bounds__(TX * TY, (BatchOcc<T, TX * TY>::value))
 k_batch_step(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ items, int parity) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -135,9 +137,11 @@ k_batch_step(const BatchSim<T> *__restrict__ sims, const int4 *__restrict__ item
     // and the tile waits for the copy only before its first use of the coefficients
     load_desc(dg, d);
     const Geom geom = dg.geom;
-    fused2d_tile<NN, T, SF, TX, TY, false, Q4_GLOBAL, false, false, true>(
+    constexpr int Q4 = FORM == 1 ? Q4_NOPHI : Q4_GLOBAL;
+    fused2d_tile<NN, T, SF, TX, TY, false, Q4, FORM == 2, false, true>(
         geom, d.coef, static_cast<const SF *>(dg.f[parity]), static_cast<SF *>(dg.f[1 - parity]),
-        static_cast<const T *>(dg.C[parity]), static_cast<T *>(dg.C[1 - parity]), dg.flag, w.y, w.z, smem_raw);
+        static_cast<const T *>(dg.C[parity]), static_cast<T *>(dg.C[1 - parity]), dg.flag, w.y, w.z, smem_raw,
+        FORM == 2 ? static_cast<const T *>(dg.g[parity]) : nullptr, FORM == 2 ? static_cast<T *>(dg.g[1 - parity]) : nullptr);
 }
 
 template <typename T, int TX, int TY>
@@ -145,18 +149,31 @@ constexpr size_t batch_smem() { return Fused2DShape<5, T, TX, TY>::BYTES; }
 
 template <typename T, typename SF, int TX, int TY>
 struct BatchKernels {
-    template <int NN>
+    // the stored-population form exists for 32 x 8 tiles only
+    static constexpr bool kHasForm2 = TY == 8;
+    template <int NN, int FORM>
     static cudaError_t step_attr() {
-        return cudaFuncSetAttribute(k_batch_step<T, SF, TX, TY, NN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    int(Fused2DShape<NN, T, TX, TY>::BYTES));
+        if constexpr (FORM == 2 && !kHasForm2) {
+            return cudaSuccess;
+        } else {
+            return cudaFuncSetAttribute(k_batch_step<T, SF, TX, TY, NN, FORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        int(Fused2DShape<NN, T, TX, TY>::BYTES));
+        }
+    }
+    template <int NN>
+    static cudaError_t step_attr_n() {
+        cudaError_t e = step_attr<NN, 0>();
+        if (e == cudaSuccess) e = step_attr<NN, 1>();
+        if (e == cudaSuccess) e = step_attr<NN, 2>();
+        return e;
     }
     static cudaError_t setup(int *blocks_per_sm) {
         const size_t smem = batch_smem<T, TX, TY>();
         cudaError_t e = cudaFuncSetAttribute(k_batch_persistent<T, SF, TX, TY>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        if ((e = step_attr<2>()) != cudaSuccess || (e = step_attr<3>()) != cudaSuccess ||
-            (e = step_attr<4>()) != cudaSuccess || (e = step_attr<5>()) != cudaSuccess)
+        if ((e = step_attr_n<2>()) != cudaSuccess || (e = step_attr_n<3>()) != cudaSuccess ||
+            (e = step_attr_n<4>()) != cudaSuccess || (e = step_attr_n<5>()) != cudaSuccess)
             return e;
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_persistent<T, SF, TX, TY>,
                                                              TX * TY, smem);
@@ -176,12 +193,22 @@ struct BatchKernels {
                                   static_cast<const BatchSim<T> *>(L.sims), L.items, L.nitems, L.nsteps,
                                   L.parity, L.sync, L.spin_limit, L.expected);
     }
+    template <int NN, int FORM>
+    static void step_nf(const BatchLaunch &L, int parity, cudaStream_t st) {
+        const int q = (NN - 2) * kBatchForms + FORM;
+        if (L.ncount[q] <= 0) return;
+        if constexpr (FORM == 2 && !kHasForm2) {
+            return;                       // never listed: the host keeps such batches on 32 x 8 tiles
+        } else {
+            k_batch_step<T, SF, TX, TY, NN, FORM><<<L.ncount[q], TX * TY, Fused2DShape<NN, T, TX, TY>::BYTES, st>>>(
+                static_cast<const BatchSim<T> *>(L.sims), L.items + L.nstart[q], parity);
+        }
+    }
     template <int NN>
     static void step_n(const BatchLaunch &L, int parity, cudaStream_t st) {
-        const int g = NN - 2;
-        if (L.ncount[g] <= 0) return;
-        k_batch_step<T, SF, TX, TY, NN><<<L.ncount[g], TX * TY, Fused2DShape<NN, T, TX, TY>::BYTES, st>>>(
-            static_cast<const BatchSim<T> *>(L.sims), L.items + L.nstart[g], parity);
+        step_nf<NN, 0>(L, parity, st);
+        step_nf<NN, 1>(L, parity, st);
+        step_nf<NN, 2>(L, parity, st);
     }
     static cudaError_t per_step(const BatchLaunch &L, cudaStream_t st) {
         for (int t = 0; t < L.nsteps; ++t) {

@@ -10,6 +10,10 @@
 namespace nfe {
 
 constexpr int kBatchMaxN = 5;   // component counts 2..5 in a batch
+// forms of a batch member's step: 0 the method as stated, 1 the no-phi ablation (flux potential
+// without phi_j), 2 stored component populations (tau_g != 1)
+constexpr int kBatchForms = 3;
+constexpr int kBatchGroups = (kBatchMaxN - 1) * kBatchForms;   // work-list group (N - 2) * kBatchForms + form
 
 // One simulation as the batched kernel sees it (device memory, read-only).
 // The coefficients come last: the kernel copies the descriptor into shared memory
@@ -18,9 +22,10 @@ template <typename T>
 struct __align__(16) BatchSim {
     Geom geom;
     int N;
-    int pad_;
+    int form;               // 0, 1 or 2, as kBatchForms above
     void *f[2];
     void *C[2];
+    void *g[2];             // component populations (form 2), else null
     int *flag;
     Coef<T> coef;
 };
@@ -48,8 +53,8 @@ struct BatchLaunch {
     long long spin_limit;   // polls before a barrier wait gives up
     unsigned expected;      // CTAs a barrier waits for (normally the grid size)
     int grid;
-    int nstart[kBatchMaxN - 1];   // items of simulations with N = 2 + g: [nstart[g], nstart[g] + ncount[g])
-    int ncount[kBatchMaxN - 1];
+    int nstart[kBatchGroups];     // items of group q (N = 2 + q / kBatchForms, form q % kBatchForms):
+    int ncount[kBatchGroups];     // [nstart[q], nstart[q] + ncount[q])
 };
 
 using BatchSetup = cudaError_t (*)(int *blocks_per_sm);

@@ -912,8 +912,9 @@ struct nfe_batch {
     int variant = -1;
     int grid = 0;
     int nitems = 0;
-    int nstart[kBatchMaxN - 1] = {0};   // work-list range of the simulations with N = 2 + g
-    int ncount[kBatchMaxN - 1] = {0};
+    int nstart[kBatchGroups] = {0};     // work-list range of each (N, form) group
+    int ncount[kBatchGroups] = {0};
+    bool forms = false;                 // some member runs the no-phi or the stored-population form
     int parity = 0;
     int mode = NFE_BATCH_AUTO;        // requested form
     int form = -1;                    // form in use (persistent or per-step) after tuning
@@ -927,16 +928,22 @@ struct nfe_batch {
 
 namespace {
 
+// form of a member's step (kBatchForms)
+int batch_form(const nfe_sim *s) { return s->buf.g[0] ? 2 : (s->no_phi ? 1 : 0); }
+
 template <typename T>
 void fill_batch_sim(const nfe_sim *s, BatchSim<T> &d) {
     std::memset(&d, 0, sizeof d);
     d.geom = s->geom;
     d.N = s->N;
+    d.form = batch_form(s);
     d.coef = *static_cast<const Coef<T> *>(s->coef);
     d.f[0] = s->buf.f[0];
     d.f[1] = s->buf.f[1];
     d.C[0] = s->buf.C[0];
     d.C[1] = s->buf.C[1];
+    d.g[0] = s->buf.g[0];
+    d.g[1] = s->buf.g[1];
     d.flag = s->buf.flag;
 }
 
@@ -952,17 +959,18 @@ nfe_status upload_batch_sim(nfe_batch *b, int i) {
 
 nfe_status batch_items(nfe_batch *b, int v) {
     const int TX = 32, TY = b->ops->ty[v];
-    // simulations grouped by component count: CTAs that run at the same time then execute the
-    // same tile code (one unrolled body per N), which keeps the instruction cache warm (grouping
-    // further by walls or Omega measured no difference)
+    // simulations grouped by component count and form: CTAs that run at the same time then
+    // execute the same tile code (one unrolled body per N), which keeps the instruction cache
+    // warm (grouping further by walls or Omega measured no difference)
+    auto group = [&](int i) { return (b->sims[i]->N - 2) * kBatchForms + batch_form(b->sims[i]); };
     std::vector<int> order(b->nsims);
     for (int i = 0; i < b->nsims; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return b->sims[a]->N < b->sims[c]->N; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return group(a) < group(c); });
     std::vector<int4> items;
-    for (int g = 0; g < kBatchMaxN - 1; ++g) { b->nstart[g] = 0; b->ncount[g] = 0; }
+    for (int q = 0; q < kBatchGroups; ++q) { b->nstart[q] = 0; b->ncount[q] = 0; }
     for (int i : order) {
         const Geom &g = b->sims[i]->geom;
-        const int grp = b->sims[i]->N - 2;
+        const int grp = group(i);
         if (b->ncount[grp] == 0) b->nstart[grp] = int(items.size());
         for (int y0 = 0; y0 < g.ny; y0 += TY)
             for (int x0 = 0; x0 < g.nx; x0 += TX) {
@@ -1001,7 +1009,7 @@ BatchLaunch batch_launch_args(const nfe_batch *b, int64_t nsteps, long long spin
     L.spin_limit = spins;
     L.expected = unsigned(b->grid) + extra;
     L.grid = b->grid;
-    for (int g = 0; g < kBatchMaxN - 1; ++g) { L.nstart[g] = b->nstart[g]; L.ncount[g] = b->ncount[g]; }
+    for (int q = 0; q < kBatchGroups; ++q) { L.nstart[q] = b->nstart[q]; L.ncount[q] = b->ncount[q]; }
     return L;
 }
 
@@ -1024,7 +1032,10 @@ nfe_status batch_autotune(nfe_batch *b) {
     int best_v = 0, best_form = NFE_BATCH_PERSISTENT;
     for (int form = NFE_BATCH_PERSISTENT; form <= NFE_BATCH_PER_STEP; ++form) {
         if (b->mode != NFE_BATCH_AUTO && b->mode != form) continue;
+        // members with the no-phi or stored-population form: per-step launches on 32 x 8 tiles
+        if (b->forms && form == NFE_BATCH_PERSISTENT) continue;
         for (int v = 0; v < kBatchVariants; ++v) {
+            if (b->forms && b->ops->ty[v] != 8) continue;
             nfe_status st = batch_items(b, v);
             if (st != NFE_OK) return st;
             BatchLaunch L = batch_launch_args(b, 1, b->spin_default, 0);
@@ -1090,10 +1101,6 @@ nfe_status nfe_batch_create(int nsims, const nfe_grid *grids, const int *N, cons
         if (grids[i].lattice != NFE_D2Q9) return fail(NFE_EUNSUPPORTED, "batched sweeps are D2Q9 (simulation %d)", i);
         if (N[i] < 2 || N[i] > 5) return fail(NFE_EUNSUPPORTED, "batched sweeps take N = 2..5 (simulation %d)", i);
         if (params[i].precision != prec) return fail(NFE_EINVAL, "all simulations of a batch share one precision");
-        if (params[i].flags & NFE_NO_PHI)
-            return fail(NFE_EUNSUPPORTED, "the no-phi ablation (NFE_NO_PHI) is not available in batched sweeps (simulation %d)", i);
-        if (params[i].tau_g != 0.0 && params[i].tau_g != 1.0)
-            return fail(NFE_EUNSUPPORTED, "batched sweeps run tau_g = 1 (simulation %d)", i);
     }
     nfe_batch *b = new (std::nothrow) nfe_batch();
     if (!b) return fail(NFE_ENOMEM, "host allocation failed");
@@ -1119,6 +1126,7 @@ nfe_status nfe_batch_create(int nsims, const nfe_grid *grids, const int *N, cons
             return fail(st, "simulation %d: %s", i, msg.c_str());
         }
         b->sites += b->sims[i]->geom.n;
+        if (batch_form(b->sims[i]) != 0) b->forms = true;
     }
     b->sim_bytes = prec == NFE_FP64 ? sizeof(BatchSim<double>) : sizeof(BatchSim<float>);
     cudaError_t e = cudaMalloc(&b->d_sims, b->sim_bytes * nsims);
@@ -1151,6 +1159,7 @@ nfe_status nfe_batch_set_fields(nfe_batch *b, int sim, const double *C, const do
         // the batch's current buffer is 1 for every simulation: swap this one's buffers
         std::swap(s->buf.f[0], s->buf.f[1]);
         std::swap(s->buf.C[0], s->buf.C[1]);
+        std::swap(s->buf.g[0], s->buf.g[1]);
         s->buf.cur = 1;
         for (auto &g : s->graph) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
         return upload_batch_sim(b, sim);
@@ -1161,6 +1170,8 @@ nfe_status nfe_batch_set_fields(nfe_batch *b, int sim, const double *C, const do
 nfe_status nfe_batch_set_mode(nfe_batch *b, int mode) {
     if (!b || (mode != NFE_BATCH_PERSISTENT && mode != NFE_BATCH_PER_STEP && mode != NFE_BATCH_AUTO))
         return fail(NFE_EINVAL, "bad mode");
+    if (mode == NFE_BATCH_PERSISTENT && b->forms)
+        return fail(NFE_EUNSUPPORTED, "the persistent form runs members without NFE_NO_PHI and with tau_g = 1");
     CK(cudaStreamSynchronize(b->stream));
     b->mode = mode;
     b->variant = -1;                 // re-tune for the new mode
@@ -1172,6 +1183,7 @@ nfe_status nfe_batch_set_mode(nfe_batch *b, int mode) {
 
 nfe_status nfe_batch_set_barrier_test(nfe_batch *b, int64_t spins, int extra) {
     if (!b || extra < 0) return fail(NFE_EINVAL, "bad arguments");
+    if (b->forms) return fail(NFE_EUNSUPPORTED, "the barrier test runs the persistent form");
     b->spin_next = spins > 0 ? spins : 0;
     b->extra_next = unsigned(extra);
     return NFE_OK;

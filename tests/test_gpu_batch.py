@@ -109,6 +109,58 @@ def test_batch_members_match_oracle(oracle_members, precision, tol_c, tol_v, mod
             assert b.diagnostics(i)["step"] == 41
 
 
+@pytest.mark.parametrize("precision,tol_c,tol_v", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 1e-3)])
+def test_batch_with_no_phi_and_stored_g_members_matches_oracle(precision, tol_c, tol_v):
+    # a batch mixing the method as stated, the no-phi ablation and stored component populations
+    # (tau_g = 0.8 and 1.3): each member against the oracle's literal form of its step
+    plain = _mixture(37, 21, 3, 31)
+    # the no-phi member: a lens with an absent fourth component (implicit component 0)
+    lens = W.lens_2d(nx=40, ny=34, radius=8)
+    sig = np.full((4, 4), 0.005)
+    np.fill_diagonal(sig, 0.0)
+    sig[:3, :3] = lens["sigma"]
+    nophi = W.base_params(9, 40, 34, 1, 4, sig, 1.0, walls=(False, True, False), m=0.05, implicit=0)
+    nophi["C0"] = np.zeros((4,) + lens["C0"].shape[1:])
+    nophi["C0"][:3] = lens["C0"]
+    nophi["flags"] = nfe.NFE_NO_PHI
+    sg1 = _mixture(45, 30, 4, 32)
+    sg1["tau_g"] = 0.8
+    sg2 = _mixture(33, 41, 2, 33)
+    sg2["tau_g"] = 1.3
+    sims = [plain, nophi, sg1, sg2]
+    steps = 30
+    ref = []
+    for p in sims:
+        prm = lbm.Params(p)
+        if p.get("flags", 0) & nfe.NFE_NO_PHI:
+            st = lbm.run(prm, lbm.init_state(prm, p["C0"]), steps, with_phi=False)
+            C, v, P, _ = lbm.fields(prm, st)
+        else:
+            st = lbm.run(prm, lbm.init_state(prm, p["C0"], flux_form="factored"), steps, flux_form="factored")
+            C, v, P, _ = lbm.fields(prm, st, flux_form="factored")
+        ref.append(dict(C=C, v=v, P=P))
+    with nfe.Batch(sims, precision) as b:
+        with pytest.raises(nfe.NfeError) as e:
+            b.set_mode(nfe.NFE_BATCH_PERSISTENT)
+        assert e.value.status == 7
+        for i, p in enumerate(sims):
+            b.set_fields(i, p["C0"])
+        b.step(13)           # odd: parity flips (the stored g swap with f and C)
+        b.set_fields(0, sims[0]["C0"])
+        b.step(steps - 13)
+        b.sync()
+        info = b.info()
+        assert info["form"] == nfe.NFE_BATCH_PER_STEP and info["tile_y"] == 8
+        for i, o in enumerate(ref):
+            if i == 0:
+                continue                  # restarted above
+            Cb, vb, Pb = b.fields(i)
+            errs = dict(C=rel(Cb, o["C"]), v=rel(vb, o["v"]), P=rel(Pb, o["P"]))
+            assert errs["C"] <= tol_c, (i, errs)
+            assert errs["v"] <= tol_v and errs["P"] <= tol_v, (i, errs)
+        assert np.abs(b.fields(1)[0][3]).max() > 1e-7          # the absent component nucleates
+
+
 def test_set_fields_after_odd_steps_and_absent_component():
     sims = _sims()[:3]
     q = sims[0]
