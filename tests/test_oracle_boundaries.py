@@ -127,6 +127,28 @@ def test_outflow_column_relaxes_towards_the_upstream_value():
     assert np.abs(moved - u / (1 + u)).max() < 2e-3
 
 
+def test_outflow_plane_relaxes_towards_the_upstream_value_d3q19():
+    # the same implicit upwind rule on the D3Q19 outflow plane and its ghost plane
+    N, nx, ny, nz, u = 2, 10, 4, 3, 0.02
+    sig = np.array([[0.0, 0.005], [0.005, 0.0]])
+    p = W.base_params(W.D3Q19, nx, ny, nz, N, sig, 1.0)
+    prm = lbm.Params(p)
+    node = np.zeros((nz, ny, nx), int)
+    node[..., 0] = B.INLET0
+    geo = B.Geometry(prm, node, [[u, 0.0, 0.0, 1.0, 0.0]], outflow=True)
+    C0 = np.zeros((N, nz, ny, nx))
+    C0[0] = 1.0
+    C0[0, ..., -1], C0[1, ..., -1] = 0.8, 0.2
+    v0 = np.zeros((3, nz, ny, nx))
+    v0[0] = u
+    st = B.step(prm, geo, B.init_state(prm, geo, C0, v0))
+    C, _, _, _ = B.fields(prm, geo, st)
+    expect = (0.8 + u * 1.0) / (1 + u)
+    assert np.abs(C[0, :, :, -1] - expect).max() < 2e-3
+    moved = (st.ghost[0] - 0.8) / (C[0, :, :, -1] - 0.8)
+    assert np.abs(moved - u / (1 + u)).max() < 2e-3
+
+
 def test_geometry_validation():
     p = W.base_params(W.D2Q9, 8, 4, 1, 2, np.array([[0, 0.005], [0.005, 0]]), 1.0)
     prm = lbm.Params(p)
