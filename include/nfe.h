@@ -14,7 +14,9 @@
  *   - TRT collision with forcing and streaming of the hydrodynamic populations
  *     f_k on D2Q9 or D3Q19 (Sec. III A, Eqs. 22-30, 37-38), and the
  *     Cahn-Hilliard lattice Boltzmann update of the N-1 evolved volume
- *     fractions (Sec. III B, Eqs. 39-43) with tau_g = 1,
+ *     fractions (Sec. III B, Eqs. 39-43): with tau_g = 1 collapsed onto C (no
+ *     stored component populations), or with the populations stored for any
+ *     other tau_g (nfe_params.tau_g),
  *   - halfway bounce-back and the wall-gradient rule on walls, periodic
  *     wrap on every other edge (Sec. III C, Eqs. 44-45);
  *   - solid nodes anywhere in the grid, velocity and volume-fraction inlets and the
